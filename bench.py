@@ -1,0 +1,311 @@
+"""Benchmark of the coupled fluid + solute lattice-Boltzmann step on GB300.
+
+Workload: the miscible layered anisotropic medium, 128^3 cells, FP32
+population storage, solute inlet/outlet, linear hardening viscosity, FP64
+mass / solute / flux reductions every step (the fused per-cell update of
+the paper's Sections 2-4). One "step" = one lattice update of every cell.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun each rank advances its own replica of
+the domain (weak scaling, no data-path collective); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = NZ = 128
+ALGO_BYTES_PER_LUP = 321  # f 152 + h 152 + eps 4 + K^-1 12 + solid mask 1 (FP32 storage)
+METRIC = "coupled LB MLUPS"
+WORKLOAD = ("miscible porous medium 128^3, D3Q19 fluid + D3Q19 solute, FP32 storage, "
+            "diagonal anisotropic K, linear hardening tau(C), inlet/outlet flux, "
+            "FP64 reductions every step")
+PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_miscible128_traffic.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0912_4230_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(prob, budget_s: float = 12.0):
+    """The FP64 oracle on this host's cores, on a bounded sample of the
+    workload: the full lattice for as many steps as fit the budget."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    o = O.Oracle(prob, threads=threads)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(50, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": prob.N * steps / dt / 1e6, "unit": "MLUPS", "cores": threads,
+            "kind": "oracle",
+            "sample": f"full {prob.nx}x{prob.ny}x{prob.nz} lattice, {steps} steps after 1 warm-up "
+                      f"step, FP64, OpenMP over {threads} threads"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: K timed steps (after W warm-up) on a
+    bounded sample of the workload, on the host cores."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_0912_4230_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    prob = W.miscible(NX, NY, NZ, seed=0)
+    o = O.Oracle(prob, threads=threads)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    # bound the whole run to about two minutes: crop the lattice in z if needed
+    budget = 120.0
+    nz = NZ
+    est = one * (args.steps + args.warmup)
+    if est > budget:
+        nz = max(4, int(NZ * budget / est))
+        prob = W.crop(prob, 0, 0, 0, NX, NY, nz)
+        o = O.Oracle(prob, threads=threads)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = prob.N * args.steps / dt / 1e6
+    sample = f"{NX}x{NY}x{nz} lattice (of {NX}x{NY}x{NZ}), {args.steps} steps, FP64"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 * (NZ / nz),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "cells": NX * NY * NZ},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-iters", type=int, default=5)
+    ap.add_argument("--e2e-inner", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(ws)
+    from paper_0912_4230_gb300 import lb, workloads as W
+
+    prob = W.miscible(NX, NY, NZ, seed=rank)
+    stream = torch.cuda.current_stream()
+    lat = lb.Lattice(prob, storage="fp32", check_every=1, stream=stream.cuda_stream)
+    N = prob.N
+    for _ in range(args.warmup):
+        lat.step(1)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            lat.step(1)
+            ev[k][1].record(stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    total_ms = start.elapsed_time(stop)
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    lat.sync()  # raises on a non-finite reduction
+    total_ms = max_over_ranks(ws, total_ms)
+    kern_ms = max_over_ranks(ws, kern_ms)
+    ms_per_step = total_ms / K
+    value = ws * N * K / (total_ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: upload the initial
+    # fields, advance, read the fields and totals back
+    rho0 = torch.from_numpy(prob.rho0).pin_memory()
+    u0 = torch.from_numpy(prob.u0).pin_memory()
+    C0 = torch.from_numpy(prob.C0).pin_memory()
+    out = [torch.empty(n, dtype=torch.float32).pin_memory() for n in (N, 3 * N, N, N)]
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_iters):
+        lb.lb_init(lat.ctx, rho0, u0, C0)
+        lb.lb_step(lat.ctx, args.e2e_inner)
+        lb.lb_fields(lat.ctx, *out)
+        lb.lb_reduce(lat.ctx)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
+    e2e_val = ws * N * args.e2e_inner * args.e2e_iters / e2e_s / 1e6
+    h2d = 5 * N * 4
+    d2h = 6 * N * 4 + 2 * 8 + 48
+
+    peak, peak_kind = measured_peaks()
+    achieved = ALGO_BYTES_PER_LUP * N / (kern_ms * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(PROFILE_JSON):
+        pj = json.load(open(PROFILE_JSON))
+        if pj.get("source_hash") == kernel_source_hash():
+            traffic = pj.get("dram_bytes_per_launch")
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(W.miscible(NX, NY, NZ, seed=0))
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": N, "lattice": [NX, NY, NZ],
+                   "parallelism": f"replicas{ws}",
+                   "l2": f"inputs larger than L2: {ALGO_BYTES_PER_LUP * N / 1e6:.0f} MB moved per step"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "kernel": "step_kernel<StoreF32, KM_DIAG, solute>",
+                     "kernel_ms": kern_ms, "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "step": f"lb_init from pinned host fields + {args.e2e_inner} lattice steps + "
+                        f"lb_fields to pinned host + lb_reduce"},
+        "gpu_launches": K,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * lb.h - C ABI of the GB300 (sm_103a) lattice-Boltzmann library for flow of
+ * mixtures through anisotropic porous media, after Mendoza, Wittel and
+ * Herrmann, "Simulation of Flow of Mixtures Through Anisotropic Porous Media
+ * using a Lattice Boltzmann Model" (arXiv:0912.4230).
+ *
+ * One lattice ("context") lives on one GPU. The calls follow the paper's
+ * statement of the problem (Section 4): the caller sets the porosity field,
+ * the permeability-tensor field, the impermeable cells, the relaxation times
+ * and the boundary conditions (lb_create), then the initial density, velocity,
+ * concentration and cell types (lb_init), advances the coupled fluid + solute
+ * update (lb_step), and reads back density, velocity, concentration and
+ * viscosity (lb_fields).
+ *
+ * Conventions (all calls):
+ *  - Cell index n = x + nx*(y + ny*z), x fastest. Per-cell vectors are packed
+ *    per cell (u[3*n + a]); per-direction arrays are direction-major
+ *    (f[q*N + n]) in the library's D3Q19 order (Section 2.1): q = 0 is the rest
+ *    vector and q = 1 + 6p + (i-1) is orientation i = 1..6 in reference plane
+ *    p = 0 (x-y), 1 (y-z), 2 (z-x); i = 1..4 are the plane's diagonals
+ *    counter-clockwise from (+,+), i = 5, 6 are +/- the plane's first axis.
+ *  - Pointer arguments may point to host memory or to device memory of the
+ *    context's GPU (unified addressing); input arrays are copied and stay
+ *    owned by the caller; output arrays are caller-owned and written in full.
+ *  - The library owns every device allocation it makes (through the allocator
+ *    set by lb_set_allocator, else cudaMalloc) and releases it in lb_destroy.
+ *  - Every call returns LB_OK or a negative LB_E* status; no exception or
+ *    abort crosses the ABI; lb_last_error gives a message for the context.
+ *  - Calls on one context are not thread-safe; distinct contexts are.
+ *  - Work is enqueued on the context's stream (lb_set_stream, default: the
+ *    legacy default stream). Calls that return data to the caller
+ *    (lb_fields, lb_reduce, lb_get_populations, lb_debug_neighbors,
+ *    lb_free_surface_state, lb_sync) synchronise that stream first.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx; /* opaque, library-owned */
+
+enum {
+  LB_OK = 0,
+  LB_EINVAL = -1,        /* invalid argument or field value */
+  LB_ENOMEM = -2,        /* device or host allocation failed */
+  LB_ECUDA = -3,         /* a CUDA runtime call failed */
+  LB_ENONFINITE = -4,    /* a reduction met a NaN or an infinity */
+  LB_ETIMEOUT = -5,      /* a bounded device wait gave up */
+  LB_EUNSUPPORTED = -6   /* valid request outside what this build implements */
+};
+
+/* Face kinds, per axis and side. The fluid lattice takes PERIODIC or WALL
+ * (halfway bounce-back, "impermeability" in Section 4). The solute lattice
+ * takes PERIODIC, WALL, INLET (populations entering through the face carry
+ * the equilibrium of Eq. equild at concentration C_in) or OUTLET
+ * (zero-gradient outflow). Both sides of an axis are periodic or neither. */
+enum { LB_BC_PERIODIC = 0, LB_BC_WALL = 1, LB_BC_INLET = 2, LB_BC_OUTLET = 3 };
+
+/* Population storage (the collision always runs in FP32, or FP64 for
+ * LB_STORE_FP64). FP32 and FP64 store f_q - w_q and h_q; FP16DEV and
+ * BF16DEV store (f_q - w_q)/w_q and h_q/w_q, deviations from the
+ * equilibrium weights normalised by them. */
+enum { LB_STORE_FP32 = 0, LB_STORE_FP64 = 1, LB_STORE_FP16DEV = 2, LB_STORE_BF16DEV = 3 };
+
+/* Free-surface cell types (Section 3). */
+enum { LB_CELL_LIQUID = 0, LB_CELL_INTERFACE = 1, LB_CELL_EMPTY = 2 };
+
+/* Classes returned by lb_debug_neighbors for populations not pulled from a
+ * cell. */
+enum { LB_SRC_NOT_UPDATED = -1, LB_SRC_BOUNCE = -2, LB_SRC_INLET = -3, LB_SRC_OUTLET = -4 };
+
+typedef struct {
+  int32_t nx, ny, nz;   /* lattice size, each >= 1 */
+  int32_t bc[3][2];     /* fluid faces [axis x,y,z][low, high] */
+  int32_t sbc[3][2];    /* solute faces; must be WALL where bc is WALL */
+} lb_domain;
+
+typedef struct {
+  double tau;           /* fluid relaxation time (visc_law 0), > 1/2 */
+  int32_t visc_law;     /* 0 constant tau; 1 tau = tau0 + (tau1-tau0)*clamp(C,0,1);
+                           2 Eq. nuall: nu = nu_g (1 + a e^{alpha t}) e^{beta (1-C)},
+                           tau = 3 nu + 1/2, t = step index (0 at lb_init) */
+  double tau0, tau1;    /* visc_law 1, each > 1/2 */
+  double nu_g, a, alpha, beta; /* visc_law 2 */
+  double G[3];          /* body force per unit mass, Eq. forcement */
+  double A;             /* surface-tension strength, Eqs. equilc1/equilc2 (0 = off) */
+  double wall_rho;      /* colour-gradient density seen at solid cells and
+                           wall faces (wetting); used when A != 0 */
+  double forchheimer;   /* Forchheimer coefficient: the paper gives no term, so
+                           this build accepts 0 only (else LB_EUNSUPPORTED) */
+  int32_t solute;       /* 1: solute lattice on (Section 2.2) */
+  double tau_D;         /* solute relaxation time, > 1/2; D = (tau_D - 1/2)/3 */
+  double C_in;          /* concentration entering through INLET faces */
+  int32_t free_surface; /* 1: free-surface cell types and liquid mass (Section 3);
+                           requires solute = 0 and no permeability (K6 = NULL) */
+  int32_t storage;      /* LB_STORE_* */
+  int32_t check_every;  /* every this many steps the step kernel also forms the
+                           FP64 mass and solute totals and checks them for
+                           NaN/Inf (0 = never) */
+} lb_params;
+
+/* Create a lattice (flowchart of Section 4, "set the porosity field, the
+ * permeability fields, the relaxation times and the boundary conditions").
+ *   porosity  N floats, 0 < eps <= 1 in every non-solid cell (Eq. momentum).
+ *   K6        N*6 floats per cell (K_xx, K_yy, K_zz, K_xy, K_yz, K_zx), a
+ *             symmetric positive-definite permeability tensor (Eq. forcement);
+ *             NULL = infinite permeability (no Darcy force). Diagonal tensors
+ *             (all off-diagonals zero) use a 3-value inverse per cell.
+ *   solid     N bytes, nonzero = impermeable cell (never updated; links into
+ *             it bounce back).
+ * Returns LB_EINVAL for bad sizes, face kinds, tau <= 1/2, eps out of range or
+ * a K that fails a Cholesky test; LB_EUNSUPPORTED for forchheimer != 0 or
+ * free_surface together with solute or K6; LB_ENOMEM/LB_ECUDA on device
+ * failures. *out is NULL on failure. */
+int lb_create(const lb_domain *domain, const float *porosity, const float *K6,
+              const uint8_t *solid, const lb_params *params, lb_ctx **out);
+
+/* Enqueue all further work of the context on this cudaStream_t. */
+int lb_set_stream(lb_ctx *ctx, void *cuda_stream);
+
+/* Initial fields (flowchart steps a-c, Section 4): f = f^eq (Eqs. equilc1,
+ * equilc2) at density rho0 and velocity u0 (taken as V'), h = h^eq (Eq.
+ * equild) at concentration C0; t = 0.
+ *   rho0 N, u0 3N, C0 N (required iff solute), cell_type N (LB_CELL_*,
+ *   required iff free_surface), lambda0 N liquid fraction (NULL: 1 liquid,
+ *   0.5 interface, 0 empty), f_scale 19*N factors multiplying the initial f
+ *   (NULL = 1; seeded perturbations). Solid cells are ignored. */
+int lb_init(lb_ctx *ctx, const float *rho0, const float *u0, const float *C0,
+            const uint8_t *cell_type, const float *lambda0, const float *f_scale);
+
+/* Overwrite / read the post-collision populations as absolute FP64 values
+ * (19*N each, direction-major; h ignored or untouched without solute). */
+int lb_set_populations(lb_ctx *ctx, const double *f, const double *h);
+int lb_get_populations(lb_ctx *ctx, double *f, double *h);
+
+/* Advance n time steps (flowchart steps d-j, Section 4): stream f and h with
+ * periodic wrap, halfway bounce-back and inlet/outlet faces (Eqs. lbe2,
+ * boltzeqD); moments (Eqs. macros1, macros); viscosity from the law; colour
+ * gradient (Eq. macros) when A != 0; V' and the Darcy force (Eqs. forcement,
+ * expandV); BGK collision with forcing (Eqs. coeffforce1, equilc1, equilc2)
+ * and the solute collision (Eq. equild); with a free surface also the mass
+ * exchange, empty-neighbour reconstruction and cell re-typing (Section 3).
+ * Enqueued asynchronously; launch errors return LB_ECUDA. */
+int lb_step(lb_ctx *ctx, int64_t n);
+
+/* Macroscopic fields after the last step (or lb_init): rho, u = V' (3 per
+ * cell), C and the kinematic viscosity nu = (tau - 1/2)/3. Any pointer may be
+ * NULL. Solid and empty cells read 0. Returns LB_ENONFINITE if a reduction of
+ * a previous step flagged NaN/Inf. */
+int lb_fields(lb_ctx *ctx, float *rho, float *u, float *C, float *nu);
+
+/* FP64 totals of the current state, summed in a fixed order: fluid mass
+ * (sum of populations over non-solid cells; with a free surface the liquid
+ * mass sum m, Eq. eq:massmacro), solute sum_q h_q, and the cumulative solute
+ * fluxes through INLET and OUTLET faces since lb_init (in: entered minus
+ * left through inlets; out: left minus re-entered through outlets). Any
+ * pointer may be NULL. */
+int lb_reduce(lb_ctx *ctx, double *mass, double *solute, double *flux_in,
+              double *flux_out);
+
+/* Test hook: for lattice 0 (fluid) or 1 (solute), src[q*N + n] = the cell the
+ * population q of cell n is pulled from, or an LB_SRC_* class. */
+int lb_debug_neighbors(lb_ctx *ctx, int32_t lattice, int32_t *src);
+
+/* Free-surface state: cell types (LB_CELL_*) and liquid mass m per cell. */
+int lb_free_surface_state(lb_ctx *ctx, uint8_t *type, float *mass);
+
+/* Wait for the context's stream; reports LB_ENONFINITE like lb_fields. */
+int lb_sync(lb_ctx *ctx);
+
+/* Steps taken since lb_init. */
+int64_t lb_time(const lb_ctx *ctx);
+
+/* Message of the context's last failure ("" if none); for a NULL context the
+ * message of the last failed lb_create on this thread. */
+const char *lb_last_error(const lb_ctx *ctx);
+
+/* Release the context and all its device memory (NULL is a no-op). */
+void lb_destroy(lb_ctx *ctx);
+
+/* Route the library's device allocations through caller functions (for
+ * example a framework's caching allocator); both NULL restores cudaMalloc.
+ * Affects contexts created afterwards. alloc returns NULL on failure. */
+int lb_set_allocator(void *(*alloc)(size_t bytes, void *user),
+                     void (*release)(void *ptr, void *user), void *user);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB_H */

@@ -1,0 +1,549 @@
+// C ABI of the library (declared in include/lb.h): context management,
+// validation, device memory, and the per-step launch sequence.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_kernels.cuh"
+#include "lb_ops.h"
+
+using namespace lbgb;
+
+namespace {
+
+void *(*g_alloc)(size_t, void *) = nullptr;
+void (*g_release)(void *, void *) = nullptr;
+void *g_alloc_user = nullptr;
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct lb_ctx {
+  lb_domain dom{};
+  lb_params prm{};
+  const StorageOps *ops = nullptr;
+  cudaStream_t stream = nullptr;
+  unsigned N = 0, nblk = 0;
+  int kmode = KM_NONE;
+  bool solute = false, fs = false, has_solid = false, flux = false;
+  unsigned f_wall = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
+  long long t = 0;
+  long long n_live = 0;
+  int cur = 0;
+  void *f[2] = {nullptr, nullptr};
+  void *h[2] = {nullptr, nullptr};
+  void *eps = nullptr, *kinv = nullptr, *geps = nullptr, *rhohat = nullptr;
+  uint32_t *link = nullptr;
+  float *fields = nullptr;
+  double *partials = nullptr;
+  DevState *state = nullptr;
+  // free surface
+  uint8_t *type[2] = {nullptr, nullptr};
+  float *mass[2] = {nullptr, nullptr};
+  float *lam = nullptr;
+  uint8_t *flag = nullptr;
+  // reusable staging for lb_init and the FP64 population exchange
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+  std::vector<void *> allocs;
+  void *(*alloc_fn)(size_t, void *) = nullptr;
+  void (*release_fn)(void *, void *) = nullptr;
+  void *alloc_user = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(lb_ctx *c, int code, const std::string &msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+#define CK(ctx, call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail((ctx), LB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void *dev_alloc(lb_ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  if (c->alloc_fn) {
+    p = c->alloc_fn(bytes, c->alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+void dev_free(lb_ctx *c, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) {
+      c->allocs.erase(c->allocs.begin() + i);
+      break;
+    }
+  if (c->release_fn)
+    c->release_fn(p, c->alloc_user);
+  else
+    cudaFree(p);
+}
+
+void free_all(lb_ctx *c) {
+  for (void *p : c->allocs) {
+    if (c->release_fn)
+      c->release_fn(p, c->alloc_user);
+    else
+      cudaFree(p);
+  }
+  c->allocs.clear();
+}
+
+void *stage(lb_ctx *c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return c->stage;
+  dev_free(c, c->stage);
+  c->stage = dev_alloc(c, bytes);
+  c->stage_bytes = c->stage ? bytes : 0;
+  return c->stage;
+}
+
+unsigned face_mask(const int32_t (&k)[3][2], int kind) {
+  unsigned m = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 2; ++s)
+      if (k[a][s] == kind) m |= 1u << (2 * a + s);
+  return m;
+}
+
+template <class Real>
+void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
+  std::memset(&a, 0, sizeof a);
+  a.nx = c->dom.nx;
+  a.ny = c->dom.ny;
+  a.nz = c->dom.nz;
+  a.N = c->N;
+  a.f_wall = c->f_wall;
+  a.s_wall = c->s_wall;
+  a.s_inlet = c->s_inlet;
+  a.s_outlet = c->s_outlet;
+  a.f_in = c->f[c->cur];
+  a.f_out = c->f[1 - c->cur];
+  a.h_in = c->h[c->cur];
+  a.h_out = c->h[1 - c->cur];
+  a.eps = static_cast<const Real *>(c->eps);
+  a.kinv = static_cast<const Real *>(c->kinv);
+  a.geps = static_cast<const Real *>(c->geps);
+  a.link = c->has_solid ? c->link : nullptr;
+  a.rhohat = static_cast<const Real *>(c->rhohat);
+  for (int i = 0; i < 3; ++i) a.G[i] = Real(c->prm.G[i]);
+  a.tau = Real(c->prm.tau);
+  a.tau0 = Real(c->prm.tau0);
+  a.tau1 = Real(c->prm.tau1);
+  a.nu_g = Real(c->prm.nu_g);
+  a.a_h = Real(c->prm.a);
+  a.alpha = Real(c->prm.alpha);
+  a.beta = Real(c->prm.beta);
+  a.visc_law = c->prm.visc_law;
+  a.A = Real(c->prm.A);
+  a.wall_rho = Real(c->prm.wall_rho);
+  if (c->solute) {
+    a.inv_tau_D = Real(1.0 / c->prm.tau_D);
+    a.D = Real((c->prm.tau_D - 0.5) / 3.0);
+    a.C_in = Real(c->prm.C_in);
+  }
+  a.t = c->t;
+  a.flux = c->flux ? 1 : 0;
+  a.partials = c->partials;
+  a.state = c->state;
+}
+
+// Run fn(args) with StepArgs of the context's collision type.
+template <class Fn>
+int with_args(lb_ctx *c, Fn &&fn) {
+  if (c->ops->fp64) {
+    StepArgs<double> a;
+    fill_args(c, a);
+    return fn(static_cast<void *>(&a), a);
+  }
+  StepArgs<float> a;
+  fill_args(c, a);
+  return fn(static_cast<void *>(&a), a);
+}
+
+int check_status(lb_ctx *c) {
+  DevState st;
+  CK(c, cudaMemcpyAsync(&st, c->state, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (st.status & 1u) return fail(c, LB_ENONFINITE, "a step reduction met a NaN or an infinity");
+  return LB_OK;
+}
+
+bool valid_faces(const int32_t (&k)[3][2], bool fluid) {
+  for (int a = 0; a < 3; ++a) {
+    for (int s = 0; s < 2; ++s) {
+      if (k[a][s] < 0 || k[a][s] > 3) return false;
+      if (fluid && k[a][s] > 1) return false;
+    }
+    if ((k[a][0] == LB_BC_PERIODIC) != (k[a][1] == LB_BC_PERIODIC)) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user) {
+  if ((alloc == nullptr) != (release == nullptr)) return LB_EINVAL;
+  g_alloc = alloc;
+  g_release = release;
+  g_alloc_user = user;
+  return LB_OK;
+}
+
+int lb_create(const lb_domain *dom, const float *porosity, const float *K6, const uint8_t *solid,
+              const lb_params *prm, lb_ctx **out) {
+  if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!dom || !porosity || !solid || !prm)
+    return fail(nullptr, LB_EINVAL, "domain, porosity, solid and params are required");
+  const long long N64 = (long long)dom->nx * dom->ny * dom->nz;
+  if (dom->nx < 1 || dom->ny < 1 || dom->nz < 1 || N64 > 0x7fffffffLL)
+    return fail(nullptr, LB_EINVAL, "lattice size out of range");
+  if (!valid_faces(dom->bc, true) || !valid_faces(dom->sbc, false))
+    return fail(nullptr, LB_EINVAL, "invalid face kinds");
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 2; ++s)
+      if (dom->bc[a][s] == LB_BC_WALL && dom->sbc[a][s] != LB_BC_WALL)
+        return fail(nullptr, LB_EINVAL, "solute faces must be WALL where the fluid has a wall");
+  if (prm->forchheimer != 0.0)
+    return fail(nullptr, LB_EUNSUPPORTED, "Forchheimer term: the paper gives no equation for it");
+  if (prm->visc_law < 0 || prm->visc_law > 2) return fail(nullptr, LB_EINVAL, "visc_law");
+  if (prm->visc_law == 0 && !(prm->tau > 0.5)) return fail(nullptr, LB_EINVAL, "tau <= 1/2");
+  if (prm->visc_law == 1 && !(prm->tau0 > 0.5 && prm->tau1 > 0.5))
+    return fail(nullptr, LB_EINVAL, "tau0, tau1 <= 1/2");
+  if (prm->visc_law == 2 && !(prm->nu_g > 0.0)) return fail(nullptr, LB_EINVAL, "nu_g <= 0");
+  if (prm->visc_law != 0 && !prm->solute)
+    return fail(nullptr, LB_EINVAL, "a concentration-dependent viscosity needs the solute lattice");
+  if (prm->solute && !(prm->tau_D > 0.5)) return fail(nullptr, LB_EINVAL, "tau_D <= 1/2");
+  if (prm->free_surface && (prm->solute || K6))
+    return fail(nullptr, LB_EUNSUPPORTED, "free surface with solute or permeability");
+  if (prm->check_every < 0) return fail(nullptr, LB_EINVAL, "check_every < 0");
+  const StorageOps *ops = nullptr;
+  switch (prm->storage) {
+    case LB_STORE_FP32: ops = &ops_f32(); break;
+    case LB_STORE_FP64: ops = &ops_f64(); break;
+    case LB_STORE_FP16DEV: ops = &ops_f16(); break;
+    case LB_STORE_BF16DEV: ops = &ops_bf16(); break;
+    default: return fail(nullptr, LB_EINVAL, "storage");
+  }
+  if (prm->free_surface && !ops->fs_step)
+    return fail(nullptr, LB_EUNSUPPORTED, "free surface is not built for this storage");
+
+  lb_ctx *c = new (std::nothrow) lb_ctx;
+  if (!c) return fail(nullptr, LB_ENOMEM, "host allocation");
+  c->dom = *dom;
+  c->prm = *prm;
+  c->ops = ops;
+  c->alloc_fn = g_alloc;
+  c->release_fn = g_release;
+  c->alloc_user = g_alloc_user;
+  c->N = unsigned(N64);
+  c->nblk = (c->N + BLOCK - 1) / BLOCK;
+  c->solute = prm->solute != 0;
+  c->fs = prm->free_surface != 0;
+  c->f_wall = face_mask(dom->bc, LB_BC_WALL);
+  c->s_wall = face_mask(dom->sbc, LB_BC_WALL);
+  c->s_inlet = c->solute ? face_mask(dom->sbc, LB_BC_INLET) : 0;
+  c->s_outlet = c->solute ? face_mask(dom->sbc, LB_BC_OUTLET) : 0;
+  c->flux = (c->s_inlet | c->s_outlet) != 0;
+  auto bail = [&](int code) {
+    std::string m = c->err;
+    free_all(c);
+    delete c;
+    g_create_error = m;
+    return code;
+  };
+  const size_t N = c->N;
+  const size_t rb = ops->fp64 ? 8 : 4;
+  const size_t pb = size_t(Q) * N * ops->elt_bytes;
+  // device memory
+  for (int b = 0; b < 2; ++b) {
+    if (!(c->f[b] = dev_alloc(c, pb))) return bail(fail(c, LB_ENOMEM, "populations f"));
+    if (c->solute && !(c->h[b] = dev_alloc(c, pb))) return bail(fail(c, LB_ENOMEM, "populations h"));
+  }
+  c->eps = dev_alloc(c, N * rb);
+  c->link = static_cast<uint32_t *>(dev_alloc(c, N * 4));
+  c->fields = static_cast<float *>(dev_alloc(c, 6 * N * sizeof(float)));
+  c->partials = static_cast<double *>(dev_alloc(c, size_t(c->nblk) * 4 * sizeof(double)));
+  c->state = static_cast<DevState *>(dev_alloc(c, sizeof(DevState)));
+  if (!c->eps || !c->link || !c->fields || !c->partials || !c->state)
+    return bail(fail(c, LB_ENOMEM, "static fields"));
+  if (c->solute && !(c->geps = dev_alloc(c, 3 * N * rb))) return bail(fail(c, LB_ENOMEM, "geps"));
+  if ((prm->A != 0.0 || c->fs) && !(c->rhohat = dev_alloc(c, N * rb)))
+    return bail(fail(c, LB_ENOMEM, "rhohat"));
+  if (c->fs) {
+    for (int b = 0; b < 2; ++b) {
+      c->type[b] = static_cast<uint8_t *>(dev_alloc(c, N));
+      c->mass[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
+      if (!c->type[b] || !c->mass[b]) return bail(fail(c, LB_ENOMEM, "free surface"));
+    }
+    c->lam = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
+    c->flag = static_cast<uint8_t *>(dev_alloc(c, N));
+    if (!c->lam || !c->flag) return bail(fail(c, LB_ENOMEM, "free surface"));
+  }
+  // inputs -> device (caller pointers may be host or device)
+  const size_t in_bytes = N * 4 + (K6 ? 6 * N * 4 : 0) + N + 64;
+  char *in = static_cast<char *>(dev_alloc(c, in_bytes + 256));
+  if (!in) return bail(fail(c, LB_ENOMEM, "staging"));
+  float *eps_in = reinterpret_cast<float *>(in);
+  float *K_in = K6 ? eps_in + N : nullptr;
+  uint8_t *sol_in = reinterpret_cast<uint8_t *>(in + N * 4 + (K6 ? 6 * N * 4 : 0));
+  unsigned *flags = reinterpret_cast<unsigned *>(in + ((in_bytes + 15) & ~size_t(15)));
+  int rc = LB_OK;
+  auto ck = [&](cudaError_t e, const char *what) {
+    if (e != cudaSuccess && rc == LB_OK) rc = fail(c, LB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  ck(cudaMemcpyAsync(eps_in, porosity, N * 4, cudaMemcpyDefault, c->stream), "copy porosity");
+  if (K6) ck(cudaMemcpyAsync(K_in, K6, 6 * N * 4, cudaMemcpyDefault, c->stream), "copy K");
+  ck(cudaMemcpyAsync(sol_in, solid, N, cudaMemcpyDefault, c->stream), "copy solid");
+  ck(cudaMemsetAsync(flags, 0, sizeof(unsigned), c->stream), "memset");
+  ck(cudaMemsetAsync(c->state, 0, sizeof(DevState), c->stream), "memset");
+  if (rc != LB_OK) return bail(rc);
+  SetupArgs sa{};
+  sa.nx = dom->nx;
+  sa.ny = dom->ny;
+  sa.nz = dom->nz;
+  sa.N = c->N;
+  sa.f_wall = c->f_wall;
+  sa.s_wall = c->s_wall;
+  sa.s_open = face_mask(dom->sbc, LB_BC_INLET) | face_mask(dom->sbc, LB_BC_OUTLET);
+  sa.eps_in = eps_in;
+  sa.K6_in = K_in;
+  sa.solid = sol_in;
+  sa.D = c->solute ? (prm->tau_D - 0.5) / 3.0 : 0.0;
+  sa.flags = flags;
+  ck(setup_scan(sa, ops->fp64, c->stream), "setup scan");
+  unsigned hflags = 0;
+  ck(cudaMemcpyAsync(&hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, c->stream), "flags");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  if (rc != LB_OK) return bail(rc);
+  if (hflags & 1u) return bail(fail(c, LB_EINVAL, "porosity outside (0, 1] in a non-solid cell"));
+  if (hflags & 2u) return bail(fail(c, LB_EINVAL, "permeability tensor not positive definite"));
+  c->has_solid = (hflags & 8u) != 0;
+  c->kmode = !K6 ? KM_NONE : ((hflags & 4u) ? KM_SPD : KM_DIAG);
+  if (K6 && !(c->kinv = dev_alloc(c, (c->kmode == KM_SPD ? 6 : 3) * N * rb)))
+    return bail(fail(c, LB_ENOMEM, "K inverse"));
+  sa.eps = c->eps;
+  sa.kinv = c->kinv;
+  sa.geps = c->geps;
+  sa.link = c->link;
+  sa.kmode = c->kmode;
+  ck(setup_fields(sa, ops->fp64, c->stream), "setup fields");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  if (rc != LB_OK) return bail(rc);
+  dev_free(c, in);
+  std::vector<uint8_t> hs(N);
+  // count of live cells, for the mass of the in-step check
+  if (cudaMemcpy(hs.data(), solid, N, cudaMemcpyDefault) == cudaSuccess) {
+    long long live = 0;
+    for (size_t i = 0; i < N; ++i) live += hs[i] == 0;
+    c->n_live = live;
+  }
+  *out = c;
+  return LB_OK;
+}
+
+int lb_set_stream(lb_ctx *c, void *stream) {
+  if (!c) return LB_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LB_OK;
+}
+
+int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
+            const uint8_t *cell_type, const float *lambda0, const float *f_scale) {
+  if (!c) return LB_EINVAL;
+  if (!rho0 || !u0) return fail(c, LB_EINVAL, "rho0 and u0 are required");
+  if (c->solute && !C0) return fail(c, LB_EINVAL, "C0 is required with the solute lattice");
+  if (c->fs && !cell_type) return fail(c, LB_EINVAL, "cell_type is required with a free surface");
+  const size_t N = c->N;
+  const size_t bytes = N * 4 * 5 + (f_scale ? size_t(Q) * N * 4 : 0) + N * 4 + N + 256;
+  char *st = static_cast<char *>(stage(c, bytes));
+  if (!st) return fail(c, LB_ENOMEM, "staging");
+  float *d_rho = reinterpret_cast<float *>(st);
+  float *d_u = d_rho + N;
+  float *d_C = d_u + 3 * N;
+  float *d_lam = d_C + N;
+  float *d_fs = d_lam + N;
+  uint8_t *d_type = reinterpret_cast<uint8_t *>(d_fs + (f_scale ? size_t(Q) * N : 0));
+  CK(c, cudaMemcpyAsync(d_rho, rho0, N * 4, cudaMemcpyDefault, c->stream));
+  CK(c, cudaMemcpyAsync(d_u, u0, 3 * N * 4, cudaMemcpyDefault, c->stream));
+  if (C0) CK(c, cudaMemcpyAsync(d_C, C0, N * 4, cudaMemcpyDefault, c->stream));
+  if (f_scale) CK(c, cudaMemcpyAsync(d_fs, f_scale, size_t(Q) * N * 4, cudaMemcpyDefault, c->stream));
+  if (c->fs) {
+    CK(c, cudaMemcpyAsync(d_type, cell_type, N, cudaMemcpyDefault, c->stream));
+    if (lambda0) CK(c, cudaMemcpyAsync(d_lam, lambda0, N * 4, cudaMemcpyDefault, c->stream));
+  }
+  c->t = 0;
+  c->cur = 0;
+  CK(c, cudaMemsetAsync(c->state, 0, sizeof(DevState), c->stream));
+  if (c->fs) return LB_EUNSUPPORTED;  // free-surface initialisation lives in lb_free_surface.cu
+  if (c->prm.A != 0.0)
+    CK(c, rhohat_init(c->N, c->link, d_rho, nullptr, c->prm.wall_rho, c->rhohat, c->ops->fp64,
+                      c->stream));
+  return with_args(c, [&](void *args, auto &a) {
+    using Real = std::remove_reference_t<decltype(a.G[0])>;
+    a.link = c->link;  // solid cells are always skipped at init
+    a.t = 0;
+    a.fields = c->fields;
+    InitArgs<Real> in{};
+    in.rho0 = d_rho;
+    in.u0 = d_u;
+    in.C0 = C0 ? d_C : nullptr;
+    in.f_scale = f_scale ? d_fs : nullptr;
+    in.type = nullptr;
+    CK(c, c->ops->init(c->kmode, c->solute, args, &in, c->nblk, c->stream));
+    return int(LB_OK);
+  });
+}
+
+int lb_step(lb_ctx *c, int64_t n) {
+  if (!c) return LB_EINVAL;
+  if (n < 0) return fail(c, LB_EINVAL, "n < 0");
+  for (int64_t i = 0; i < n; ++i) {
+    c->t += 1;
+    const bool last = (i == n - 1);
+    const int rc = with_args(c, [&](void *args, auto &a) {
+      a.t = c->t;
+      a.reduce = (c->prm.check_every > 0 && c->t % c->prm.check_every == 0) ? 1 : 0;
+      a.fields = last ? c->fields : nullptr;
+      if (c->prm.A != 0.0) CK(c, c->ops->rhohat(args, c->rhohat, c->nblk, c->stream));
+      CK(c, c->ops->step(c->kmode, c->solute, args, c->nblk, c->stream));
+      return int(LB_OK);
+    });
+    if (rc != LB_OK) return rc;
+    c->cur = 1 - c->cur;
+  }
+  return LB_OK;
+}
+
+int lb_fields(lb_ctx *c, float *rho, float *u, float *C, float *nu) {
+  if (!c) return LB_EINVAL;
+  const size_t N = c->N;
+  if (rho) CK(c, cudaMemcpyAsync(rho, c->fields, N * 4, cudaMemcpyDefault, c->stream));
+  if (u) CK(c, cudaMemcpyAsync(u, c->fields + N, 3 * N * 4, cudaMemcpyDefault, c->stream));
+  if (C) CK(c, cudaMemcpyAsync(C, c->fields + 4 * N, N * 4, cudaMemcpyDefault, c->stream));
+  if (nu) CK(c, cudaMemcpyAsync(nu, c->fields + 5 * N, N * 4, cudaMemcpyDefault, c->stream));
+  return check_status(c);
+}
+
+int lb_reduce(lb_ctx *c, double *mass, double *solute, double *flux_in, double *flux_out) {
+  if (!c) return LB_EINVAL;
+  double *out = static_cast<double *>(stage(c, 64));
+  if (!out) return fail(c, LB_ENOMEM, "staging");
+  double tot[2] = {0.0, 0.0};
+  if (!c->fs) {
+    CK(c, c->ops->totals(c->f[c->cur], c->solute ? c->h[c->cur] : nullptr,
+                         c->has_solid ? c->link : nullptr, c->N, c->partials, c->nblk, c->stream));
+    CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
+    CK(c, cudaMemcpyAsync(tot, out, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
+  }
+  DevState st;
+  CK(c, cudaMemcpyAsync(&st, c->state, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (mass) *mass = tot[0];
+  if (solute) *solute = tot[1];
+  if (flux_in) *flux_in = st.flux_in;
+  if (flux_out) *flux_out = st.flux_out;
+  if (st.status & 1u) return fail(c, LB_ENONFINITE, "a step reduction met a NaN or an infinity");
+  return LB_OK;
+}
+
+int lb_set_populations(lb_ctx *c, const double *f, const double *h) {
+  if (!c) return LB_EINVAL;
+  const size_t N = c->N;
+  double *st = static_cast<double *>(stage(c, size_t(Q) * N * sizeof(double)));
+  if (!st) return fail(c, LB_ENOMEM, "staging");
+  if (f) {
+    CK(c, cudaMemcpyAsync(st, f, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
+    CK(c, c->ops->from_f64(st, c->f[c->cur], c->N, 0, c->stream));
+  }
+  if (h && c->solute) {
+    CK(c, cudaMemcpyAsync(st, h, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
+    CK(c, c->ops->from_f64(st, c->h[c->cur], c->N, 1, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LB_OK;
+}
+
+int lb_get_populations(lb_ctx *c, double *f, double *h) {
+  if (!c) return LB_EINVAL;
+  const size_t N = c->N;
+  double *st = static_cast<double *>(stage(c, size_t(Q) * N * sizeof(double)));
+  if (!st) return fail(c, LB_ENOMEM, "staging");
+  if (f) {
+    CK(c, c->ops->to_f64(c->f[c->cur], st, c->N, 0, c->stream));
+    CK(c, cudaMemcpyAsync(f, st, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  if (h && c->solute) {
+    CK(c, c->ops->to_f64(c->h[c->cur], st, c->N, 1, c->stream));
+    CK(c, cudaMemcpyAsync(h, st, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LB_OK;
+}
+
+int lb_debug_neighbors(lb_ctx *c, int32_t lattice, int32_t *src) {
+  if (!c || !src || lattice < 0 || lattice > 1) return c ? fail(c, LB_EINVAL, "arguments") : LB_EINVAL;
+  const size_t N = c->N;
+  int32_t *st = static_cast<int32_t *>(stage(c, size_t(Q) * N * 4));
+  if (!st) return fail(c, LB_ENOMEM, "staging");
+  const int rc = with_args(c, [&](void *args, auto &a) {
+    a.link = c->link;
+    CK(c, neighbors(args, c->ops->fp64, lattice, st, c->nblk, c->stream));
+    return int(LB_OK);
+  });
+  if (rc != LB_OK) return rc;
+  CK(c, cudaMemcpyAsync(src, st, size_t(Q) * N * 4, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LB_OK;
+}
+
+int lb_free_surface_state(lb_ctx *c, uint8_t *type, float *mass) {
+  if (!c) return LB_EINVAL;
+  if (!c->fs) return fail(c, LB_EINVAL, "no free surface in this context");
+  const size_t N = c->N;
+  if (type) CK(c, cudaMemcpyAsync(type, c->type[c->cur], N, cudaMemcpyDefault, c->stream));
+  if (mass) CK(c, cudaMemcpyAsync(mass, c->mass[c->cur], N * 4, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LB_OK;
+}
+
+int lb_sync(lb_ctx *c) {
+  if (!c) return LB_EINVAL;
+  return check_status(c);
+}
+
+int64_t lb_time(const lb_ctx *c) { return c ? c->t : -1; }
+
+const char *lb_last_error(const lb_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void lb_destroy(lb_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// Shared device-side definitions of the GB300 lattice-Boltzmann library:
+// the D3Q19 velocity set, population storage formats and kernel arguments.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbgb {
+
+constexpr int Q = 19;
+constexpr int BLOCK = 256;  // threads per block of the per-cell kernels
+
+// D3Q19 velocity set in the paper's (orientation i, reference plane p) order
+// (Section 2.1, Fig. d3q19): q = 0 rest; q = 1 + 6p + (i-1) with planes
+// p = 0 (x-y), 1 (y-z), 2 (z-x); i = 1..4 the plane's diagonals
+// counter-clockwise starting at (+first, +second) axis; i = 5, 6 = +/- the
+// plane's first axis. The figure is not reproduced in the paper's text, so
+// this ordering is a reading; the physics does not depend on it.
+__host__ __device__ constexpr int cx(int q) {
+  constexpr int t[Q] = {0, 1, -1, -1, 1, 1, -1, 0, 0, 0, 0, 0, 0, 1, 1, -1, -1, 0, 0};
+  return t[q];
+}
+__host__ __device__ constexpr int cy(int q) {
+  constexpr int t[Q] = {0, 1, 1, -1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 0, 0, 0, 0, 0, 0};
+  return t[q];
+}
+__host__ __device__ constexpr int cz(int q) {
+  constexpr int t[Q] = {0, 0, 0, 0, 0, 0, 0, 1, 1, -1, -1, 0, 0, 1, -1, -1, 1, 1, -1};
+  return t[q];
+}
+// opposite direction: diagonals i <-> i+2 (mod 4), axis 5 <-> 6, same plane
+__host__ __device__ constexpr int opp(int q) {
+  constexpr int t[Q] = {0, 3, 4, 1, 2, 6, 5, 9, 10, 7, 8, 12, 11, 15, 16, 13, 14, 18, 17};
+  return t[q];
+}
+// weights after Eq. equilc2: 1/3 rest, 1/18 axis, 1/36 diagonal
+template <class R>
+__host__ __device__ constexpr R wq(int q) {
+  return q == 0 ? R(1) / R(3)
+                : ((cx(q) * cx(q) + cy(q) * cy(q) + cz(q) * cz(q)) == 1 ? R(1) / R(18)
+                                                                        : R(1) / R(36));
+}
+// 1/w_q, exact small integers
+__host__ __device__ constexpr int inv_wq(int q) {
+  return q == 0 ? 3 : ((cx(q) * cx(q) + cy(q) * cy(q) + cz(q) * cz(q)) == 1 ? 18 : 36);
+}
+
+// Faces of the box, bit index: 0 x-low, 1 x-high, 2 y-low, 3 y-high, 4 z-low, 5 z-high.
+// faces_crossed(q): faces a pull along c_q may leave through (the source is
+// x - c_q, so c = +1 looks at the low face and c = -1 at the high face).
+__host__ __device__ constexpr unsigned faces_crossed(int q) {
+  return (cx(q) > 0 ? 1u : 0u) | (cx(q) < 0 ? 2u : 0u) | (cy(q) > 0 ? 4u : 0u) |
+         (cy(q) < 0 ? 8u : 0u) | (cz(q) > 0 ? 16u : 0u) | (cz(q) < 0 ? 32u : 0u);
+}
+// faces the step x + c_q may leave through (stencils that look forward)
+__host__ __device__ constexpr unsigned faces_ahead(int q) { return faces_crossed(opp(q)); }
+
+// ------------------------------------------------------------------------
+// Population storage formats. ld_f returns f_q - w_q, ld_h returns h_q, both
+// in the collision type Real; st_* take the same quantities.
+// ------------------------------------------------------------------------
+struct StoreF32 {
+  using T = float;
+  using Real = float;
+  static constexpr int id = 0;
+  template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
+  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
+  template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
+  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { __stcs(p, v); }
+  __host__ __device__ static double to_f(T v, int q) { return double(v) + wq<double>(q); }
+  __host__ __device__ static T from_f(double f, int q) { return T(f - wq<double>(q)); }
+  __host__ __device__ static double to_h(T v, int) { return double(v); }
+  __host__ __device__ static T from_h(double h, int) { return T(h); }
+};
+
+struct StoreF64 {
+  using T = double;
+  using Real = double;
+  static constexpr int id = 1;
+  template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
+  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
+  template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
+  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { __stcs(p, v); }
+  __host__ __device__ static double to_f(T v, int q) { return v + wq<double>(q); }
+  __host__ __device__ static T from_f(double f, int q) { return f - wq<double>(q); }
+  __host__ __device__ static double to_h(T v, int) { return v; }
+  __host__ __device__ static T from_h(double h, int) { return h; }
+};
+
+struct StoreF16 {
+  using T = __half;
+  using Real = float;
+  static constexpr int id = 2;
+  template <int q> __device__ __forceinline__ static Real ld_f(const T *p) {
+    return __half2float(__ldg(p)) * wq<float>(q);
+  }
+  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) {
+    __stcs(p, __float2half_rn(v * float(inv_wq(q))));
+  }
+  template <int q> __device__ __forceinline__ static Real ld_h(const T *p) {
+    return __half2float(__ldg(p)) * wq<float>(q);
+  }
+  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) {
+    __stcs(p, __float2half_rn(v * float(inv_wq(q))));
+  }
+  __device__ static double to_f(T v, int q) { return double(__half2float(v)) * wq<double>(q) + wq<double>(q); }
+  __device__ static T from_f(double f, int q) { return __float2half_rn(float((f - wq<double>(q)) * inv_wq(q))); }
+  __device__ static double to_h(T v, int q) { return double(__half2float(v)) * wq<double>(q); }
+  __device__ static T from_h(double h, int q) { return __float2half_rn(float(h * inv_wq(q))); }
+};
+
+struct StoreBF16 {
+  using T = __nv_bfloat16;
+  using Real = float;
+  static constexpr int id = 3;
+  template <int q> __device__ __forceinline__ static Real ld_f(const T *p) {
+    return __bfloat162float(__ldg(p)) * wq<float>(q);
+  }
+  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) {
+    __stcs(p, __float2bfloat16_rn(v * float(inv_wq(q))));
+  }
+  template <int q> __device__ __forceinline__ static Real ld_h(const T *p) {
+    return __bfloat162float(__ldg(p)) * wq<float>(q);
+  }
+  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) {
+    __stcs(p, __float2bfloat16_rn(v * float(inv_wq(q))));
+  }
+  __device__ static double to_f(T v, int q) { return double(__bfloat162float(v)) * wq<double>(q) + wq<double>(q); }
+  __device__ static T from_f(double f, int q) { return __float2bfloat16_rn(float((f - wq<double>(q)) * inv_wq(q))); }
+  __device__ static double to_h(T v, int q) { return double(__bfloat162float(v)) * wq<double>(q); }
+  __device__ static T from_h(double h, int q) { return __float2bfloat16_rn(float(h * inv_wq(q))); }
+};
+
+// ------------------------------------------------------------------------
+// Kernel arguments (passed by value).
+// ------------------------------------------------------------------------
+enum : int { KM_NONE = 0, KM_DIAG = 1, KM_SPD = 2 };
+enum : uint8_t { CELL_LIQUID = 0, CELL_INTERFACE = 1, CELL_EMPTY = 2 };
+
+// Device-resident per-context counters, updated by the last block of a step.
+struct DevState {
+  double flux_in, flux_out;   // cumulative solute fluxes
+  double mass, solute;        // totals of the last checked step
+  unsigned counter;           // blocks finished in the current launch
+  unsigned status;            // bit 0: non-finite total seen
+};
+
+template <class Real>
+struct StepArgs {
+  int nx, ny, nz;
+  unsigned N;
+  // face-kind masks over the 6 faces (bit layout of faces_crossed)
+  unsigned f_wall;                   // fluid wall faces (others periodic)
+  unsigned s_wall, s_inlet, s_outlet;  // solute faces
+  const void *f_in;
+  void *f_out;
+  const void *h_in;
+  void *h_out;
+  const Real *eps;       // N
+  const Real *kinv;      // KM_DIAG: 3 x N (xx, yy, zz); KM_SPD: 6 x N (xx, yy, zz, xy, yz, zx)
+  const Real *geps;      // 3 x N: D grad(eps)/eps (solute only)
+  const uint32_t *link;  // N: bit q = source x - c_q solid; bit 31 = cell solid (NULL: no solids)
+  const Real *rhohat;    // N colour-gradient field (A != 0)
+  Real G[3];
+  Real tau, tau0, tau1, nu_g, a_h, alpha, beta;
+  int visc_law;
+  Real A, wall_rho;
+  Real inv_tau_D, D, C_in;
+  long long t;          // step index after the increment
+  int reduce;           // form mass / solute totals this step
+  int flux;             // inlet/outlet faces present
+  float *fields;        // NULL or 6 x N: rho, ux, uy, uz, C, nu
+  double *partials;     // gridDim.x x 4
+  DevState *state;
+  // free surface
+  const uint8_t *type;  // N cell types at t
+  const float *mass_new;  // N liquid mass after the exchange (m(t+1))
+  float *lam_out;       // N liquid fraction written after collision
+  uint8_t *flag_out;    // N: 1 fill, 2 empty candidate, 0 none
+};
+
+}  // namespace lbgb

@@ -1,0 +1,84 @@
+// Instantiation of every per-cell kernel for one storage format; included by
+// one small translation unit per format (lb_inst_*.cu).
+#pragma once
+
+#include "lb_kernels.cuh"
+#include "lb_ops.h"
+
+namespace lbgb {
+
+template <class S>
+struct Instance {
+  using Real = typename S::Real;
+  using A = StepArgs<Real>;
+
+  template <int KM, bool SOL>
+  static cudaError_t step_t(const A &a, unsigned nblk, cudaStream_t s) {
+    step_kernel<S, KM, SOL><<<nblk, BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t step(int kmode, bool solute, const void *args, unsigned nblk, cudaStream_t s) {
+    const A &a = *static_cast<const A *>(args);
+    switch (kmode * 2 + (solute ? 1 : 0)) {
+      case 0: return step_t<KM_NONE, false>(a, nblk, s);
+      case 1: return step_t<KM_NONE, true>(a, nblk, s);
+      case 2: return step_t<KM_DIAG, false>(a, nblk, s);
+      case 3: return step_t<KM_DIAG, true>(a, nblk, s);
+      case 4: return step_t<KM_SPD, false>(a, nblk, s);
+      default: return step_t<KM_SPD, true>(a, nblk, s);
+    }
+  }
+  template <int KM, bool SOL>
+  static cudaError_t init_t(const A &a, const InitArgs<Real> &in, unsigned nblk, cudaStream_t s) {
+    init_kernel<S, KM, SOL><<<nblk, BLOCK, 0, s>>>(a, in);
+    return cudaGetLastError();
+  }
+  static cudaError_t init(int kmode, bool solute, const void *args, const void *init_args,
+                          unsigned nblk, cudaStream_t s) {
+    const A &a = *static_cast<const A *>(args);
+    const InitArgs<Real> &in = *static_cast<const InitArgs<Real> *>(init_args);
+    // the initial state does not depend on K; one instantiation per lattice set
+    return solute ? init_t<KM_NONE, true>(a, in, nblk, s) : init_t<KM_NONE, false>(a, in, nblk, s);
+  }
+  static cudaError_t rhohat(const void *args, void *rh, unsigned nblk, cudaStream_t s) {
+    rhohat_kernel<S><<<nblk, BLOCK, 0, s>>>(*static_cast<const A *>(args), static_cast<Real *>(rh));
+    return cudaGetLastError();
+  }
+  static cudaError_t to_f64(const void *src, double *dst, unsigned N, int lattice, cudaStream_t s) {
+    const size_t tot = size_t(Q) * N;
+    to_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(
+        static_cast<const typename S::T *>(src), dst, N, lattice);
+    return cudaGetLastError();
+  }
+  static cudaError_t from_f64(const double *src, void *dst, unsigned N, int lattice, cudaStream_t s) {
+    const size_t tot = size_t(Q) * N;
+    from_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(
+        src, static_cast<typename S::T *>(dst), N, lattice);
+    return cudaGetLastError();
+  }
+  static cudaError_t totals(const void *f, const void *h, const uint32_t *link, unsigned N,
+                            double *partials, unsigned nblk, cudaStream_t s) {
+    totals_kernel<S><<<nblk, BLOCK, 0, s>>>(static_cast<const typename S::T *>(f),
+                                             static_cast<const typename S::T *>(h), link, N,
+                                             partials);
+    return cudaGetLastError();
+  }
+  static StorageOps make() {
+    StorageOps o{};
+    o.storage = S::id;
+    o.elt_bytes = sizeof(typename S::T);
+    o.fp64 = sizeof(Real) == 8;
+    o.step = &step;
+    o.init = &init;
+    o.rhohat = &rhohat;
+    o.to_f64 = &to_f64;
+    o.from_f64 = &from_f64;
+    o.totals = &totals;
+    o.fs_mass = nullptr;
+    o.fs_step = nullptr;
+    o.fs_newcells = nullptr;
+    return o;
+  }
+};
+
+}  // namespace lbgb

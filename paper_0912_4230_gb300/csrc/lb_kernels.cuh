@@ -1,0 +1,600 @@
+// Per-cell kernels of the GB300 lattice-Boltzmann library (templated on the
+// population storage format, the permeability mode and the solute lattice).
+//
+// Layout: populations are structure-of-arrays, pop[q * N + n], n = x + nx*(y
+// + ny*z), two buffers (A -> B -> A ...). Streaming is "pull": cell n reads
+// f_q from n - c_q of the previous post-collision buffer, so every population
+// is read once and written once per step and no atomics are needed. One
+// thread owns one cell; consecutive threads are consecutive x, so each of the
+// 19 loads and 19 stores of a warp is one contiguous 128-byte row segment
+// (the x-shifted pulls straddle two segments, whose other half is read by the
+// neighbouring warp and served from L1/L2).
+#pragma once
+
+#include <type_traits>
+
+#include "lb_common.cuh"
+
+namespace lbgb {
+
+template <int I, int N>
+struct Unroll {
+  template <class F>
+  __device__ __forceinline__ static void run(F &&f) {
+    f(std::integral_constant<int, I>{});
+    Unroll<I + 1, N>::run(f);
+  }
+};
+template <int N>
+struct Unroll<N, N> {
+  template <class F>
+  __device__ __forceinline__ static void run(F &&) {}
+};
+
+template <class Real>
+__device__ __forceinline__ Real warp_sum(Real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Geometry of one cell: wrapped index deltas to the six neighbours along the
+// axes and the set of box faces the cell touches.
+struct CellGeo {
+  int dxm, dxp, dym, dyp, dzm, dzp;  // index delta to coord-1 / coord+1, wrapped
+  unsigned onface;                   // faces_crossed bit layout
+};
+
+__device__ __forceinline__ CellGeo cell_geo(unsigned n, unsigned nx, unsigned ny, unsigned nz) {
+  const unsigned x = n % nx, yz = n / nx, y = yz % ny, z = yz / ny;
+  const int sy = int(nx), sz = int(nx * ny);
+  CellGeo g;
+  g.dxm = (x == 0) ? int(nx - 1) : -1;
+  g.dxp = (x == nx - 1) ? -int(nx - 1) : 1;
+  g.dym = (y == 0) ? int(ny - 1) * sy : -sy;
+  g.dyp = (y == ny - 1) ? -int(ny - 1) * sy : sy;
+  g.dzm = (z == 0) ? int(nz - 1) * sz : -sz;
+  g.dzp = (z == nz - 1) ? -int(nz - 1) * sz : sz;
+  g.onface = (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
+             (y == ny - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
+  return g;
+}
+
+// index delta of the pull source n - c_q (wrapped)
+template <int q>
+__device__ __forceinline__ int src_delta(const CellGeo &g) {
+  return (cx(q) > 0 ? g.dxm : (cx(q) < 0 ? g.dxp : 0)) +
+         (cy(q) > 0 ? g.dym : (cy(q) < 0 ? g.dyp : 0)) +
+         (cz(q) > 0 ? g.dzm : (cz(q) < 0 ? g.dzp : 0));
+}
+// index delta of the neighbour n + c_q (wrapped)
+template <int q>
+__device__ __forceinline__ int ahead_delta(const CellGeo &g) {
+  return src_delta<opp(q)>(g);
+}
+
+// Pull classes (shared by the step kernels and the debug export).
+enum : int { PULL_CELL = 0, PULL_BOUNCE = 1, PULL_INLET = 2, PULL_OUTLET = 3 };
+
+template <int q>
+__device__ __forceinline__ int fluid_class(const CellGeo &g, uint32_t link, unsigned f_wall) {
+  if (q == 0) return PULL_CELL;
+  const unsigned fc = faces_crossed(q) & g.onface;
+  if (fc & f_wall) return PULL_BOUNCE;
+  return ((link >> q) & 1u) ? PULL_BOUNCE : PULL_CELL;
+}
+
+template <int q>
+__device__ __forceinline__ int solute_class(const CellGeo &g, uint32_t link, unsigned s_wall,
+                                            unsigned s_inlet, unsigned s_outlet) {
+  if (q == 0) return PULL_CELL;
+  const unsigned fc = faces_crossed(q) & g.onface;
+  if (fc & s_wall) return PULL_BOUNCE;
+  if (fc & s_inlet) return PULL_INLET;
+  if (fc & s_outlet) return PULL_OUTLET;
+  return ((link >> q) & 1u) ? PULL_BOUNCE : PULL_CELL;
+}
+
+// Stream the fluid populations into d[] (f_q - w_q of the arriving populations).
+template <class S>
+__device__ __forceinline__ void gather_f(const typename S::T *__restrict__ fin, unsigned N,
+                                         unsigned n, const CellGeo &g, uint32_t link,
+                                         unsigned f_wall, typename S::Real (&d)[Q]) {
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int cls = fluid_class<q>(g, link, f_wall);
+    const typename S::T *p = (cls == PULL_BOUNCE)
+                                 ? fin + size_t(opp(q)) * N + n
+                                 : fin + size_t(q) * N + (long long)n + src_delta<q>(g);
+    d[q] = S::template ld_f<q>(p);
+  });
+}
+
+// Relaxation time from the viscosity law (Section 2, after Eq. eqsurftens;
+// Eq. nuall for law 2 with t the step index after the increment).
+template <class Real>
+__device__ __forceinline__ Real tau_of(const StepArgs<Real> &a, Real C) {
+  if (a.visc_law == 1) {
+    const Real cl = C < Real(0) ? Real(0) : (C > Real(1) ? Real(1) : C);
+    return a.tau0 + (a.tau1 - a.tau0) * cl;
+  }
+  if (a.visc_law == 2) {
+    const Real nu = a.nu_g * (Real(1) + a.a_h * exp(a.alpha * Real(a.t))) *
+                    exp(a.beta * (Real(1) - C));
+    return Real(3) * nu + Real(0.5);
+  }
+  return a.tau;
+}
+
+// V' = Lambda^-1 (V + eps G / 2), Lambda = I + (eps nu / 2) K^-1, and
+// F^ext = -eps nu K^-1 V' + eps G (Eqs. forcement, expandV, expandVsub).
+template <int KMODE, class Real>
+__device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, unsigned N,
+                                               unsigned n, Real eps, Real nu, const Real (&V)[3],
+                                               const Real (&G)[3], Real (&Vp)[3],
+                                               Real (&Fe)[3]) {
+  const Real r0 = V[0] + Real(0.5) * eps * G[0];
+  const Real r1 = V[1] + Real(0.5) * eps * G[1];
+  const Real r2 = V[2] + Real(0.5) * eps * G[2];
+  const Real en = eps * nu;
+  if (KMODE == KM_NONE) {
+    Vp[0] = r0; Vp[1] = r1; Vp[2] = r2;
+    Fe[0] = eps * G[0]; Fe[1] = eps * G[1]; Fe[2] = eps * G[2];
+  } else if (KMODE == KM_DIAG) {
+    const Real kx = __ldg(kinv + n), ky = __ldg(kinv + N + n), kz = __ldg(kinv + 2 * size_t(N) + n);
+    const Real hs = Real(0.5) * en;
+    Vp[0] = r0 / (Real(1) + hs * kx);
+    Vp[1] = r1 / (Real(1) + hs * ky);
+    Vp[2] = r2 / (Real(1) + hs * kz);
+    Fe[0] = -en * kx * Vp[0] + eps * G[0];
+    Fe[1] = -en * ky * Vp[1] + eps * G[1];
+    Fe[2] = -en * kz * Vp[2] + eps * G[2];
+  } else {
+    const Real kxx = __ldg(kinv + n), kyy = __ldg(kinv + N + n), kzz = __ldg(kinv + 2 * size_t(N) + n);
+    const Real kxy = __ldg(kinv + 3 * size_t(N) + n), kyz = __ldg(kinv + 4 * size_t(N) + n),
+               kzx = __ldg(kinv + 5 * size_t(N) + n);
+    const Real hs = Real(0.5) * en;
+    const Real l00 = Real(1) + hs * kxx, l11 = Real(1) + hs * kyy, l22 = Real(1) + hs * kzz;
+    const Real l01 = hs * kxy, l12 = hs * kyz, l02 = hs * kzx;
+    // adjugate of the symmetric matrix Lambda
+    const Real c00 = l11 * l22 - l12 * l12, c01 = l02 * l12 - l01 * l22, c02 = l01 * l12 - l02 * l11;
+    const Real c11 = l00 * l22 - l02 * l02, c12 = l01 * l02 - l00 * l12, c22 = l00 * l11 - l01 * l01;
+    const Real idet = Real(1) / (l00 * c00 + l01 * c01 + l02 * c02);
+    Vp[0] = (c00 * r0 + c01 * r1 + c02 * r2) * idet;
+    Vp[1] = (c01 * r0 + c11 * r1 + c12 * r2) * idet;
+    Vp[2] = (c02 * r0 + c12 * r1 + c22 * r2) * idet;
+    Fe[0] = -en * (kxx * Vp[0] + kxy * Vp[1] + kzx * Vp[2]) + eps * G[0];
+    Fe[1] = -en * (kxy * Vp[0] + kyy * Vp[1] + kyz * Vp[2]) + eps * G[1];
+    Fe[2] = -en * (kzx * Vp[0] + kyz * Vp[1] + kzz * Vp[2]) + eps * G[2];
+  }
+}
+
+// Colour gradient F = sum_q rhohat(x + c_q) c_q (Eq. macros); a step out
+// through a wall face sees wall_rho (solid cells already hold wall_rho).
+template <class Real>
+__device__ __forceinline__ void colour_gradient(const Real *__restrict__ rh, unsigned n,
+                                                const CellGeo &g, unsigned f_wall, Real wall_rho,
+                                                Real (&F)[3]) {
+  F[0] = F[1] = F[2] = Real(0);
+  Unroll<1, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const bool out = (faces_ahead(q) & g.onface & f_wall) != 0;
+    const Real r = out ? wall_rho : __ldg(rh + (long long)n + ahead_delta<q>(g));
+    if (cx(q)) F[0] += Real(cx(q)) * r;
+    if (cy(q)) F[1] += Real(cy(q)) * r;
+    if (cz(q)) F[2] += Real(cz(q)) * r;
+  });
+}
+
+// BGK collision with the porous equilibrium (Eqs. equilc1, equilc2) and the
+// forcing terms (Eq. coeffforce1, with the weight and density factor w_q rho)
+// for one direction, in deviation form:
+//   f~_q - w_q = (f_q - w_q)(1 - 1/tau) + (f^eq_q - w_q)/tau + T_q.
+template <class Real>
+struct FluidCollide {
+  Real drho, rho, ie, uu, uF, itau, omt, pre, stc, Fn, iFn;
+  Real Vp[3], Fe[3], F[3];
+  bool st;
+
+  template <int q>
+  __device__ __forceinline__ Real feq_dev() const {
+    constexpr Real w = wq<Real>(q);
+    if (q == 0) {
+      return w * (drho - rho * Real(1.5) * ie * uu) + (st ? stc * w * Fn : Real(0));
+    } else {
+      const Real cu = Real(cx(q)) * Vp[0] + Real(cy(q)) * Vp[1] + Real(cz(q)) * Vp[2];
+      Real e = w * (drho + rho * (Real(3) * cu + Real(4.5) * ie * cu * cu - Real(1.5) * ie * uu));
+      if (st) {
+        const Real cF = Real(cx(q)) * F[0] + Real(cy(q)) * F[1] + Real(cz(q)) * F[2];
+        e += w * stc * (cF * cF * iFn - Fn);
+      }
+      return e;
+    }
+  }
+  template <int q>
+  __device__ __forceinline__ Real force() const {
+    constexpr Real w = wq<Real>(q);
+    const Real cu = Real(cx(q)) * Vp[0] + Real(cy(q)) * Vp[1] + Real(cz(q)) * Vp[2];
+    const Real cF = Real(cx(q)) * Fe[0] + Real(cy(q)) * Fe[1] + Real(cz(q)) * Fe[2];
+    return w * pre * (Real(3) * cF + Real(9) * ie * cu * cF - Real(3) * ie * uF);
+  }
+  template <int q>
+  __device__ __forceinline__ Real post(Real d) const {
+    return d * omt + feq_dev<q>() * itau + force<q>();
+  }
+};
+
+// Exported fields, 6 x N floats: rho [N], u packed per cell [3N], C [N], nu [N].
+template <class Real>
+__device__ __forceinline__ void write_fields(float *fl, unsigned N, unsigned n, Real rho,
+                                             const Real (&u)[3], Real C, Real nu) {
+  fl[n] = float(rho);
+  fl[size_t(N) + 3 * size_t(n)] = float(u[0]);
+  fl[size_t(N) + 3 * size_t(n) + 1] = float(u[1]);
+  fl[size_t(N) + 3 * size_t(n) + 2] = float(u[2]);
+  fl[4 * size_t(N) + n] = float(C);
+  fl[5 * size_t(N) + n] = float(nu);
+}
+
+template <class Real>
+__device__ __forceinline__ Real st_threshold();
+template <>
+__device__ __forceinline__ float st_threshold<float>() { return 1e-20f; }
+template <>
+__device__ __forceinline__ double st_threshold<double>() { return 1e-30; }
+
+// Last block of a launch adds the per-block partial sums in a fixed order.
+template <class Real>
+__device__ void reduce_and_finish(const StepArgs<Real> &a, const Real (&v)[4]) {
+  __shared__ double sh_w[BLOCK / 32][4];
+  __shared__ double sh_r[BLOCK][4];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const Real s = warp_sum(v[k]);
+    if (lane == 0) sh_w[warp][k] = double(s);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int w = 0; w < BLOCK / 32; ++w) s += sh_w[w][threadIdx.x];
+    a.partials[size_t(blockIdx.x) * 4 + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&a.state->counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += BLOCK)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += __ldcg(a.partials + size_t(b) * 4 + k);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sh_r[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int s = BLOCK / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sh_r[threadIdx.x][k] += sh_r[threadIdx.x + s][k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    DevState *st = a.state;
+    st->flux_in += sh_r[0][0];
+    st->flux_out += sh_r[0][1];
+    if (a.reduce) {
+      st->mass = sh_r[0][2];
+      st->solute = sh_r[0][3];
+      if (!isfinite(sh_r[0][2]) || !isfinite(sh_r[0][3])) st->status |= 1u;
+    }
+    st->counter = 0;
+  }
+}
+
+// One time step for every non-solid cell: stream f (and h), moments,
+// viscosity, colour gradient, V' and the Darcy force, fluid and solute
+// collision, store; optional fields export and FP64 totals.
+template <class S, int KMODE, bool SOLUTE>
+__global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<typename S::Real> a) {
+  using Real = typename S::Real;
+  using T = typename S::T;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned N = a.N;
+  Real red[4] = {Real(0), Real(0), Real(0), Real(0)};
+  uint32_t link = 0;
+  bool live = n < N;
+  if (live && a.link) {
+    link = __ldg(a.link + n);
+    live = !(link >> 31);
+  }
+  if (live) {
+    const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+    const T *__restrict__ fin = static_cast<const T *>(a.f_in);
+    T *__restrict__ fout = static_cast<T *>(a.f_out);
+    Real d[Q];
+    gather_f<S>(fin, N, n, g, link, a.f_wall, d);
+
+    Real drho = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      drho += d[q];
+      if (cx(q)) j0 += Real(cx(q)) * d[q];
+      if (cy(q)) j1 += Real(cy(q)) * d[q];
+      if (cz(q)) j2 += Real(cz(q)) * d[q];
+    });
+    const Real rho = Real(1) + drho;
+    const Real irho = Real(1) / rho;
+    const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
+    const Real eps = __ldg(a.eps + n);
+
+    Real hh[SOLUTE ? Q : 1];
+    Real sC = Real(0), gx = Real(0), gy = Real(0), gz = Real(0);
+    if (SOLUTE) {
+      const T *__restrict__ hin = static_cast<const T *>(a.h_in);
+      gx = __ldg(a.geps + n);
+      gy = __ldg(a.geps + N + n);
+      gz = __ldg(a.geps + 2 * size_t(N) + n);
+      const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
+      Real fin_acc = Real(0), fout_acc = Real(0);
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
+        Real v;
+        if (cls == PULL_CELL) {
+          v = S::template ld_h<q>(hin + size_t(q) * N + (long long)n + src_delta<q>(g));
+        } else if (cls == PULL_BOUNCE) {
+          v = S::template ld_h<opp(q)>(hin + size_t(opp(q)) * N + n);
+        } else if (cls == PULL_INLET) {
+          // entering through an inlet face: h^eq at C_in with the cell's
+          // bare streamed velocity plus D grad(eps)/eps
+          const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
+          v = wq<Real>(q) * eps * a.C_in * (Real(1) + Real(3) * cv);
+          fin_acc += v - S::template ld_h<opp(q)>(hin + size_t(opp(q)) * N + n);
+        } else {
+          // outlet: the cell's own post-collision value (zero gradient)
+          v = S::template ld_h<q>(hin + size_t(q) * N + n);
+          fout_acc += S::template ld_h<opp(q)>(hin + size_t(opp(q)) * N + n) - v;
+        }
+        hh[SOLUTE ? q : 0] = v;
+        sC += v;
+      });
+      red[0] = fin_acc;
+      red[1] = fout_acc;
+    }
+    const Real C = sC / eps;
+    const Real tau = tau_of(a, C);
+    const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
+
+    FluidCollide<Real> fc;
+    fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
+    if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
+    velocity_solve<KMODE>(a.kinv, N, n, eps, nu, V, a.G, fc.Vp, fc.Fe);
+    fc.drho = drho;
+    fc.rho = rho;
+    fc.ie = Real(1) / eps;
+    fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
+    fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
+    fc.itau = Real(1) / tau;
+    fc.omt = Real(1) - fc.itau;
+    fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
+    fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
+    fc.st = (a.A != Real(0)) && fc.Fn > st_threshold<Real>();
+    fc.stc = fc.st ? a.A * eps * tau : Real(0);
+    fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      S::template st_f<q>(fout + size_t(q) * N + n, fc.template post<q>(d[q]));
+    });
+
+    if (SOLUTE) {
+      T *__restrict__ hout = static_cast<T *>(a.h_out);
+      const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+        const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
+        const Real h = hh[SOLUTE ? q : 0];
+        S::template st_h<q>(hout + size_t(q) * N + n, h + (heq - h) * a.inv_tau_D);
+      });
+    }
+    if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
+    red[2] = drho;
+    red[3] = sC;
+  }
+  if (a.flux || a.reduce) reduce_and_finish(a, red);
+}
+
+// Post-stream density for the colour gradient (flowchart: stream -> moments
+// -> gradient): rhohat = sum_q f_q(x - c_q), solid cells = wall_rho.
+template <class S>
+__global__ void __launch_bounds__(BLOCK) rhohat_kernel(const StepArgs<typename S::Real> a,
+                                                       typename S::Real *rhohat) {
+  using Real = typename S::Real;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  if (n >= a.N) return;
+  uint32_t link = a.link ? __ldg(a.link + n) : 0u;
+  if (link >> 31) {
+    rhohat[n] = a.wall_rho;
+    return;
+  }
+  const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+  Real d[Q];
+  gather_f<S>(static_cast<const typename S::T *>(a.f_in), a.N, n, g, link, a.f_wall, d);
+  Real s = Real(0);
+  Unroll<0, Q>::run([&](auto qc) { s += d[decltype(qc)::value]; });
+  rhohat[n] = Real(1) + s;
+}
+
+// ------------------------------------------------------------------------
+// Initialisation (flowchart step c): f = f^eq, h = h^eq.
+// ------------------------------------------------------------------------
+template <class Real>
+struct InitArgs {
+  const float *rho0, *u0, *C0, *f_scale;  // device copies of the caller's arrays
+  const uint8_t *type;                      // NULL unless free surface
+};
+
+template <class S, int KMODE, bool SOLUTE>
+__global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::Real> a,
+                                                     const InitArgs<typename S::Real> in) {
+  using Real = typename S::Real;
+  using T = typename S::T;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned N = a.N;
+  if (n >= N) return;
+  T *fout = static_cast<T *>(a.f_out);
+  T *fout2 = static_cast<T *>(const_cast<void *>(a.f_in));  // both buffers get the same state
+  const bool solid = a.link && (__ldg(a.link + n) >> 31);
+  const bool empty = in.type && in.type[n] == CELL_EMPTY;
+  if (solid || empty) {
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      // absolute population 0
+      S::template st_f<q>(fout + size_t(q) * N + n, -wq<Real>(q));
+      S::template st_f<q>(fout2 + size_t(q) * N + n, -wq<Real>(q));
+    });
+    if (SOLUTE) {
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        S::template st_h<q>(static_cast<T *>(a.h_out) + size_t(q) * N + n, Real(0));
+        S::template st_h<q>(const_cast<T *>(static_cast<const T *>(a.h_in)) + size_t(q) * N + n,
+                            Real(0));
+      });
+    }
+    if (a.fields)
+      for (int k = 0; k < 6; ++k) a.fields[size_t(k) * N + n] = 0.0f;
+    return;
+  }
+  const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+  const Real rho = Real(in.rho0[n]);
+  const Real u[3] = {Real(in.u0[3 * size_t(n)]), Real(in.u0[3 * size_t(n) + 1]),
+                     Real(in.u0[3 * size_t(n) + 2])};
+  const Real eps = a.eps[n];
+  const Real C = SOLUTE ? Real(in.C0[n]) : Real(0);
+  const Real tau = tau_of(a, C);  // a.t = 0
+  FluidCollide<Real> fc;
+  fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
+  if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
+  fc.drho = rho - Real(1);
+  fc.rho = rho;
+  fc.ie = Real(1) / eps;
+  fc.Vp[0] = u[0]; fc.Vp[1] = u[1]; fc.Vp[2] = u[2];
+  fc.uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
+  fc.st = (a.A != Real(0)) && fc.Fn > st_threshold<Real>();
+  fc.stc = fc.st ? a.A * eps * tau : Real(0);
+  fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    Real dev = fc.template feq_dev<q>();
+    if (in.f_scale) {
+      const Real sc = Real(in.f_scale[size_t(q) * N + n]);
+      dev = (dev + wq<Real>(q)) * sc - wq<Real>(q);
+    }
+    S::template st_f<q>(fout + size_t(q) * N + n, dev);
+    S::template st_f<q>(fout2 + size_t(q) * N + n, dev);
+  });
+  if (SOLUTE) {
+    const Real vs0 = u[0] + a.geps[n], vs1 = u[1] + a.geps[N + n], vs2 = u[2] + a.geps[2 * size_t(N) + n];
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+      const Real h = wq<Real>(q) * eps * C * (Real(1) + Real(3) * cv);
+      S::template st_h<q>(static_cast<T *>(a.h_out) + size_t(q) * N + n, h);
+      S::template st_h<q>(const_cast<T *>(static_cast<const T *>(a.h_in)) + size_t(q) * N + n, h);
+    });
+  }
+  if (a.fields) write_fields(a.fields, N, n, rho, u, C, (tau - Real(0.5)) / Real(3));
+}
+
+// ------------------------------------------------------------------------
+// Populations <-> absolute FP64, totals and the neighbour export.
+// ------------------------------------------------------------------------
+template <class S>
+__global__ void to_f64_kernel(const typename S::T *src, double *dst, unsigned N, int lattice) {
+  const size_t i = size_t(blockIdx.x) * BLOCK + threadIdx.x;
+  if (i >= size_t(Q) * N) return;
+  const int q = int(i / N);
+  dst[i] = lattice == 0 ? S::to_f(src[i], q) : S::to_h(src[i], q);
+}
+
+template <class S>
+__global__ void from_f64_kernel(const double *src, typename S::T *dst, unsigned N, int lattice) {
+  const size_t i = size_t(blockIdx.x) * BLOCK + threadIdx.x;
+  if (i >= size_t(Q) * N) return;
+  const int q = int(i / N);
+  dst[i] = lattice == 0 ? S::from_f(src[i], q) : S::from_h(src[i], q);
+}
+
+// Per-block FP64 sums of the fluid mass and the solute over non-solid cells.
+template <class S>
+__global__ void __launch_bounds__(BLOCK) totals_kernel(const typename S::T *f, const typename S::T *h,
+                                                       const uint32_t *link, unsigned N,
+                                                       double *partials) {
+  __shared__ double sh[BLOCK][2];
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  double m = 0.0, s = 0.0;
+  if (n < N && !(link && (link[n] >> 31))) {
+    for (int q = 0; q < Q; ++q) m += S::to_f(f[size_t(q) * N + n], q);
+    if (h)
+      for (int q = 0; q < Q; ++q) s += S::to_h(h[size_t(q) * N + n], q);
+  }
+  sh[threadIdx.x][0] = m;
+  sh[threadIdx.x][1] = s;
+  __syncthreads();
+  for (int k = BLOCK / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      sh[threadIdx.x][0] += sh[threadIdx.x + k][0];
+      sh[threadIdx.x][1] += sh[threadIdx.x + k][1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * size_t(blockIdx.x)] = sh[0][0];
+    partials[2 * size_t(blockIdx.x) + 1] = sh[0][1];
+  }
+}
+
+// Fixed-order sum of nblk x K partials by one block.
+template <int K>
+__global__ void __launch_bounds__(BLOCK) finish_sum_kernel(const double *partials, unsigned nblk,
+                                                           double *out) {
+  __shared__ double sh[BLOCK][K];
+  double acc[K];
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < nblk; b += BLOCK)
+    for (int k = 0; k < K; ++k) acc[k] += partials[size_t(b) * K + k];
+  for (int k = 0; k < K; ++k) sh[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int s = BLOCK / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < K; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
+    __syncthreads();
+  }
+  if (threadIdx.x < K) out[threadIdx.x] = sh[0][threadIdx.x];
+}
+
+template <class Real>
+__global__ void neighbors_kernel(const StepArgs<Real> a, int lattice, int32_t *src) {
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned N = a.N;
+  if (n >= N) return;
+  const uint32_t link = a.link ? a.link[n] : 0u;
+  const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    int32_t v;
+    if (link >> 31) {
+      v = -1;
+    } else {
+      const int cls = lattice == 0 ? fluid_class<q>(g, link, a.f_wall)
+                                   : solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
+      v = cls == PULL_CELL ? int32_t((long long)n + src_delta<q>(g)) : -(1 + cls);
+    }
+    src[size_t(q) * N + n] = v;
+  });
+}
+
+}  // namespace lbgb

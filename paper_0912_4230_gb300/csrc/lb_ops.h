@@ -1,0 +1,59 @@
+// Host-side table of the kernels compiled for one population storage format.
+// Each storage format is instantiated in its own translation unit so the
+// build compiles them in parallel; the C-ABI layer picks a table at create.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbgb {
+
+struct StorageOps {
+  int storage;       // LB_STORE_*
+  size_t elt_bytes;  // bytes per stored population
+  bool fp64;         // collision type is double (StepArgs<double>)
+  // step / init / rhohat take a StepArgs<Real>* matching fp64
+  cudaError_t (*step)(int kmode, bool solute, const void *args, unsigned nblk, cudaStream_t s);
+  cudaError_t (*init)(int kmode, bool solute, const void *args, const void *init_args,
+                      unsigned nblk, cudaStream_t s);
+  cudaError_t (*rhohat)(const void *args, void *rhohat, unsigned nblk, cudaStream_t s);
+  cudaError_t (*to_f64)(const void *src, double *dst, unsigned N, int lattice, cudaStream_t s);
+  cudaError_t (*from_f64)(const double *src, void *dst, unsigned N, int lattice, cudaStream_t s);
+  cudaError_t (*totals)(const void *f, const void *h, const uint32_t *link, unsigned N,
+                        double *partials, unsigned nblk, cudaStream_t s);
+  // free surface (storage-typed)
+  cudaError_t (*fs_mass)(const void *args, unsigned nblk, cudaStream_t s);
+  cudaError_t (*fs_step)(const void *args, unsigned nblk, cudaStream_t s);
+  cudaError_t (*fs_newcells)(const void *args, unsigned nblk, cudaStream_t s);
+};
+
+const StorageOps &ops_f32();
+const StorageOps &ops_f64();
+const StorageOps &ops_f16();
+const StorageOps &ops_bf16();
+
+// Setup kernels (lb_setup.cu), Real = float or double.
+struct SetupArgs {
+  int nx, ny, nz;
+  unsigned N;
+  unsigned f_wall, s_wall, s_open;  // face masks; s_open = solute inlet | outlet faces
+  const float *eps_in;   // N
+  const float *K6_in;    // 6 x N packed per cell, or NULL
+  const uint8_t *solid;  // N
+  double D;              // solute diffusivity (0 without solute)
+  void *eps;             // N Real
+  void *kinv;            // 3N or 6N Real (SoA), NULL without K
+  void *geps;            // 3N Real or NULL
+  uint32_t *link;        // N
+  unsigned *flags;       // bit 0 bad porosity, 1 K not SPD, 2 K has off-diagonals, 3 some solid
+  int kmode;             // 1 diagonal, 2 full SPD (second pass)
+};
+cudaError_t setup_scan(const SetupArgs &a, bool fp64, cudaStream_t s);
+cudaError_t setup_fields(const SetupArgs &a, bool fp64, cudaStream_t s);
+cudaError_t finish_sum(const double *partials, unsigned nblk, int k, double *out, cudaStream_t s);
+cudaError_t neighbors(const void *args, bool fp64, int lattice, int32_t *src, unsigned nblk,
+                      cudaStream_t s);
+cudaError_t rhohat_init(unsigned N, const uint32_t *link, const float *rho0, const float *mass,
+                        double wall_rho, void *rhohat, bool fp64, cudaStream_t s);
+
+}  // namespace lbgb

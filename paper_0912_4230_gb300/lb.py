@@ -1,0 +1,318 @@
+"""ctypes binding of the CUDA library (C ABI in ``include/lb.h``).
+
+Argument marshalling only: every step of the lattice-Boltzmann update runs in
+the library's CUDA kernels. The functions keep the C names (``lb_create``,
+``lb_step``, ``lb_fields`` ...); :class:`Lattice` wraps one context for a
+:class:`~paper_0912_4230_gb300.workloads.Problem`.
+
+Array arguments may be numpy arrays (host memory) or torch CUDA tensors
+(device memory); both are passed as raw pointers. There is no CPU fallback:
+if the shared library is missing or cannot be loaded this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "liblbgb.so")
+
+Q = 19
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ETIMEOUT, LB_EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6
+PERIODIC, WALL, INLET, OUTLET = 0, 1, 2, 3
+STORE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
+
+EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_get_populations",
+           "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
+           "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator"]
+
+
+class LbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lb error {code}: {msg}")
+        self.code = code
+
+
+class lb_domain(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32),
+                ("bc", (c_int32 * 2) * 3), ("sbc", (c_int32 * 2) * 3)]
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("tau", c_double), ("visc_law", c_int32), ("tau0", c_double), ("tau1", c_double),
+                ("nu_g", c_double), ("a", c_double), ("alpha", c_double), ("beta", c_double),
+                ("G", c_double * 3), ("A", c_double), ("wall_rho", c_double),
+                ("forchheimer", c_double), ("solute", c_int32), ("tau_D", c_double),
+                ("C_in", c_double), ("free_surface", c_int32), ("storage", c_int32),
+                ("check_every", c_int32)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = c_void_p
+    L.lb_create.argtypes = [POINTER(lb_domain), vp, vp, vp, POINTER(lb_params), POINTER(vp)]
+    L.lb_set_stream.argtypes = [vp, vp]
+    L.lb_init.argtypes = [vp] * 7
+    L.lb_set_populations.argtypes = [vp, vp, vp]
+    L.lb_get_populations.argtypes = [vp, vp, vp]
+    L.lb_step.argtypes = [vp, c_int64]
+    L.lb_fields.argtypes = [vp] * 5
+    L.lb_reduce.argtypes = [vp] * 5
+    L.lb_debug_neighbors.argtypes = [vp, c_int32, vp]
+    L.lb_free_surface_state.argtypes = [vp, vp, vp]
+    L.lb_sync.argtypes = [vp]
+    L.lb_time.argtypes = [vp]
+    L.lb_time.restype = c_int64
+    L.lb_last_error.argtypes = [vp]
+    L.lb_last_error.restype = ctypes.c_char_p
+    L.lb_destroy.argtypes = [vp]
+    L.lb_destroy.restype = None
+    ALLOC = ctypes.CFUNCTYPE(vp, c_size_t, vp)
+    FREE = ctypes.CFUNCTYPE(None, vp, vp)
+    L.lb_set_allocator.argtypes = [ALLOC, FREE, vp]
+    L._ALLOC, L._FREE = ALLOC, FREE
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return c_void_p(a.data_ptr())
+    return a.ctypes.data_as(c_void_p)
+
+
+def _check(rc: int, ctx=None):
+    if rc != LB_OK:
+        msg = load().lb_last_error(ctx).decode(errors="replace")
+        raise LbError(rc, msg)
+
+
+# ---------------------------------------------------------------- C names
+
+def lb_create(domain: lb_domain, porosity, K6, solid, params: lb_params):
+    ctx = c_void_p()
+    rc = load().lb_create(ctypes.byref(domain), _ptr(porosity), _ptr(K6), _ptr(solid),
+                          ctypes.byref(params), ctypes.byref(ctx))
+    _check(rc, None)
+    return ctx
+
+
+def lb_set_stream(ctx, stream_handle: int):
+    _check(load().lb_set_stream(ctx, c_void_p(stream_handle)), ctx)
+
+
+def lb_init(ctx, rho0, u0, C0=None, cell_type=None, lambda0=None, f_scale=None):
+    _check(load().lb_init(ctx, _ptr(rho0), _ptr(u0), _ptr(C0), _ptr(cell_type), _ptr(lambda0),
+                          _ptr(f_scale)), ctx)
+
+
+def lb_set_populations(ctx, f=None, h=None):
+    _check(load().lb_set_populations(ctx, _ptr(f), _ptr(h)), ctx)
+
+
+def lb_get_populations(ctx, f=None, h=None):
+    _check(load().lb_get_populations(ctx, _ptr(f), _ptr(h)), ctx)
+
+
+def lb_step(ctx, n: int):
+    _check(load().lb_step(ctx, int(n)), ctx)
+
+
+def lb_fields(ctx, rho=None, u=None, C=None, nu=None):
+    _check(load().lb_fields(ctx, _ptr(rho), _ptr(u), _ptr(C), _ptr(nu)), ctx)
+
+
+def lb_reduce(ctx):
+    out = [c_double() for _ in range(4)]
+    _check(load().lb_reduce(ctx, *[ctypes.byref(o) for o in out]), ctx)
+    return np.array([o.value for o in out])
+
+
+def lb_debug_neighbors(ctx, lattice: int, src):
+    _check(load().lb_debug_neighbors(ctx, int(lattice), _ptr(src)), ctx)
+
+
+def lb_free_surface_state(ctx, cell_type=None, mass=None):
+    _check(load().lb_free_surface_state(ctx, _ptr(cell_type), _ptr(mass)), ctx)
+
+
+def lb_sync(ctx):
+    _check(load().lb_sync(ctx), ctx)
+
+
+def lb_time(ctx) -> int:
+    return load().lb_time(ctx)
+
+
+def lb_last_error(ctx=None) -> str:
+    return load().lb_last_error(ctx).decode(errors="replace")
+
+
+def lb_destroy(ctx):
+    load().lb_destroy(ctx)
+
+
+_allocator_refs = None
+
+
+def lb_set_allocator(alloc=None, release=None):
+    """Route device allocations through Python callables alloc(nbytes) -> int
+    pointer and release(ptr); ``use_torch_allocator()`` installs torch's."""
+    global _allocator_refs
+    L = load()
+    if alloc is None:
+        _check(L.lb_set_allocator(L._ALLOC(0), L._FREE(0), None))
+        _allocator_refs = None
+        return
+
+    def _a(nbytes, _user):
+        try:
+            return alloc(int(nbytes)) or None
+        except Exception:
+            return None
+
+    def _r(ptr, _user):
+        release(ptr)
+
+    refs = (L._ALLOC(_a), L._FREE(_r))
+    _check(L.lb_set_allocator(refs[0], refs[1], None))
+    _allocator_refs = refs
+
+
+def use_torch_allocator():
+    """Allocate the library's device memory from torch's caching allocator."""
+    import torch
+    lb_set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n),
+                     lambda p: torch.cuda.caching_allocator_delete(p))
+
+
+# ---------------------------------------------------------------- convenience
+
+def make_domain(prob) -> lb_domain:
+    d = lb_domain()
+    d.nx, d.ny, d.nz = prob.nx, prob.ny, prob.nz
+    for a in range(3):
+        for s in range(2):
+            d.bc[a][s] = prob.bc[a][s]
+            d.sbc[a][s] = prob.sbc[a][s]
+    return d
+
+
+def make_params(prob, storage=None, check_every=0) -> lb_params:
+    k = prob.params
+    p = lb_params()
+    p.tau = k.get("tau", 1.0)
+    p.visc_law = k.get("visc_law", 0)
+    p.tau0, p.tau1 = k.get("tau0", 1.0), k.get("tau1", 1.0)
+    p.nu_g, p.a, p.alpha, p.beta = (k.get("nu_g", 0.0), k.get("a", 0.0), k.get("alpha", 0.0),
+                                    k.get("beta", 0.0))
+    for i in range(3):
+        p.G[i] = k.get("G", (0.0, 0.0, 0.0))[i]
+    p.A = k.get("A", 0.0)
+    p.wall_rho = k.get("wall_rho", 0.0)
+    p.forchheimer = k.get("forchheimer", 0.0)
+    p.solute = int(k.get("solute", 0))
+    p.tau_D = k.get("tau_D", 1.0)
+    p.C_in = k.get("C_in", 0.0)
+    p.free_surface = int(k.get("free_surface", 0))
+    p.storage = STORE[storage or prob.storage]
+    p.check_every = check_every
+    return p
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Lattice:
+    """One library context built from a workload description."""
+
+    def __init__(self, prob, storage=None, check_every=0, stream=None, init=True):
+        self.prob = prob
+        self.N = prob.N
+        self.solute = bool(prob.params.get("solute"))
+        self.fs = bool(prob.params.get("free_surface"))
+        self._dom = make_domain(prob)
+        self._prm = make_params(prob, storage, check_every)
+        self.ctx = lb_create(self._dom, _f32(prob.eps), _f32(prob.K6),
+                             np.ascontiguousarray(prob.solid, np.uint8), self._prm)
+        if stream is not None:
+            lb_set_stream(self.ctx, stream)
+        if init:
+            self.init()
+
+    def init(self, rho0=None, u0=None, C0=None):
+        p = self.prob
+        lb_init(self.ctx, _f32(p.rho0 if rho0 is None else rho0),
+                _f32(p.u0 if u0 is None else u0),
+                _f32(p.C0 if C0 is None else C0) if self.solute else None,
+                None if p.cell_type is None else np.ascontiguousarray(p.cell_type, np.uint8),
+                _f32(p.lambda0), _f32(p.f_scale))
+
+    def step(self, n=1):
+        lb_step(self.ctx, n)
+
+    @property
+    def t(self):
+        return lb_time(self.ctx)
+
+    def fields(self):
+        N = self.N
+        rho, u = np.zeros(N, np.float32), np.zeros(3 * N, np.float32)
+        C, nu = np.zeros(N, np.float32), np.zeros(N, np.float32)
+        lb_fields(self.ctx, rho, u, C, nu)
+        return rho, u.reshape(N, 3), C, nu
+
+    def reduce(self):
+        return lb_reduce(self.ctx)
+
+    def populations(self):
+        f = np.zeros(Q * self.N)
+        h = np.zeros(Q * self.N) if self.solute else None
+        lb_get_populations(self.ctx, f, h)
+        return f.reshape(Q, self.N), (None if h is None else h.reshape(Q, self.N))
+
+    def set_populations(self, f=None, h=None):
+        lb_set_populations(self.ctx, None if f is None else np.ascontiguousarray(f, np.float64),
+                           None if h is None else np.ascontiguousarray(h, np.float64))
+
+    def neighbors(self, lattice=0):
+        src = np.zeros(Q * self.N, np.int32)
+        lb_debug_neighbors(self.ctx, lattice, src)
+        return src.reshape(Q, self.N)
+
+    def free_surface_state(self):
+        t = np.zeros(self.N, np.uint8)
+        m = np.zeros(self.N, np.float32)
+        lb_free_surface_state(self.ctx, t, m)
+        return t, m
+
+    def sync(self):
+        lb_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

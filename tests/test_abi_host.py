@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/lb.h declares, and rejects invalid requests before
+touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_0912_4230_gb300 import build as lib_build
+from paper_0912_4230_gb300 import lb, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    lib_build.build()
+    return lb.load()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "lb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(lb.EXPORTS)
+
+
+def test_struct_layouts_match_header():
+    # lb_domain: 3 + 6 + 6 int32; lb_params: doubles and int32 in header order
+    assert lb.lb_domain.bc.offset == 12 and lb.lb_domain.sbc.offset == 36
+    src = open(os.path.join(ROOT, "include", "lb.h")).read()
+    body = src[src.index("typedef struct {\n  double tau;") + len("typedef struct {"):src.index("} lb_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        names += [v.strip().split("[")[0] for v in decl.split(None, 1)[1].split(",")]
+    assert names == [f[0] for f in lb.lb_params._fields_]
+
+
+def _create(prob, **over):
+    dom = lb.make_domain(prob)
+    prm = lb.make_params(prob)
+    for k, v in over.items():
+        if k.startswith("dom_"):
+            setattr(dom, k[4:], v)
+        else:
+            setattr(prm, k, v)
+    return lb.lb_create(dom, prob.eps, prob.K6, prob.solid, prm)
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(forchheimer=0.5), lb.LB_EUNSUPPORTED),
+    (dict(visc_law=0, tau=0.5), lb.LB_EINVAL),
+    (dict(tau0=0.5), lb.LB_EINVAL),
+    (dict(solute=0), lb.LB_EINVAL),
+    (dict(visc_law=3), lb.LB_EINVAL),
+    (dict(tau_D=0.4), lb.LB_EINVAL),
+    (dict(storage=9), lb.LB_EINVAL),
+    (dict(check_every=-1), lb.LB_EINVAL),
+    (dict(free_surface=1), lb.LB_EUNSUPPORTED),
+    (dict(dom_nx=0), lb.LB_EINVAL),
+])
+def test_invalid_requests_are_rejected_on_the_host(L, over, code):
+    prob = W.random_medium(4, 4, 4, seed=0)
+    with pytest.raises(lb.LbError) as e:
+        _create(prob, **over)
+    assert e.value.code == code
+    assert lb.lb_last_error(None)
+
+
+def test_invalid_face_kinds_rejected(L):
+    prob = W.random_medium(4, 4, 4, seed=0)
+    dom = lb.make_domain(prob)
+    dom.bc[0][0] = W.WALL       # one side periodic, the other a wall
+    dom.bc[0][1] = W.PERIODIC
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_create(dom, prob.eps, prob.K6, prob.solid, lb.make_params(prob))
+    assert e.value.code == lb.LB_EINVAL
+    dom = lb.make_domain(prob)
+    dom.bc[2][0] = dom.bc[2][1] = W.INLET  # fluid faces cannot be inlets
+    with pytest.raises(lb.LbError):
+        lb.lb_create(dom, prob.eps, prob.K6, prob.solid, lb.make_params(prob))

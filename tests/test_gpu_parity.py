@@ -1,0 +1,194 @@
+"""GPU (CUDA library through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP32 storage max|du| <= 1e-5 max|u|, max|drho| <= 1e-6,
+max|dC| <= 1e-5, max|dnu| <= 3.4e-6 (nu = (tau0 + (tau1 - tau0) C - 1/2)/3
+turns the C tolerance into 0.3e-5); FP64 storage 1e-11 relative on u and
+1e-12 on rho. Index work (pull sources, boundary classes) is bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0912_4230_gb300 import lb, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {
+    "fp32": dict(u=1e-5, rho=1e-6, C=1e-5, nu=3.4e-6),
+    "fp64": dict(u=1e-11, rho=1e-12, C=1e-12, nu=1e-12),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def run_both(prob, steps, storage, threads=0, check_every=0):
+    g = lb.Lattice(prob, storage=storage, check_every=check_every)
+    g.step(steps)
+    o = O.Oracle(prob, threads=threads)
+    o.step(steps)
+    return g, o
+
+
+def compare(g, o, prob, storage, tol=None):
+    tol = tol or TOL[storage]
+    rho, u, C, nu = g.fields()
+    r_rho, r_u, r_C, r_nu = o.fields()
+    live = prob.solid == 0
+    if prob.cell_type is not None:
+        t, _ = o.free_surface_state()
+        live = live & (t != W.EMPTY)
+    umax = np.abs(r_u[live]).max()
+    err = dict(
+        u=np.abs(u[live] - r_u[live]).max() / umax if umax > 0 else np.abs(u[live]).max(),
+        rho=np.abs(rho[live] - r_rho[live]).max(),
+        C=np.abs(C[live] - r_C[live]).max(),
+        nu=np.abs(nu[live] - r_nu[live]).max(),
+    )
+    for k in ("u", "rho", "C", "nu"):
+        assert err[k] <= tol[k], (k, err)
+    return err
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 5), (4, 3, 5), (1, 2, 3), (37, 5, 3)])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_neighbor_table_bit_exact(dims, seed):
+    prob = W.random_medium(*dims, seed=seed, solid_frac=0.2)
+    g = lb.Lattice(prob, storage="fp32")
+    o = O.Oracle(prob)
+    for lattice in (0, 1):
+        assert np.array_equal(g.neighbors(lattice), o.neighbors(lattice))
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("law", [1, 2])
+@pytest.mark.parametrize("A", [0.0, 1e-3])
+def test_random_medium_all_features(storage, law, A):
+    """Every feature at once: random porosity, full SPD K, solid cells, walls,
+    solute inlet/outlet, hardening law, surface tension, body force; sizes
+    spanning several blocks with a ragged tail."""
+    prob = W.random_medium(19, 13, 11, seed=21, visc_law=law, A=A)
+    g, o = run_both(prob, 25, storage)
+    compare(g, o, prob, storage)
+    f, h = g.populations()
+    rf, rh = o.populations()
+    live = prob.solid == 0
+    tolp = 1e-13 if storage == "fp64" else 2e-7
+    assert np.abs(f[:, live] - rf[:, live]).max() < tolp
+    assert np.abs(h[:, live] - rh[:, live]).max() < tolp
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_diagonal_and_no_permeability(storage):
+    p = W.random_medium(17, 9, 8, seed=5, spd=False)
+    g, o = run_both(p, 20, storage)
+    compare(g, o, p, storage)
+    p2 = p.replace(K6=None)
+    g, o = run_both(p2, 20, storage)
+    compare(g, o, p2, storage)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_plain_channel_full(storage):
+    """16x16x64 plain channel, 2000 steps, against the oracle and against the
+    Darcy velocity in the bulk."""
+    p = W.plain_channel()
+    g, o = run_both(p, p.steps, storage)
+    compare(g, o, p, storage)
+    _, u, _, _ = g.fields()
+    darcy = 1e-6 * float(np.float32(1e-2)) / 0.1
+    bulk = u[:, 0].reshape(p.shape)[20:-20]
+    assert np.abs(bulk / darcy - 1).max() < (1e-9 if storage == "fp64" else 1e-4)
+
+
+def test_miscible_small_parity_and_balances():
+    """Layered anisotropic medium with solute inlet (40x36x30, 300 steps):
+    fields against the oracle, and the GPU's own solute and mass balance."""
+    p = W.miscible(40, 36, 30, seed=3)
+    g = lb.Lattice(p, storage="fp32", check_every=1)
+    m0 = g.reduce()
+    g.step(300)
+    o = O.Oracle(p)
+    o.step(300)
+    err = compare(g, o, p, "fp32")
+    r = g.reduce()
+    ro = o.reduce()
+    assert r[0] == pytest.approx(m0[0], rel=1e-9)          # mass
+    assert r[2] == pytest.approx(ro[2], rel=1e-5)          # flux in
+    assert r[3] == pytest.approx(ro[3], rel=1e-4, abs=1e-9)  # flux out
+    assert (r[1] - m0[1]) == pytest.approx(r[2] - r[3], rel=1e-4)
+    assert err["u"] < 1e-5
+
+
+def test_miscible_full_size_first_steps():
+    """128^3 in the benchmark's launch configuration: three steps from the
+    seeded initial state, every cell against the oracle."""
+    p = W.miscible(128, 128, 128, seed=0)
+    g, o = run_both(p, 3, "fp32")
+    compare(g, o, p, "fp32")
+
+
+def test_precision_crop_spd_fp32():
+    """32^3 crop of the rotated-tensor medium, FP32 storage."""
+    big = W.precision(64, 64, 64, storage="fp32")
+    p = W.crop(big, 16, 0, 8, 32, 32, 32)
+    g, o = run_both(p, 200, "fp32")
+    compare(g, o, p, "fp32")
+
+
+@pytest.mark.parametrize("storage,bound", [("fp16", 1e-3), ("bf16", 2e-2)])
+def test_reduced_precision_storage_error(storage, bound):
+    """FP16 / BF16 deviation storage on the rotated-tensor crop: error of u
+    against the FP64 oracle, relative to max|u|, and mass drift."""
+    big = W.precision(64, 64, 64, storage=storage)
+    p = W.crop(big, 16, 0, 8, 32, 32, 32)
+    g = lb.Lattice(p, storage=storage)
+    m0 = g.reduce()[0]
+    g.step(200)
+    o = O.Oracle(p)
+    o.step(200)
+    _, u, _, _ = g.fields()
+    _, ru, _, _ = o.fields()
+    rel = np.abs(u - ru).max() / np.abs(ru).max()
+    print(f"{storage}: max|du|/max|u| = {rel:.3e}")
+    assert rel <= bound
+    assert abs(g.reduce()[0] / m0 - 1) <= 1e-6
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN population makes the step's FP64 reduction report LB_ENONFINITE."""
+    p = W.random_medium(8, 8, 8, seed=2)
+    g = lb.Lattice(p, storage="fp32", check_every=1)
+    f, h = g.populations()
+    f[3, 17] = np.nan
+    g.set_populations(f, h)
+    g.step(2)
+    with pytest.raises(lb.LbError) as e:
+        g.sync()
+    assert e.value.code == lb.LB_ENONFINITE
+
+
+def test_single_cell_and_thin_lattices():
+    for dims in [(1, 1, 1), (1, 1, 7), (5, 1, 1)]:
+        p = W.random_medium(*dims, seed=9, solid_frac=0.0, walls=False, inlet=False)
+        g, o = run_both(p, 10, "fp64")
+        compare(g, o, p, "fp64")
+
+
+def test_torch_allocator_and_stream():
+    torch = pytest.importorskip("torch")
+    lb.use_torch_allocator()
+    try:
+        s = torch.cuda.Stream()
+        p = W.random_medium(12, 10, 8, seed=6)
+        g = lb.Lattice(p, storage="fp32", stream=s.cuda_stream)
+        g.step(5)
+        o = O.Oracle(p)
+        o.step(5)
+        compare(g, o, p, "fp32")
+        g.close()
+    finally:
+        lb.lb_set_allocator(None)
