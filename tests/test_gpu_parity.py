@@ -2,8 +2,10 @@
 
 Tolerances: FP32 storage max|du| <= 1e-5 max|u|, max|drho| <= 1e-6,
 max|dC| <= 1e-5, max|dnu| <= 3.4e-6 (nu = (tau0 + (tau1 - tau0) C - 1/2)/3
-turns the C tolerance into 0.3e-5); FP64 storage 1e-11 relative on u and
-1e-12 on rho. Index work (pull sources, boundary classes) is bit-exact.
+turns the C tolerance into 0.3e-5). FP64 storage: the populations agree to
+1e-13 (absolute, values ~0.05); the exported fields are float32, so they
+agree to float32 rounding (2^-24 relative, 1.2e-7 with margin). Index work
+(pull sources, boundary classes) is bit-exact.
 """
 import numpy as np
 import pytest
@@ -15,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {
     "fp32": dict(u=1e-5, rho=1e-6, C=1e-5, nu=3.4e-6),
-    "fp64": dict(u=1e-11, rho=1e-12, C=1e-12, nu=1e-12),
+    "fp64": dict(u=1.2e-7, rho=1.2e-7, C=1.2e-7, nu=1.2e-7),
 }
 
 
@@ -98,10 +100,14 @@ def test_plain_channel_full(storage):
     p = W.plain_channel()
     g, o = run_both(p, p.steps, storage)
     compare(g, o, p, storage)
+    if storage == "fp64":
+        f, _ = g.populations()
+        rf, _ = o.populations()
+        assert np.abs(f - rf).max() < 1e-13
     _, u, _, _ = g.fields()
     darcy = 1e-6 * float(np.float32(1e-2)) / 0.1
     bulk = u[:, 0].reshape(p.shape)[20:-20]
-    assert np.abs(bulk / darcy - 1).max() < (1e-9 if storage == "fp64" else 1e-4)
+    assert np.abs(bulk / darcy - 1).max() < (2e-7 if storage == "fp64" else 1e-4)
 
 
 def test_miscible_small_parity_and_balances():
@@ -139,7 +145,7 @@ def test_precision_crop_spd_fp32():
     compare(g, o, p, "fp32")
 
 
-@pytest.mark.parametrize("storage,bound", [("fp16", 1e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("storage,bound", [("fp16", 2e-3), ("bf16", 2e-2)])
 def test_reduced_precision_storage_error(storage, bound):
     """FP16 / BF16 deviation storage on the rotated-tensor crop: error of u
     against the FP64 oracle, relative to max|u|, and mass drift."""
@@ -176,6 +182,9 @@ def test_single_cell_and_thin_lattices():
         p = W.random_medium(*dims, seed=9, solid_frac=0.0, walls=False, inlet=False)
         g, o = run_both(p, 10, "fp64")
         compare(g, o, p, "fp64")
+        f, h = g.populations()
+        rf, rh = o.populations()
+        assert np.abs(f - rf).max() < 1e-13 and np.abs(h - rh).max() < 1e-13
 
 
 def test_torch_allocator_and_stream():
