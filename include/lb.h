@@ -104,8 +104,10 @@ typedef struct {
                            NaN/Inf (0 = never) */
 } lb_params;
 
-/* Create a lattice (flowchart of Section 4, "set the porosity field, the
- * permeability fields, the relaxation times and the boundary conditions").
+/* Create a lattice (flowchart of Section 4: the porosity field, the
+ * permeability fields, the relaxation times and the boundary conditions are
+ * set before the distributions are initialised). Sizes: nz <= 65535 and
+ * 19 * nx * ny * nz < 2^31 (LB_EUNSUPPORTED beyond).
  *   porosity  N floats, 0 < eps <= 1 in every non-solid cell (Eq. momentum).
  *   K6        N*6 floats per cell (K_xx, K_yy, K_zz, K_xy, K_yz, K_zx), a
  *             symmetric positive-definite permeability tensor (Eq. forcement);
@@ -167,8 +169,9 @@ int lb_reduce(lb_ctx *ctx, double *mass, double *solute, double *flux_in,
  * population q of cell n is pulled from, or an LB_SRC_* class. */
 int lb_debug_neighbors(lb_ctx *ctx, int32_t lattice, int32_t *src);
 
-/* Free-surface state: cell types (LB_CELL_*) and liquid mass m per cell. */
-int lb_free_surface_state(lb_ctx *ctx, uint8_t *type, float *mass);
+/* Free-surface state: cell types (LB_CELL_*) and liquid mass m per cell
+ * (in the collision precision, widened to double). */
+int lb_free_surface_state(lb_ctx *ctx, uint8_t *type, double *mass);
 
 /* Wait for the context's stream; reports LB_ENONFINITE like lb_fields. */
 int lb_sync(lb_ctx *ctx);

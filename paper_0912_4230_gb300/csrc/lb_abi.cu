@@ -28,6 +28,8 @@ struct lb_ctx {
   const StorageOps *ops = nullptr;
   cudaStream_t stream = nullptr;
   unsigned N = 0, nblk = 0;
+  dim3 sgrid, sblock;  // launch shape of the step kernel
+  unsigned nwarps = 0;
   int kmode = KM_NONE;
   bool solute = false, fs = false, has_solid = false, flux = false;
   unsigned f_wall = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
@@ -39,13 +41,15 @@ struct lb_ctx {
   void *eps = nullptr, *kinv = nullptr, *geps = nullptr, *rhohat = nullptr;
   uint32_t *link = nullptr;
   float *fields = nullptr;
-  double *partials = nullptr;
+  double *partials = nullptr;    // per-block sums of lb_reduce
+  double *flux_slots = nullptr;  // per-warp cumulative inlet / outlet flux
   DevState *state = nullptr;
   // free surface
   uint8_t *type[2] = {nullptr, nullptr};
-  float *mass[2] = {nullptr, nullptr};
-  float *lam = nullptr;
-  uint8_t *flag = nullptr;
+  void *mass[2] = {nullptr, nullptr};
+  void *lam = nullptr, *share = nullptr;
+  uint8_t *flag_a = nullptr, *flag_b = nullptr;
+  unsigned *any = nullptr;
   // reusable staging for lb_init and the FP64 population exchange
   void *stage = nullptr;
   size_t stage_bytes = 0;
@@ -163,7 +167,7 @@ void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
   }
   a.t = c->t;
   a.flux = c->flux ? 1 : 0;
-  a.partials = c->partials;
+  a.flux_slots = c->flux_slots;
   a.state = c->state;
 }
 
@@ -218,8 +222,10 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (!dom || !porosity || !solid || !prm)
     return fail(nullptr, LB_EINVAL, "domain, porosity, solid and params are required");
   const long long N64 = (long long)dom->nx * dom->ny * dom->nz;
-  if (dom->nx < 1 || dom->ny < 1 || dom->nz < 1 || N64 > 0x7fffffffLL)
-    return fail(nullptr, LB_EINVAL, "lattice size out of range");
+  if (dom->nx < 1 || dom->ny < 1 || dom->nz < 1 || dom->nz > 65535)
+    return fail(nullptr, LB_EINVAL, "lattice size out of range (nz <= 65535)");
+  if (19 * N64 > 0x7fffffffLL)
+    return fail(nullptr, LB_EUNSUPPORTED, "lattice too large: 19 N must stay below 2^31");
   if (!valid_faces(dom->bc, true) || !valid_faces(dom->sbc, false))
     return fail(nullptr, LB_EINVAL, "invalid face kinds");
   for (int a = 0; a < 3; ++a)
@@ -260,6 +266,14 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   c->alloc_user = g_alloc_user;
   c->N = unsigned(N64);
   c->nblk = (c->N + BLOCK - 1) / BLOCK;
+  {
+    // step kernel: rows of BX threads (a multiple of 32), BY rows per block
+    unsigned bx = 32;
+    while (bx < 128 && bx < unsigned(dom->nx)) bx *= 2;
+    c->sblock = dim3(bx, BLOCK / bx, 1);
+    c->sgrid = dim3((dom->nx + bx - 1) / bx, (dom->ny + c->sblock.y - 1) / c->sblock.y, dom->nz);
+    c->nwarps = c->sgrid.x * c->sgrid.y * c->sgrid.z * (BLOCK / 32);
+  }
   c->solute = prm->solute != 0;
   c->fs = prm->free_surface != 0;
   c->f_wall = face_mask(dom->bc, LB_BC_WALL);
@@ -286,8 +300,9 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   c->link = static_cast<uint32_t *>(dev_alloc(c, N * 4));
   c->fields = static_cast<float *>(dev_alloc(c, 6 * N * sizeof(float)));
   c->partials = static_cast<double *>(dev_alloc(c, size_t(c->nblk) * 4 * sizeof(double)));
+  c->flux_slots = static_cast<double *>(dev_alloc(c, size_t(c->nwarps) * 2 * sizeof(double)));
   c->state = static_cast<DevState *>(dev_alloc(c, sizeof(DevState)));
-  if (!c->eps || !c->link || !c->fields || !c->partials || !c->state)
+  if (!c->eps || !c->link || !c->fields || !c->partials || !c->flux_slots || !c->state)
     return bail(fail(c, LB_ENOMEM, "static fields"));
   if (c->solute && !(c->geps = dev_alloc(c, 3 * N * rb))) return bail(fail(c, LB_ENOMEM, "geps"));
   if ((prm->A != 0.0 || c->fs) && !(c->rhohat = dev_alloc(c, N * rb)))
@@ -295,12 +310,16 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (c->fs) {
     for (int b = 0; b < 2; ++b) {
       c->type[b] = static_cast<uint8_t *>(dev_alloc(c, N));
-      c->mass[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
+      c->mass[b] = dev_alloc(c, N * rb);
       if (!c->type[b] || !c->mass[b]) return bail(fail(c, LB_ENOMEM, "free surface"));
     }
-    c->lam = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
-    c->flag = static_cast<uint8_t *>(dev_alloc(c, N));
-    if (!c->lam || !c->flag) return bail(fail(c, LB_ENOMEM, "free surface"));
+    c->lam = dev_alloc(c, N * rb);
+    c->share = dev_alloc(c, N * rb);
+    c->flag_a = static_cast<uint8_t *>(dev_alloc(c, N));
+    c->flag_b = static_cast<uint8_t *>(dev_alloc(c, N));
+    c->any = static_cast<unsigned *>(dev_alloc(c, sizeof(unsigned)));
+    if (!c->lam || !c->share || !c->flag_a || !c->flag_b || !c->any)
+      return bail(fail(c, LB_ENOMEM, "free surface"));
   }
   // inputs -> device (caller pointers may be host or device)
   const size_t in_bytes = N * 4 + (K6 ? 6 * N * 4 : 0) + N + 64;
@@ -397,10 +416,16 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
   c->t = 0;
   c->cur = 0;
   CK(c, cudaMemsetAsync(c->state, 0, sizeof(DevState), c->stream));
-  if (c->fs) return LB_EUNSUPPORTED;  // free-surface initialisation lives in lb_free_surface.cu
-  if (c->prm.A != 0.0)
+  CK(c, cudaMemsetAsync(c->flux_slots, 0, size_t(c->nwarps) * 2 * sizeof(double), c->stream));
+  if (c->fs) {
+    CK(c, fs_init(c->N, c->link, d_type, d_rho, lambda0 ? d_lam : nullptr, c->type[0], c->type[1],
+                  c->mass[0], c->lam, c->ops->fp64, c->stream));
+    CK(c, rhohat_init(c->N, c->link, d_rho, c->mass[0], c->prm.wall_rho, c->rhohat, c->ops->fp64,
+                      c->stream));
+  } else if (c->prm.A != 0.0) {
     CK(c, rhohat_init(c->N, c->link, d_rho, nullptr, c->prm.wall_rho, c->rhohat, c->ops->fp64,
                       c->stream));
+  }
   return with_args(c, [&](void *args, auto &a) {
     using Real = std::remove_reference_t<decltype(a.G[0])>;
     a.link = c->link;  // solid cells are always skipped at init
@@ -411,7 +436,7 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
     in.u0 = d_u;
     in.C0 = C0 ? d_C : nullptr;
     in.f_scale = f_scale ? d_fs : nullptr;
-    in.type = nullptr;
+    in.type = c->fs ? c->type[0] : nullptr;
     CK(c, c->ops->init(c->kmode, c->solute, args, &in, c->nblk, c->stream));
     return int(LB_OK);
   });
@@ -424,11 +449,30 @@ int lb_step(lb_ctx *c, int64_t n) {
     c->t += 1;
     const bool last = (i == n - 1);
     const int rc = with_args(c, [&](void *args, auto &a) {
+      using Real = std::remove_reference_t<decltype(a.G[0])>;
       a.t = c->t;
       a.reduce = (c->prm.check_every > 0 && c->t % c->prm.check_every == 0) ? 1 : 0;
       a.fields = last ? c->fields : nullptr;
+      if (c->fs) {
+        FsArgs<Real> fa;
+        a.fields = c->fields;  // rho and V' of every live cell feed the re-typing
+        a.link = c->link;
+        fa.a = a;
+        fa.type_old = c->type[c->cur];
+        fa.type_new = c->type[1 - c->cur];
+        fa.m_old = static_cast<const Real *>(c->mass[c->cur]);
+        fa.m_new = static_cast<Real *>(c->mass[1 - c->cur]);
+        fa.lam = static_cast<Real *>(c->lam);
+        fa.rhohat_w = static_cast<Real *>(c->rhohat);
+        fa.flag_a = c->flag_a;
+        fa.flag_b = c->flag_b;
+        fa.share = static_cast<Real *>(c->share);
+        fa.any = c->any;
+        CK(c, c->ops->fs_step(&fa, c->nblk, c->stream));
+        return int(LB_OK);
+      }
       if (c->prm.A != 0.0) CK(c, c->ops->rhohat(args, c->rhohat, c->nblk, c->stream));
-      CK(c, c->ops->step(c->kmode, c->solute, args, c->nblk, c->stream));
+      CK(c, c->ops->step(c->kmode, c->solute, args, c->sgrid, c->sblock, c->stream));
       return int(LB_OK);
     });
     if (rc != LB_OK) return rc;
@@ -451,20 +495,22 @@ int lb_reduce(lb_ctx *c, double *mass, double *solute, double *flux_in, double *
   if (!c) return LB_EINVAL;
   double *out = static_cast<double *>(stage(c, 64));
   if (!out) return fail(c, LB_ENOMEM, "staging");
-  double tot[2] = {0.0, 0.0};
-  if (!c->fs) {
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  if (c->fs)
+    CK(c, fs_totals(c->N, c->link, c->mass[c->cur], c->partials, c->ops->fp64, c->stream));
+  else
     CK(c, c->ops->totals(c->f[c->cur], c->solute ? c->h[c->cur] : nullptr,
                          c->has_solid ? c->link : nullptr, c->N, c->partials, c->nblk, c->stream));
-    CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
-    CK(c, cudaMemcpyAsync(tot, out, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
-  }
+  CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
+  CK(c, finish_sum(c->flux_slots, c->nwarps, 2, out + 2, c->stream));
+  CK(c, cudaMemcpyAsync(tot, out, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
   DevState st;
   CK(c, cudaMemcpyAsync(&st, c->state, sizeof st, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   if (mass) *mass = tot[0];
   if (solute) *solute = tot[1];
-  if (flux_in) *flux_in = st.flux_in;
-  if (flux_out) *flux_out = st.flux_out;
+  if (flux_in) *flux_in = tot[2];
+  if (flux_out) *flux_out = tot[3];
   if (st.status & 1u) return fail(c, LB_ENONFINITE, "a step reduction met a NaN or an infinity");
   return LB_OK;
 }
@@ -520,12 +566,17 @@ int lb_debug_neighbors(lb_ctx *c, int32_t lattice, int32_t *src) {
   return LB_OK;
 }
 
-int lb_free_surface_state(lb_ctx *c, uint8_t *type, float *mass) {
+int lb_free_surface_state(lb_ctx *c, uint8_t *type, double *mass) {
   if (!c) return LB_EINVAL;
   if (!c->fs) return fail(c, LB_EINVAL, "no free surface in this context");
   const size_t N = c->N;
   if (type) CK(c, cudaMemcpyAsync(type, c->type[c->cur], N, cudaMemcpyDefault, c->stream));
-  if (mass) CK(c, cudaMemcpyAsync(mass, c->mass[c->cur], N * 4, cudaMemcpyDefault, c->stream));
+  if (mass) {
+    double *st = static_cast<double *>(stage(c, N * sizeof(double)));
+    if (!st) return fail(c, LB_ENOMEM, "staging");
+    CK(c, to_double(c->N, c->mass[c->cur], st, c->ops->fp64, c->stream));
+    CK(c, cudaMemcpyAsync(mass, st, N * sizeof(double), cudaMemcpyDefault, c->stream));
+  }
   CK(c, cudaStreamSynchronize(c->stream));
   return LB_OK;
 }

@@ -139,12 +139,10 @@ struct StoreBF16 {
 enum : int { KM_NONE = 0, KM_DIAG = 1, KM_SPD = 2 };
 enum : uint8_t { CELL_LIQUID = 0, CELL_INTERFACE = 1, CELL_EMPTY = 2 };
 
-// Device-resident per-context counters, updated by the last block of a step.
+// Device-resident per-context status word.
 struct DevState {
-  double flux_in, flux_out;   // cumulative solute fluxes
-  double mass, solute;        // totals of the last checked step
-  unsigned counter;           // blocks finished in the current launch
-  unsigned status;            // bit 0: non-finite total seen
+  unsigned status;  // bit 0: a checked step met a non-finite mass or solute sum
+  unsigned pad;
 };
 
 template <class Real>
@@ -172,13 +170,27 @@ struct StepArgs {
   int reduce;           // form mass / solute totals this step
   int flux;             // inlet/outlet faces present
   float *fields;        // NULL or 6 x N: rho, ux, uy, uz, C, nu
-  double *partials;     // gridDim.x x 4
+  double *flux_slots;   // 2 per warp of the step launch: cumulative inlet / outlet flux
   DevState *state;
-  // free surface
-  const uint8_t *type;  // N cell types at t
-  const float *mass_new;  // N liquid mass after the exchange (m(t+1))
-  float *lam_out;       // N liquid fraction written after collision
-  uint8_t *flag_out;    // N: 1 fill, 2 empty candidate, 0 none
+};
+
+// Free-surface state of one step (Section 3): cell types, liquid mass m,
+// liquid fraction lambda and the re-typing scratch.
+enum : uint8_t { CELL_NEW_INTERFACE = 3 };
+enum : uint8_t { FS_NONE = 0, FS_FILL = 1, FS_EMPTYING = 2 };
+
+template <class Real>
+struct FsArgs {
+  StepArgs<Real> a;      // fields must be set: rho and V' of every live cell
+  const uint8_t *type_old;
+  uint8_t *type_new;
+  const Real *m_old;
+  Real *m_new;
+  Real *lam;             // lambda(t) in, lambda(t+1) out
+  Real *rhohat_w;        // colour-gradient field written by the mass exchange
+  uint8_t *flag_a, *flag_b;
+  Real *share;           // excess mass handed to each interface neighbour
+  unsigned *any;         // nonzero when some cell fills or empties this step
 };
 
 }  // namespace lbgb

@@ -1,0 +1,357 @@
+// Free-surface kernels (Section 3 of the paper): liquid-mass exchange,
+// stream/collide of liquid and interface cells with the reconstruction of
+// populations coming from empty cells, and the re-typing of cells whose
+// liquid fraction leaves [0, 1]. One step is six dense launches over the
+// lattice; the re-typing passes return at once unless some cell flagged a
+// conversion in this step.
+#pragma once
+
+#include "lb_kernels.cuh"
+
+namespace lbgb {
+
+// the neighbour x + c_q, or -1 when the step leaves through a wall face or
+// lands on a solid cell (bit opp(q) of the link word is the solidity of
+// x - c_opp(q) = x + c_q)
+template <int q>
+__device__ __forceinline__ long long fs_neighbor(const CellGeo &g, unsigned n, uint32_t link,
+                                                 unsigned f_wall) {
+  if (faces_ahead(q) & g.onface & f_wall) return -1;
+  if ((link >> opp(q)) & 1u) return -1;
+  return (long long)n + ahead_delta<q>(g);
+}
+
+// Density of a live cell from its populations of the step being completed
+// (the f_out buffer), in the collision type.
+template <class S>
+__device__ __forceinline__ typename S::Real cell_rho(const StepArgs<typename S::Real> &a,
+                                                     unsigned n) {
+  using Real = typename S::Real;
+  const typename S::T *f = static_cast<const typename S::T *>(a.f_out);
+  Real r = Real(0);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    r += S::template ld_f<q>(f + size_t(q) * a.N + n);
+  });
+  return Real(1) + r;
+}
+
+// Flowchart step g, Eqs. eq:massmacro, eq:massevol, eq:deltamass:
+// m(x, t+1) = m(x, t) + sum_q w (f~_opp(q)(x + c_q) - f~_q(x)), with w = 1 when
+// either cell is liquid, (lambda(x) + lambda(x + c_q))/2 between two
+// interface cells, and no exchange with empty or solid cells. The colour
+// gradient field is the new liquid mass (0 in empty, wall_rho in solid cells).
+template <class S>
+__global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S::Real> s) {
+  using Real = typename S::Real;
+  using T = typename S::T;
+  const StepArgs<Real> &a = s.a;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s.any = 0u;
+  if (n >= a.N) return;
+  const uint32_t link = a.link ? __ldg(a.link + n) : 0u;
+  if (link >> 31) {
+    s.m_new[n] = Real(0);
+    s.rhohat_w[n] = a.wall_rho;
+    return;
+  }
+  const uint8_t t = s.type_old[n];
+  if (t == CELL_EMPTY) {
+    s.m_new[n] = s.m_old[n];
+    s.rhohat_w[n] = Real(0);
+    return;
+  }
+  const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+  const T *fin = static_cast<const T *>(a.f_in);
+  const unsigned N = a.N;
+  const Real lx = s.lam[n];
+  Real m = s.m_old[n];
+  Unroll<1, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
+    if (y < 0) return;
+    const uint8_t ty = s.type_old[y];
+    if (ty == CELL_EMPTY) return;
+    // the equilibrium weights of q and opp(q) are equal, so deviations subtract
+    const Real diff = S::template ld_f<opp(q)>(fin + size_t(opp(q)) * N + y) -
+                      S::template ld_f<q>(fin + size_t(q) * N + n);
+    const Real w = (t == CELL_INTERFACE && ty == CELL_INTERFACE)
+                       ? Real(0.5) * (lx + s.lam[y])
+                       : Real(1);
+    m += w * diff;
+  });
+  s.m_new[n] = m;
+  s.rhohat_w[n] = m;
+}
+
+// Flowchart steps f, h, e, i for liquid and interface cells: pull-stream with
+// bounce-back and, for populations that would come from an empty cell, Eq.
+// equilempty: f_q = f^eq_q + f^eq_opp(q) - f~_opp(q)(x) at gas density 1 and
+// the cell's own V' (recovered from its post-collision populations; exact
+// without Darcy drag); moments, colour gradient, BGK collision with forcing
+// and surface tension; then lambda = m / rho and the fill/empty flags.
+template <class S>
+__global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S::Real> s) {
+  using Real = typename S::Real;
+  using T = typename S::T;
+  const StepArgs<Real> &a = s.a;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned N = a.N;
+  if (n >= N) return;
+  const uint32_t link = a.link ? __ldg(a.link + n) : 0u;
+  const uint8_t t = s.type_old[n];
+  if ((link >> 31) || t == CELL_EMPTY) {
+    s.flag_a[n] = FS_NONE;
+    return;
+  }
+  const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+  const T *__restrict__ fin = static_cast<const T *>(a.f_in);
+  T *__restrict__ fout = static_cast<T *>(a.f_out);
+  const Real eps = __ldg(a.eps + n);
+
+  // sources that are empty cells
+  unsigned from_gas = 0;
+  Unroll<1, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    if (fluid_class<q>(g, link, a.f_wall) == PULL_CELL &&
+        s.type_old[(long long)n + src_delta<q>(g)] == CELL_EMPTY)
+      from_gas |= 1u << q;
+  });
+  Real ge[Q];  // f^eq_q - w_q at gas density 1 and the cell's own V' (time t)
+  if (from_gas) {
+    Real r = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real v = S::template ld_f<q>(fin + size_t(q) * N + n);
+      r += v;
+      if (cx(q)) j0 += Real(cx(q)) * v;
+      if (cy(q)) j1 += Real(cy(q)) * v;
+      if (cz(q)) j2 += Real(cz(q)) * v;
+    });
+    const Real ir = Real(1) / (Real(1) + r);
+    const Real u0 = j0 * ir - Real(0.5) * eps * a.G[0];
+    const Real u1 = j1 * ir - Real(0.5) * eps * a.G[1];
+    const Real u2 = j2 * ir - Real(0.5) * eps * a.G[2];
+    const Real ie = Real(1) / eps, uu = u0 * u0 + u1 * u1 + u2 * u2;
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cu = Real(cx(q)) * u0 + Real(cy(q)) * u1 + Real(cz(q)) * u2;
+      ge[q] = wq<Real>(q) * (Real(3) * cu + Real(4.5) * ie * cu * cu - Real(1.5) * ie * uu);
+    });
+  }
+  Real d[Q];
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int cls = fluid_class<q>(g, link, a.f_wall);
+    if (cls == PULL_BOUNCE) {
+      d[q] = S::template ld_f<opp(q)>(fin + size_t(opp(q)) * N + n);
+    } else if ((from_gas >> q) & 1u) {
+      d[q] = ge[q] + ge[opp(q)] - S::template ld_f<opp(q)>(fin + size_t(opp(q)) * N + n);
+    } else {
+      d[q] = S::template ld_f<q>(fin + size_t(q) * N + (long long)n + src_delta<q>(g));
+    }
+  });
+  Real drho = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    drho += d[q];
+    if (cx(q)) j0 += Real(cx(q)) * d[q];
+    if (cy(q)) j1 += Real(cy(q)) * d[q];
+    if (cz(q)) j2 += Real(cz(q)) * d[q];
+  });
+  const Real rho = Real(1) + drho;
+  const Real irho = Real(1) / rho;
+  const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
+  const Real tau = a.tau;
+  const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
+  FluidCollide<Real> fc;
+  fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
+  if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
+  velocity_solve<KM_NONE>(a.kinv, N, n, eps, nu, V, a.G, fc.Vp, fc.Fe);
+  fc.drho = drho;
+  fc.rho = rho;
+  fc.ie = Real(1) / eps;
+  fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
+  fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
+  fc.itau = Real(1) / tau;
+  fc.omt = Real(1) - fc.itau;
+  fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
+  fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
+  fc.st = (a.A != Real(0)) && fc.Fn > st_threshold<Real>();
+  fc.stc = fc.st ? a.A * eps * tau : Real(0);
+  fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    S::template st_f<q>(fout + size_t(q) * N + n, fc.template post<q>(d[q]));
+  });
+  write_fields(a.fields, N, n, rho, fc.Vp, Real(0), nu);
+  // flowchart step j, candidates: lambda > 1 + 1e-3 fills, lambda < -1e-3 empties
+  uint8_t flag = FS_NONE;
+  if (t == CELL_INTERFACE) {
+    const Real lam = s.m_new[n] / rho;
+    if (lam > Real(1.001))
+      flag = FS_FILL;
+    else if (lam < Real(-0.001))
+      flag = FS_EMPTYING;
+  }
+  s.flag_a[n] = flag;
+  if (flag) atomicOr(s.any, 1u);
+}
+
+// An emptying cell next to a filling cell stays an interface cell.
+template <class Real>
+__global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) {
+  const StepArgs<Real> &a = s.a;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  if (n >= a.N || *s.any == 0u) return;
+  uint8_t f = s.flag_a[n];
+  if (f == FS_EMPTYING) {
+    const uint32_t link = a.link ? a.link[n] : 0u;
+    const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+    bool near_fill = false;
+    Unroll<1, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
+      if (y >= 0 && s.flag_a[y] == FS_FILL) near_fill = true;
+    });
+    if (near_fill) f = FS_NONE;
+  }
+  s.flag_b[n] = f;
+}
+
+// New cell types: filled -> liquid, emptied -> empty, empty next to a filled
+// cell -> new interface, liquid next to an emptied cell -> interface.
+template <class Real>
+__global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) {
+  const StepArgs<Real> &a = s.a;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  if (n >= a.N) return;
+  uint8_t t = s.type_old[n];
+  const uint32_t link = a.link ? a.link[n] : 0u;
+  if (*s.any != 0u && !(link >> 31)) {
+    const uint8_t f = s.flag_b[n];
+    if (f == FS_FILL) {
+      t = CELL_LIQUID;
+    } else if (f == FS_EMPTYING) {
+      t = CELL_EMPTY;
+    } else if (t == CELL_EMPTY || t == CELL_LIQUID) {
+      const uint8_t look = (t == CELL_EMPTY) ? FS_FILL : FS_EMPTYING;
+      const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+      bool hit = false;
+      Unroll<1, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
+        if (y >= 0 && s.flag_b[y] == look) hit = true;
+      });
+      if (hit) t = (t == CELL_EMPTY) ? CELL_NEW_INTERFACE : CELL_INTERFACE;
+    }
+  }
+  s.type_new[n] = t;
+}
+
+// New interface cells take f = f^eq(mean rho, mean V') of their liquid and
+// interface neighbours (hydrodynamic equilibrium, no mass); filled and
+// emptied cells hand their excess mass (m - rho, or m) in equal shares to the
+// neighbours that are interface cells after the re-typing.
+template <class S>
+__global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename S::Real> s) {
+  using Real = typename S::Real;
+  using T = typename S::T;
+  const StepArgs<Real> &a = s.a;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned N = a.N;
+  if (n >= N || *s.any == 0u) return;
+  const uint8_t tn = s.type_new[n];
+  const uint8_t f = s.flag_b[n];
+  if (tn != CELL_NEW_INTERFACE && f == FS_NONE) return;
+  const uint32_t link = a.link ? a.link[n] : 0u;
+  const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+  const float *fl = a.fields;
+  if (tn == CELL_NEW_INTERFACE) {
+    Real rs = Real(0), u0 = Real(0), u1 = Real(0), u2 = Real(0);
+    int cnt = 0;
+    Unroll<1, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
+      if (y < 0) return;
+      const uint8_t ty = s.type_new[y];
+      if (ty != CELL_LIQUID && ty != CELL_INTERFACE) return;
+      rs += Real(fl[y]);
+      u0 += Real(fl[size_t(N) + 3 * size_t(y)]);
+      u1 += Real(fl[size_t(N) + 3 * size_t(y) + 1]);
+      u2 += Real(fl[size_t(N) + 3 * size_t(y) + 2]);
+      ++cnt;
+    });
+    const Real ic = Real(1) / Real(cnt > 0 ? cnt : 1);
+    const Real r = cnt > 0 ? rs * ic : Real(1);
+    const Real u[3] = {u0 * ic, u1 * ic, u2 * ic};
+    const Real eps = a.eps[n];
+    const Real ie = Real(1) / eps, uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T *fout = static_cast<T *>(a.f_out);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cu = Real(cx(q)) * u[0] + Real(cy(q)) * u[1] + Real(cz(q)) * u[2];
+      const Real dev = wq<Real>(q) * ((r - Real(1)) +
+                                      r * (Real(3) * cu + Real(4.5) * ie * cu * cu -
+                                           Real(1.5) * ie * uu));
+      S::template st_f<q>(fout + size_t(q) * N + n, dev);
+    });
+    write_fields(a.fields, N, n, r, u, Real(0), (a.tau - Real(0.5)) / Real(3));
+  }
+  if (f != FS_NONE) {
+    int cnt = 0;
+    Unroll<1, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
+      if (y < 0) return;
+      const uint8_t ty = s.type_new[y];
+      if (ty == CELL_INTERFACE || ty == CELL_NEW_INTERFACE) ++cnt;
+    });
+    // a filled cell keeps m = rho: its post-collision density, recomputed in
+    // the collision type (the exported field is float)
+    Real share = Real(0);
+    if (cnt > 0) {
+      const Real m = s.m_new[n];
+      const Real excess = (f == FS_FILL) ? m - cell_rho<S>(a, n) : m;
+      share = excess / Real(cnt);
+      s.m_new[n] = m - excess;
+    }
+    s.share[n] = share;
+  }
+}
+
+// Excess mass arrives at interface cells; types settle; lambda = m / rho.
+template <class S>
+__global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename S::Real> s) {
+  using Real = typename S::Real;
+  const StepArgs<Real> &a = s.a;
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned N = a.N;
+  if (n >= N) return;
+  const uint32_t link = a.link ? a.link[n] : 0u;
+  if (link >> 31) {
+    s.lam[n] = Real(0);
+    return;
+  }
+  uint8_t tn = s.type_new[n];
+  Real m = s.m_new[n];
+  if (*s.any != 0u) {
+    if (tn == CELL_INTERFACE || tn == CELL_NEW_INTERFACE) {
+      const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+      Unroll<1, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
+        if (y >= 0 && s.flag_b[y] != FS_NONE) m += s.share[y];
+      });
+      s.m_new[n] = m;
+    }
+    if (tn == CELL_NEW_INTERFACE) {
+      tn = CELL_INTERFACE;
+      s.type_new[n] = tn;
+    }
+    if (tn == CELL_EMPTY && s.flag_b[n] == FS_EMPTYING) zero_fields(a.fields, N, n);
+  }
+  s.lam[n] = tn == CELL_LIQUID ? Real(1) : (tn == CELL_EMPTY ? Real(0) : m / cell_rho<S>(a, n));
+}
+
+}  // namespace lbgb

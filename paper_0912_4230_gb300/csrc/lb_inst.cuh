@@ -2,6 +2,7 @@
 // one small translation unit per format (lb_inst_*.cu).
 #pragma once
 
+#include "lb_free_surface.cuh"
 #include "lb_kernels.cuh"
 #include "lb_ops.h"
 
@@ -13,19 +14,20 @@ struct Instance {
   using A = StepArgs<Real>;
 
   template <int KM, bool SOL>
-  static cudaError_t step_t(const A &a, unsigned nblk, cudaStream_t s) {
-    step_kernel<S, KM, SOL><<<nblk, BLOCK, 0, s>>>(a);
+  static cudaError_t step_t(const A &a, dim3 grid, dim3 block, cudaStream_t s) {
+    step_kernel<S, KM, SOL><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
   }
-  static cudaError_t step(int kmode, bool solute, const void *args, unsigned nblk, cudaStream_t s) {
+  static cudaError_t step(int kmode, bool solute, const void *args, dim3 grid, dim3 block,
+                          cudaStream_t s) {
     const A &a = *static_cast<const A *>(args);
     switch (kmode * 2 + (solute ? 1 : 0)) {
-      case 0: return step_t<KM_NONE, false>(a, nblk, s);
-      case 1: return step_t<KM_NONE, true>(a, nblk, s);
-      case 2: return step_t<KM_DIAG, false>(a, nblk, s);
-      case 3: return step_t<KM_DIAG, true>(a, nblk, s);
-      case 4: return step_t<KM_SPD, false>(a, nblk, s);
-      default: return step_t<KM_SPD, true>(a, nblk, s);
+      case 0: return step_t<KM_NONE, false>(a, grid, block, s);
+      case 1: return step_t<KM_NONE, true>(a, grid, block, s);
+      case 2: return step_t<KM_DIAG, false>(a, grid, block, s);
+      case 3: return step_t<KM_DIAG, true>(a, grid, block, s);
+      case 4: return step_t<KM_SPD, false>(a, grid, block, s);
+      default: return step_t<KM_SPD, true>(a, grid, block, s);
     }
   }
   template <int KM, bool SOL>
@@ -63,6 +65,16 @@ struct Instance {
                                              partials);
     return cudaGetLastError();
   }
+  static cudaError_t fs_step(const void *args, unsigned nblk, cudaStream_t s) {
+    const FsArgs<Real> &f = *static_cast<const FsArgs<Real> *>(args);
+    fs_mass_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
+    fs_step_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
+    fs_cancel_kernel<Real><<<nblk, BLOCK, 0, s>>>(f);
+    fs_retype_kernel<Real><<<nblk, BLOCK, 0, s>>>(f);
+    fs_newcell_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
+    fs_finish_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
+    return cudaGetLastError();
+  }
   static StorageOps make() {
     StorageOps o{};
     o.storage = S::id;
@@ -74,9 +86,7 @@ struct Instance {
     o.to_f64 = &to_f64;
     o.from_f64 = &from_f64;
     o.totals = &totals;
-    o.fs_mass = nullptr;
-    o.fs_step = nullptr;
-    o.fs_newcells = nullptr;
+    o.fs_step = (S::id == StoreF32::id || S::id == StoreF64::id) ? &fs_step : nullptr;
     return o;
   }
 };

@@ -236,6 +236,15 @@ __device__ __forceinline__ void write_fields(float *fl, unsigned N, unsigned n, 
   fl[5 * size_t(N) + n] = float(nu);
 }
 
+__device__ __forceinline__ void zero_fields(float *fl, unsigned N, unsigned n) {
+  fl[n] = 0.0f;
+  fl[size_t(N) + 3 * size_t(n)] = 0.0f;
+  fl[size_t(N) + 3 * size_t(n) + 1] = 0.0f;
+  fl[size_t(N) + 3 * size_t(n) + 2] = 0.0f;
+  fl[4 * size_t(N) + n] = 0.0f;
+  fl[5 * size_t(N) + n] = 0.0f;
+}
+
 template <class Real>
 __device__ __forceinline__ Real st_threshold();
 template <>
@@ -243,80 +252,90 @@ __device__ __forceinline__ float st_threshold<float>() { return 1e-20f; }
 template <>
 __device__ __forceinline__ double st_threshold<double>() { return 1e-30; }
 
-// Last block of a launch adds the per-block partial sums in a fixed order.
+// Reciprocal in the collision type: one correctly rounded reciprocal
+// instruction sequence in FP32, exact division in FP64.
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// Per-warp FP64 reductions of a step. Solute fluxes through inlet/outlet
+// faces are accumulated into one FP64 slot pair per warp of the launch
+// (each warp owns its slots across steps, so the running sums are
+// deterministic; lb_reduce adds the slots in a fixed order). On checked
+// steps the warp's mass and solute sums are tested for NaN/Inf.
 template <class Real>
-__device__ void reduce_and_finish(const StepArgs<Real> &a, const Real (&v)[4]) {
-  __shared__ double sh_w[BLOCK / 32][4];
-  __shared__ double sh_r[BLOCK][4];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const Real s = warp_sum(v[k]);
-    if (lane == 0) sh_w[warp][k] = double(s);
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double s = 0.0;
-    for (int w = 0; w < BLOCK / 32; ++w) s += sh_w[w][threadIdx.x];
-    a.partials[size_t(blockIdx.x) * 4 + threadIdx.x] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&a.state->counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += BLOCK)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] += __ldcg(a.partials + size_t(b) * 4 + k);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) sh_r[threadIdx.x][k] = acc[k];
-  __syncthreads();
-  for (int s = BLOCK / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) sh_r[threadIdx.x][k] += sh_r[threadIdx.x + s][k];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    DevState *st = a.state;
-    st->flux_in += sh_r[0][0];
-    st->flux_out += sh_r[0][1];
-    if (a.reduce) {
-      st->mass = sh_r[0][2];
-      st->solute = sh_r[0][3];
-      if (!isfinite(sh_r[0][2]) || !isfinite(sh_r[0][3])) st->status |= 1u;
+__device__ __forceinline__ void warp_reductions(const StepArgs<Real> &a, unsigned warp_gid,
+                                                bool open_face, Real fin, Real fout, Real drho,
+                                                Real sC) {
+  const unsigned lane = threadIdx.x & 31u;
+  if (a.flux && __any_sync(0xffffffffu, open_face)) {
+    const Real si = warp_sum(fin), so = warp_sum(fout);
+    if (lane == 0) {
+      a.flux_slots[2 * size_t(warp_gid)] += double(si);
+      a.flux_slots[2 * size_t(warp_gid) + 1] += double(so);
     }
-    st->counter = 0;
+  }
+  if (a.reduce) {
+    const Real m = warp_sum(drho), c = warp_sum(sC);
+    if (lane == 0 && !(isfinite(m) && isfinite(c))) atomicOr(&a.state->status, 1u);
   }
 }
 
 // One time step for every non-solid cell: stream f (and h), moments,
 // viscosity, colour gradient, V' and the Darcy force, fluid and solute
-// collision, store; optional fields export and FP64 totals.
+// collision, store; optional fields export and FP64 reductions.
+// Launch: block (BX, BY) with BX a multiple of 32, grid (ceil(nx/BX),
+// ceil(ny/BY), nz); a warp covers 32 consecutive x of one row.
 template <class S, int KMODE, bool SOLUTE>
 __global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<typename S::Real> a) {
   using Real = typename S::Real;
   using T = typename S::T;
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
+  const unsigned z = blockIdx.z;
   const unsigned N = a.N;
-  Real red[4] = {Real(0), Real(0), Real(0), Real(0)};
+  const unsigned nx = a.nx, ny = a.ny, nz = a.nz;
+  const unsigned warp_gid =
+      ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (BLOCK / 32) +
+      ((threadIdx.y * blockDim.x + threadIdx.x) >> 5);
+  bool live = x < nx && y < ny;
+  const unsigned n = x + nx * (y + ny * z);
   uint32_t link = 0;
-  bool live = n < N;
   if (live && a.link) {
     link = __ldg(a.link + n);
     live = !(link >> 31);
   }
+  Real fin_acc = Real(0), fout_acc = Real(0), drho = Real(0), sC = Real(0);
+  bool open_face = false;
   if (live) {
-    const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
-    const T *__restrict__ fin = static_cast<const T *>(a.f_in);
-    T *__restrict__ fout = static_cast<T *>(a.f_out);
+    CellGeo g;
+    {
+      const int sy = int(nx), sz = int(nx * ny);
+      g.dxm = (x == 0) ? int(nx - 1) : -1;
+      g.dxp = (x == nx - 1) ? -int(nx - 1) : 1;
+      g.dym = (y == 0) ? int(ny - 1) * sy : -sy;
+      g.dyp = (y == ny - 1) ? -int(ny - 1) * sy : sy;
+      g.dzm = (z == 0) ? int(nz - 1) * sz : -sz;
+      g.dzp = (z == nz - 1) ? -int(nz - 1) * sz : sz;
+      g.onface = (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
+                 (y == ny - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
+    }
+    const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
+    T *__restrict__ fo = static_cast<T *>(a.f_out) + n;
     Real d[Q];
-    gather_f<S>(fin, N, n, g, link, a.f_wall, d);
-
-    Real drho = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
+    if (link == 0 && !(g.onface & a.f_wall)) {
+      // every source is a cell
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        d[q] = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
+      });
+    } else {
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const bool bb = fluid_class<q>(g, link, a.f_wall) == PULL_BOUNCE;
+        d[q] = S::template ld_f<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g)));
+      });
+    }
+    Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       drho += d[q];
@@ -325,45 +344,52 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<typename S::
       if (cz(q)) j2 += Real(cz(q)) * d[q];
     });
     const Real rho = Real(1) + drho;
-    const Real irho = Real(1) / rho;
+    const Real irho = rcp(rho);
     const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
     const Real eps = __ldg(a.eps + n);
+    const Real ie = rcp(eps);
 
     Real hh[SOLUTE ? Q : 1];
-    Real sC = Real(0), gx = Real(0), gy = Real(0), gz = Real(0);
+    Real gx = Real(0), gy = Real(0), gz = Real(0);
     if (SOLUTE) {
-      const T *__restrict__ hin = static_cast<const T *>(a.h_in);
+      const T *__restrict__ hb = static_cast<const T *>(a.h_in) + n;
       gx = __ldg(a.geps + n);
       gy = __ldg(a.geps + N + n);
       gz = __ldg(a.geps + 2 * size_t(N) + n);
-      const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
-      Real fin_acc = Real(0), fout_acc = Real(0);
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
-        Real v;
-        if (cls == PULL_CELL) {
-          v = S::template ld_h<q>(hin + size_t(q) * N + (long long)n + src_delta<q>(g));
-        } else if (cls == PULL_BOUNCE) {
-          v = S::template ld_h<opp(q)>(hin + size_t(opp(q)) * N + n);
-        } else if (cls == PULL_INLET) {
-          // entering through an inlet face: h^eq at C_in with the cell's
-          // bare streamed velocity plus D grad(eps)/eps
-          const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
-          v = wq<Real>(q) * eps * a.C_in * (Real(1) + Real(3) * cv);
-          fin_acc += v - S::template ld_h<opp(q)>(hin + size_t(opp(q)) * N + n);
-        } else {
-          // outlet: the cell's own post-collision value (zero gradient)
-          v = S::template ld_h<q>(hin + size_t(q) * N + n);
-          fout_acc += S::template ld_h<opp(q)>(hin + size_t(opp(q)) * N + n) - v;
-        }
-        hh[SOLUTE ? q : 0] = v;
-        sC += v;
-      });
-      red[0] = fin_acc;
-      red[1] = fout_acc;
+      const unsigned s_open = a.s_inlet | a.s_outlet;
+      open_face = (g.onface & s_open) != 0;
+      if (link == 0 && !(g.onface & (a.s_wall | s_open))) {
+        Unroll<0, Q>::run([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+        });
+      } else {
+        const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
+        Unroll<0, Q>::run([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
+          Real v;
+          if (cls == PULL_CELL) {
+            v = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+          } else if (cls == PULL_BOUNCE) {
+            v = S::template ld_h<opp(q)>(hb + int(opp(q) * N));
+          } else if (cls == PULL_INLET) {
+            // entering through an inlet face: h^eq at C_in with the cell's
+            // bare streamed velocity plus D grad(eps)/eps
+            const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
+            v = wq<Real>(q) * eps * a.C_in * (Real(1) + Real(3) * cv);
+            fin_acc += v - S::template ld_h<opp(q)>(hb + int(opp(q) * N));
+          } else {
+            // outlet: the cell's own post-collision value (zero gradient)
+            v = S::template ld_h<q>(hb + int(q * N));
+            fout_acc += S::template ld_h<opp(q)>(hb + int(opp(q) * N)) - v;
+          }
+          hh[SOLUTE ? q : 0] = v;
+        });
+      }
+      Unroll<0, Q>::run([&](auto qc) { sC += hh[SOLUTE ? decltype(qc)::value : 0]; });
     }
-    const Real C = sC / eps;
+    const Real C = sC * ie;
     const Real tau = tau_of(a, C);
     const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
 
@@ -373,37 +399,40 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<typename S::
     velocity_solve<KMODE>(a.kinv, N, n, eps, nu, V, a.G, fc.Vp, fc.Fe);
     fc.drho = drho;
     fc.rho = rho;
-    fc.ie = Real(1) / eps;
+    fc.ie = ie;
     fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
     fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
-    fc.itau = Real(1) / tau;
+    fc.itau = rcp(tau);
     fc.omt = Real(1) - fc.itau;
     fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
-    fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
-    fc.st = (a.A != Real(0)) && fc.Fn > st_threshold<Real>();
-    fc.stc = fc.st ? a.A * eps * tau : Real(0);
-    fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+    fc.st = false;
+    fc.Fn = fc.stc = fc.iFn = Real(0);
+    if (a.A != Real(0)) {
+      fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
+      fc.st = fc.Fn > st_threshold<Real>();
+      fc.stc = fc.st ? a.A * eps * tau : Real(0);
+      fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+    }
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
-      S::template st_f<q>(fout + size_t(q) * N + n, fc.template post<q>(d[q]));
+      S::template st_f<q>(fo + int(q * N), fc.template post<q>(d[q]));
     });
 
     if (SOLUTE) {
-      T *__restrict__ hout = static_cast<T *>(a.h_out);
+      T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
       const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
+      const Real itd = a.inv_tau_D;
       Unroll<0, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
         const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
         const Real h = hh[SOLUTE ? q : 0];
-        S::template st_h<q>(hout + size_t(q) * N + n, h + (heq - h) * a.inv_tau_D);
+        S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd);
       });
     }
     if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
-    red[2] = drho;
-    red[3] = sC;
   }
-  if (a.flux || a.reduce) reduce_and_finish(a, red);
+  warp_reductions(a, warp_gid, open_face, fin_acc, fout_acc, drho, sC);
 }
 
 // Post-stream density for the colour gradient (flowchart: stream -> moments
@@ -463,8 +492,7 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
                             Real(0));
       });
     }
-    if (a.fields)
-      for (int k = 0; k < 6; ++k) a.fields[size_t(k) * N + n] = 0.0f;
+    if (a.fields) zero_fields(a.fields, N, n);
     return;
   }
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);

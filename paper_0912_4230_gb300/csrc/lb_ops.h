@@ -13,7 +13,8 @@ struct StorageOps {
   size_t elt_bytes;  // bytes per stored population
   bool fp64;         // collision type is double (StepArgs<double>)
   // step / init / rhohat take a StepArgs<Real>* matching fp64
-  cudaError_t (*step)(int kmode, bool solute, const void *args, unsigned nblk, cudaStream_t s);
+  cudaError_t (*step)(int kmode, bool solute, const void *args, dim3 grid, dim3 block,
+                      cudaStream_t s);
   cudaError_t (*init)(int kmode, bool solute, const void *args, const void *init_args,
                       unsigned nblk, cudaStream_t s);
   cudaError_t (*rhohat)(const void *args, void *rhohat, unsigned nblk, cudaStream_t s);
@@ -21,10 +22,9 @@ struct StorageOps {
   cudaError_t (*from_f64)(const double *src, void *dst, unsigned N, int lattice, cudaStream_t s);
   cudaError_t (*totals)(const void *f, const void *h, const uint32_t *link, unsigned N,
                         double *partials, unsigned nblk, cudaStream_t s);
-  // free surface (storage-typed)
-  cudaError_t (*fs_mass)(const void *args, unsigned nblk, cudaStream_t s);
-  cudaError_t (*fs_step)(const void *args, unsigned nblk, cudaStream_t s);
-  cudaError_t (*fs_newcells)(const void *args, unsigned nblk, cudaStream_t s);
+  // one free-surface step (six launches), FsArgs<Real>*; NULL when the
+  // storage format has no free-surface build
+  cudaError_t (*fs_step)(const void *fs_args, unsigned nblk, cudaStream_t s);
 };
 
 const StorageOps &ops_f32();
@@ -53,7 +53,13 @@ cudaError_t setup_fields(const SetupArgs &a, bool fp64, cudaStream_t s);
 cudaError_t finish_sum(const double *partials, unsigned nblk, int k, double *out, cudaStream_t s);
 cudaError_t neighbors(const void *args, bool fp64, int lattice, int32_t *src, unsigned nblk,
                       cudaStream_t s);
-cudaError_t rhohat_init(unsigned N, const uint32_t *link, const float *rho0, const float *mass,
+cudaError_t fs_init(unsigned N, const uint32_t *link, const uint8_t *type_in, const float *rho0,
+                    const float *lambda0, uint8_t *type0, uint8_t *type1, void *mass, void *lam,
+                    bool fp64, cudaStream_t s);
+cudaError_t fs_totals(unsigned N, const uint32_t *link, const void *mass, double *partials,
+                      bool fp64, cudaStream_t s);
+cudaError_t to_double(unsigned N, const void *src, double *dst, bool fp64, cudaStream_t s);
+cudaError_t rhohat_init(unsigned N, const uint32_t *link, const float *rho0, const void *mass,
                         double wall_rho, void *rhohat, bool fp64, cudaStream_t s);
 
 }  // namespace lbgb

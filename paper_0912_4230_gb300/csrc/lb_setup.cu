@@ -121,7 +121,7 @@ __global__ void fields_kernel(const SetupArgs a) {
 
 template <class Real>
 __global__ void rhohat_init_k(unsigned N, const uint32_t *link, const float *rho0,
-                              const float *mass, Real wall_rho, Real *rhohat) {
+                              const Real *mass, Real wall_rho, Real *rhohat) {
   const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
   if (n >= N) return;
   if (link[n] >> 31)
@@ -166,13 +166,15 @@ cudaError_t neighbors(const void *args, bool fp64, int lattice, int32_t *src, un
   return cudaGetLastError();
 }
 
-cudaError_t rhohat_init(unsigned N, const uint32_t *link, const float *rho0, const float *mass,
+cudaError_t rhohat_init(unsigned N, const uint32_t *link, const float *rho0, const void *mass,
                         double wall_rho, void *rhohat, bool fp64, cudaStream_t s) {
   if (fp64)
-    rhohat_init_k<double><<<blocks_for(N), BLOCK, 0, s>>>(N, link, rho0, mass, wall_rho,
-                                                          static_cast<double *>(rhohat));
+    rhohat_init_k<double><<<blocks_for(N), BLOCK, 0, s>>>(
+        N, link, rho0, static_cast<const double *>(mass), wall_rho, static_cast<double *>(rhohat));
   else
-    rhohat_init_k<float><<<blocks_for(N), BLOCK, 0, s>>>(N, link, rho0, mass, float(wall_rho),
+    rhohat_init_k<float><<<blocks_for(N), BLOCK, 0, s>>>(N, link, rho0,
+                                                         static_cast<const float *>(mass),
+                                                         float(wall_rho),
                                                          static_cast<float *>(rhohat));
   return cudaGetLastError();
 }

@@ -299,7 +299,7 @@ class Lattice:
 
     def free_surface_state(self):
         t = np.zeros(self.N, np.uint8)
-        m = np.zeros(self.N, np.float32)
+        m = np.zeros(self.N, np.float64)
         lb_free_surface_state(self.ctx, t, m)
         return t, m
 

@@ -1,0 +1,85 @@
+"""Free surface on the GPU against the FP64 oracle (Section 3).
+
+Parity rule: cell types are decided by thresholds on the liquid fraction, so
+types are compared bit-exactly where both sides decide in the same precision
+(FP64 storage); the FP32 path is compared on totals (liquid mass, drop
+centroid) and must conserve the liquid mass.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0912_4230_gb300 import lb, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _centroid(m, p):
+    z = np.arange(p.N) // (p.nx * p.ny)
+    return (z * m).sum() / m.sum()
+
+
+@pytest.mark.parametrize("shape", ["square", "disc"])
+def test_thin_patch_fp64_types_bit_exact(shape):
+    p = W.thin_drop(48, R=8, A=1e-3, shape=shape)
+    g = lb.Lattice(p, storage="fp64")
+    o = O.Oracle(p)
+    for _ in range(6):
+        g.step(50)
+        o.step(50)
+        gt, gm = g.free_surface_state()
+        ot, om = o.free_surface_state()
+        assert np.array_equal(gt, ot)
+        assert np.abs(gm - om).max() < 1e-11
+    rho, u, _, _ = g.fields()
+    rr, ru, _, _ = o.fields()
+    live = ot != W.EMPTY
+    assert np.abs(u[live] - ru[live]).max() <= 1.2e-7 * np.abs(ru[live]).max() + 1e-12
+    assert np.abs(rho[live] - rr[live]).max() <= 1.2e-7
+
+
+def test_falling_drop_fp64_types_bit_exact_and_mass():
+    p = W.drop(nx=24, ny=24, nz=28, R=5.0, gap=6.0, seed=3)
+    g = lb.Lattice(p, storage="fp64")
+    o = O.Oracle(p)
+    m0 = g.reduce()[0]
+    for _ in range(5):
+        g.step(100)
+        o.step(100)
+        gt, gm = g.free_surface_state()
+        ot, om = o.free_surface_state()
+        assert np.array_equal(gt, ot)
+        assert np.abs(gm - om).max() < 1e-10
+    assert abs(g.reduce()[0] / m0 - 1) < 1e-12
+    assert g.reduce()[0] == pytest.approx(o.reduce()[0], rel=1e-12)
+
+
+def test_falling_drop_fp32_totals():
+    p = W.drop(nx=24, ny=24, nz=28, R=5.0, gap=6.0, seed=3)
+    g = lb.Lattice(p, storage="fp32")
+    o = O.Oracle(p)
+    m0 = g.reduce()[0]
+    g.step(500)
+    o.step(500)
+    _, gm = g.free_surface_state()
+    _, om = o.free_surface_state()
+    assert abs(g.reduce()[0] / m0 - 1) < 1e-5
+    assert abs(_centroid(gm, p) - _centroid(om, p)) < 0.01 * p.meta["R"]
+
+
+def test_drop_full_size_runs_and_conserves_mass():
+    """192x192x128 falling drop (R = 24, 40 cells above the wall), FP32."""
+    p = W.drop()
+    g = lb.Lattice(p, storage="fp32")
+    m0 = g.reduce()[0]
+    g.step(100)
+    t, m = g.free_surface_state()
+    assert abs(g.reduce()[0] / m0 - 1) < 1e-5
+    assert set(np.unique(t)) <= {W.LIQUID, W.INTERFACE, W.EMPTY}
+    assert (t == W.LIQUID).sum() > 0.9 * (p.cell_type == W.LIQUID).sum()
