@@ -34,6 +34,22 @@ WORKLOAD = ("miscible porous medium 128^3, D3Q19 fluid + D3Q19 solute, FP32 stor
             "FP64 reductions every step")
 PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_miscible128_traffic.json")
 
+# Other workloads timed the same way (--workload); the default line is "miscible".
+# name: (factory(rank), storage, algorithmic bytes per cell update, description)
+def _other_workloads():
+    from paper_0912_4230_gb300 import workloads as W
+    prec = "precision porous medium 256^3, full SPD K per 32^3 block, D3Q19 fluid + solute, "
+    return {
+        "precision-fp32": (lambda r: W.precision(seed=r, storage="fp32"), "fp32", 333,
+                           prec + "FP32 storage"),
+        "precision-fp16": (lambda r: W.precision(seed=r, storage="fp16"), "fp16", 181,
+                           prec + "FP16 deviation storage"),
+        "precision-bf16": (lambda r: W.precision(seed=r, storage="bf16"), "bf16", 181,
+                           prec + "BF16 deviation storage"),
+        "plain-fp64": (lambda r: W.plain_channel(), "fp64", 337,
+                       "plain Brinkman channel 16x16x64, FP64, no solute"),
+    }
+
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
@@ -202,6 +218,7 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=5)
     ap.add_argument("--e2e-inner", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="miscible")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -217,9 +234,15 @@ def main():
     barrier(ws)
     from paper_0912_4230_gb300 import lb, workloads as W
 
-    prob = W.miscible(NX, NY, NZ, seed=rank)
+    algo, workload, storage = ALGO_BYTES_PER_LUP, WORKLOAD, "fp32"
+    if args.workload == "miscible":
+        prob = W.miscible(NX, NY, NZ, seed=rank)
+    else:
+        fac, storage, algo, workload = _other_workloads()[args.workload]
+        prob = fac(rank)
+        args.no_cpu_baseline = True
     stream = torch.cuda.current_stream()
-    lat = lb.Lattice(prob, storage="fp32", check_every=1, stream=stream.cuda_stream)
+    lat = lb.Lattice(prob, storage=storage, check_every=1, stream=stream.cuda_stream)
     N = prob.N
     for _ in range(args.warmup):
         lat.step(1)
@@ -252,7 +275,7 @@ def main():
     # fields, advance, read the fields and totals back
     rho0 = torch.from_numpy(prob.rho0).pin_memory()
     u0 = torch.from_numpy(prob.u0).pin_memory()
-    C0 = torch.from_numpy(prob.C0).pin_memory()
+    C0 = torch.from_numpy(prob.C0).pin_memory() if prob.C0 is not None else None
     out = [torch.empty(n, dtype=torch.float32).pin_memory() for n in (N, 3 * N, N, N)]
     torch.cuda.synchronize()
     barrier(ws)
@@ -265,13 +288,13 @@ def main():
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
     e2e_val = ws * N * args.e2e_inner * args.e2e_iters / e2e_s / 1e6
-    h2d = 5 * N * 4
+    h2d = (5 if C0 is not None else 4) * N * 4
     d2h = 6 * N * 4 + 2 * 8 + 48
 
     peak, peak_kind = measured_peaks()
-    achieved = ALGO_BYTES_PER_LUP * N / (kern_ms * 1e-3) / 1e9
+    achieved = algo * N / (kern_ms * 1e-3) / 1e9
     traffic = None
-    if os.path.exists(PROFILE_JSON):
+    if os.path.exists(PROFILE_JSON) and args.workload == "miscible":
         pj = json.load(open(PROFILE_JSON))
         if pj.get("source_hash") == kernel_source_hash():
             traffic = pj.get("dram_bytes_per_launch")
@@ -283,15 +306,17 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": N, "lattice": [NX, NY, NZ],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)",
+                  "bf16": "f32 (bf16 storage)"}[storage], "data": "synthetic",
+        "config": {"workload": workload, "cells": N, "lattice": [prob.nx, prob.ny, prob.nz],
                    "parallelism": f"replicas{ws}",
-                   "l2": f"inputs larger than L2: {ALGO_BYTES_PER_LUP * N / 1e6:.0f} MB moved per step"},
+                   "l2": f"inputs larger than L2: {algo * N / 1e6:.0f} MB moved per step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind,
-                     "kernel": "step_kernel<StoreF32, KM_DIAG, solute>",
-                     "kernel_ms": kern_ms, "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP},
+                     "kernel": "step_kernel (one launch per step)",
+                     "kernel_ms": kern_ms, "algorithmic_bytes_per_lup": algo},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

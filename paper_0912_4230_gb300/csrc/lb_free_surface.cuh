@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   const float *fl = a.fields;
   if (tn == CELL_NEW_INTERFACE) {
+    // density and V' of each neighbour from its post-collision populations
+    // in the collision type (exact: the free surface has no Darcy drag)
+    const T *fo = static_cast<const T *>(a.f_out);
     Real rs = Real(0), u0 = Real(0), u1 = Real(0), u2 = Real(0);
     int cnt = 0;
     Unroll<1, Q>::run([&](auto qc) {
@@ -276,10 +279,20 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
       if (y < 0) return;
       const uint8_t ty = s.type_new[y];
       if (ty != CELL_LIQUID && ty != CELL_INTERFACE) return;
-      rs += Real(fl[y]);
-      u0 += Real(fl[size_t(N) + 3 * size_t(y)]);
-      u1 += Real(fl[size_t(N) + 3 * size_t(y) + 1]);
-      u2 += Real(fl[size_t(N) + 3 * size_t(y) + 2]);
+      double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+      for (int k = 0; k < Q; ++k) {
+        const double v = S::to_f(fo[size_t(k) * N + y], k) - wq<double>(k);
+        r += v;
+        j0 += cx(k) * v;
+        j1 += cy(k) * v;
+        j2 += cz(k) * v;
+      }
+      const double ry = 1.0 + r;
+      const double ey = double(a.eps[y]);
+      rs += Real(ry);
+      u0 += Real(j0 / ry - 0.5 * ey * double(a.G[0]));
+      u1 += Real(j1 / ry - 0.5 * ey * double(a.G[1]));
+      u2 += Real(j2 / ry - 0.5 * ey * double(a.G[2]));
       ++cnt;
     });
     const Real ic = Real(1) / Real(cnt > 0 ? cnt : 1);
