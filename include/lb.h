@@ -192,6 +192,29 @@ void lb_destroy(lb_ctx *ctx);
 int lb_set_allocator(void *(*alloc)(size_t bytes, void *user),
                      void (*release)(void *ptr, void *user), void *user);
 
+/* Allocation-free totals (the paper has no counterpart; this serves callers
+ * that cannot allocate device memory where they need the totals, e.g. code
+ * whose device memory is all reserved up front by a framework's pool, or a
+ * loop that must not pay the device-wide synchronisation of cudaMalloc and
+ * cudaFree). Computes the same FP64 mass and solute totals as lb_reduce, but
+ * of caller-owned device arrays and with no device allocation at all:
+ *   f        19*n_cells floats in device memory, the FP32 storage form
+ *            f_q - w_q, direction-major (f[q*n_cells + n]);
+ *   h        19*n_cells floats h_q in device memory, or NULL (solute 0);
+ *   solid    n_cells bytes in device memory, nonzero = skipped, or NULL;
+ *   out      2 doubles (mass, solute), host or device memory;
+ *   stream   cudaStream_t the work is enqueued on; the call waits for it.
+ * The per-block partial sums live in one fixed array of the library image,
+ * (2 * 65536 + 2) doubles on every GPU that loads the library, held until
+ * the process exits; so n_cells must be <= 16777216 (LB_EINVAL beyond).
+ * The first call on each device looks up that array's device address (a
+ * runtime call), so make that first call before any stream capture. All
+ * calls on a device share the array: calls that overlap on the GPU race.
+ * Returns LB_OK, LB_EINVAL or LB_ECUDA (no context: lb_last_error does not
+ * report its messages). */
+int lb_totals_noalloc(const float *f, const float *h, const uint8_t *solid, int64_t n_cells,
+                      double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ STORE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_get_populations",
            "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
-           "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator"]
+           "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
+           "lb_totals_noalloc"]
 
 
 class LbError(RuntimeError):
@@ -84,6 +85,7 @@ def load() -> ctypes.CDLL:
     FREE = ctypes.CFUNCTYPE(None, vp, vp)
     L.lb_set_allocator.argtypes = [ALLOC, FREE, vp]
     L._ALLOC, L._FREE = ALLOC, FREE
+    L.lb_totals_noalloc.argtypes = [vp, vp, vp, c_int64, vp, vp]
     _lib = L
     return L
 
@@ -166,6 +168,15 @@ def lb_last_error(ctx=None) -> str:
 
 def lb_destroy(ctx):
     load().lb_destroy(ctx)
+
+
+def lb_totals_noalloc(f, h, solid, n_cells: int, out, stream_handle: int = 0):
+    """FP64 (mass, solute) of caller-owned device arrays without any device
+    allocation (see include/lb.h); out receives 2 doubles."""
+    rc = load().lb_totals_noalloc(_ptr(f), _ptr(h), _ptr(solid), int(n_cells), _ptr(out),
+                                  c_void_p(stream_handle))
+    if rc != LB_OK:
+        raise LbError(rc, "lb_totals_noalloc failed")
 
 
 _allocator_refs = None
