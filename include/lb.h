@@ -102,6 +102,11 @@ typedef struct {
   int32_t check_every;  /* every this many steps the step kernel also forms the
                            FP64 mass and solute totals and checks them for
                            NaN/Inf (0 = never) */
+  int32_t kernel;       /* step kernel: 0 automatic, 1 one thread per cell with
+                           direct loads, 2 row-pipelined with shared-memory staging
+                           (needs nx a multiple of 32, nx <= 256, FP32/FP16/BF16
+                           storage, no free surface; else LB_EUNSUPPORTED). Both
+                           compute the same arithmetic. */
 } lb_params;
 
 /* Create a lattice (flowchart of Section 4: the porosity field, the

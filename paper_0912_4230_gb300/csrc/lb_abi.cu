@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/lb.h): context management,
 // validation, device memory, and the per-step launch sequence.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,8 +29,11 @@ struct lb_ctx {
   const StorageOps *ops = nullptr;
   cudaStream_t stream = nullptr;
   unsigned N = 0, nblk = 0;
-  dim3 sgrid, sblock;  // launch shape of the step kernel
-  unsigned nwarps = 0;
+  dim3 sgrid, sblock;  // launch shape of the per-cell step kernel
+  unsigned nwarps = 0;   // flux slots (one per warp of the step launch)
+  bool use_tma = false;  // row-pipelined step kernel
+  unsigned tma_grid = 0, tma_threads = 0;
+  size_t tma_smem = 0;
   int kmode = KM_NONE;
   bool solute = false, fs = false, has_solid = false, flux = false;
   unsigned f_wall = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
@@ -188,6 +192,7 @@ int check_status(lb_ctx *c) {
   DevState st;
   CK(c, cudaMemcpyAsync(&st, c->state, sizeof st, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  if (st.status & 2u) return fail(c, LB_ETIMEOUT, "a bounded wait of the step kernel gave up");
   if (st.status & 1u) return fail(c, LB_ENONFINITE, "a step reduction met a NaN or an infinity");
   return LB_OK;
 }
@@ -245,6 +250,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (prm->free_surface && (prm->solute || K6))
     return fail(nullptr, LB_EUNSUPPORTED, "free surface with solute or permeability");
   if (prm->check_every < 0) return fail(nullptr, LB_EINVAL, "check_every < 0");
+  if (prm->kernel < 0 || prm->kernel > 2) return fail(nullptr, LB_EINVAL, "kernel");
   const StorageOps *ops = nullptr;
   switch (prm->storage) {
     case LB_STORE_FP32: ops = &ops_f32(); break;
@@ -300,9 +306,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   c->link = static_cast<uint32_t *>(dev_alloc(c, N * 4));
   c->fields = static_cast<float *>(dev_alloc(c, 6 * N * sizeof(float)));
   c->partials = static_cast<double *>(dev_alloc(c, size_t(c->nblk) * 4 * sizeof(double)));
-  c->flux_slots = static_cast<double *>(dev_alloc(c, size_t(c->nwarps) * 2 * sizeof(double)));
   c->state = static_cast<DevState *>(dev_alloc(c, sizeof(DevState)));
-  if (!c->eps || !c->link || !c->fields || !c->partials || !c->flux_slots || !c->state)
+  if (!c->eps || !c->link || !c->fields || !c->partials || !c->state)
     return bail(fail(c, LB_ENOMEM, "static fields"));
   if (c->solute && !(c->geps = dev_alloc(c, 3 * N * rb))) return bail(fail(c, LB_ENOMEM, "geps"));
   if ((prm->A != 0.0 || c->fs) && !(c->rhohat = dev_alloc(c, N * rb)))
@@ -363,6 +368,24 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   c->kmode = !K6 ? KM_NONE : ((hflags & 4u) ? KM_SPD : KM_DIAG);
   if (K6 && !(c->kinv = dev_alloc(c, (c->kmode == KM_SPD ? 6 : 3) * N * rb)))
     return bail(fail(c, LB_ENOMEM, "K inverse"));
+  // row-pipelined kernel: eligible shapes only; grid = resident blocks of all SMs
+  if (prm->kernel != 1 && !c->fs && ops->tma_config) {
+    int bps = 0, sms = 0, dev = 0;
+    if (ops->tma_config(c->kmode, c->solute, unsigned(dom->nx), &c->tma_smem, &c->tma_threads,
+                        &bps) &&
+        cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+      const unsigned rows = unsigned(dom->ny) * unsigned(dom->nz);
+      c->tma_grid = std::min(rows, unsigned(bps) * unsigned(sms));
+      c->use_tma = true;
+      c->nwarps = std::max(c->nwarps, c->tma_grid * unsigned(dom->nx / 32));
+    }
+    cudaGetLastError();
+  }
+  if (prm->kernel == 2 && !c->use_tma)
+    return bail(fail(c, LB_EUNSUPPORTED, "row-pipelined kernel: this lattice shape or storage"));
+  c->flux_slots = static_cast<double *>(dev_alloc(c, size_t(c->nwarps) * 2 * sizeof(double)));
+  if (!c->flux_slots) return bail(fail(c, LB_ENOMEM, "flux slots"));
   sa.eps = c->eps;
   sa.kinv = c->kinv;
   sa.geps = c->geps;
@@ -472,7 +495,11 @@ int lb_step(lb_ctx *c, int64_t n) {
         return int(LB_OK);
       }
       if (c->prm.A != 0.0) CK(c, c->ops->rhohat(args, c->rhohat, c->nblk, c->stream));
-      CK(c, c->ops->step(c->kmode, c->solute, args, c->sgrid, c->sblock, c->stream));
+      if (c->use_tma)
+        CK(c, c->ops->tma_step(c->kmode, c->solute, args, c->tma_grid, c->tma_threads, c->tma_smem,
+                               c->stream));
+      else
+        CK(c, c->ops->step(c->kmode, c->solute, args, c->sgrid, c->sblock, c->stream));
       return int(LB_OK);
     });
     if (rc != LB_OK) return rc;

@@ -65,6 +65,8 @@ struct StoreF32 {
   using T = float;
   using Real = float;
   static constexpr int id = 0;
+  template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
+  template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
   template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
   template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
@@ -79,6 +81,8 @@ struct StoreF64 {
   using T = double;
   using Real = double;
   static constexpr int id = 1;
+  template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
+  template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
   template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
   template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
@@ -93,6 +97,12 @@ struct StoreF16 {
   using T = __half;
   using Real = float;
   static constexpr int id = 2;
+  template <int q> __device__ __forceinline__ static Real cv_f(T v) {
+    return __half2float(v) * wq<float>(q);
+  }
+  template <int q> __device__ __forceinline__ static Real cv_h(T v) {
+    return __half2float(v) * wq<float>(q);
+  }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) {
     return __half2float(__ldg(p)) * wq<float>(q);
   }
@@ -115,6 +125,12 @@ struct StoreBF16 {
   using T = __nv_bfloat16;
   using Real = float;
   static constexpr int id = 3;
+  template <int q> __device__ __forceinline__ static Real cv_f(T v) {
+    return __bfloat162float(v) * wq<float>(q);
+  }
+  template <int q> __device__ __forceinline__ static Real cv_h(T v) {
+    return __bfloat162float(v) * wq<float>(q);
+  }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) {
     return __bfloat162float(__ldg(p)) * wq<float>(q);
   }
@@ -141,7 +157,8 @@ enum : uint8_t { CELL_LIQUID = 0, CELL_INTERFACE = 1, CELL_EMPTY = 2 };
 
 // Device-resident per-context status word.
 struct DevState {
-  unsigned status;  // bit 0: a checked step met a non-finite mass or solute sum
+  unsigned status;  // bit 0: a checked step met a non-finite mass or solute sum;
+                    // bit 1: a bounded wait of the row-pipelined kernel gave up
   unsigned pad;
 };
 

@@ -4,6 +4,7 @@
 
 #include "lb_free_surface.cuh"
 #include "lb_kernels.cuh"
+#include "lb_tma.cuh"
 #include "lb_ops.h"
 
 namespace lbgb {
@@ -75,6 +76,61 @@ struct Instance {
     fs_finish_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
     return cudaGetLastError();
   }
+  // The row-pipelined kernel is built for the coupled lattice (solute on),
+  // diagonal or full K, rows of 128 or 256 cells.
+  template <int KM, int NW>
+  static constexpr auto tma_kernel() {
+    return &tma_step_kernel<S, KM, true, NW, (NW == 4 ? 3 : 2)>;
+  }
+  template <int KM, int NW>
+  static bool tma_config_t(unsigned nx, size_t *smem, unsigned *threads, int *bps) {
+    const size_t bytes = TmaLayout<S, KM, true>::smem_bytes(nx);
+    int dev = 0, maxopt = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+    if (bytes > size_t(maxopt)) return false;
+    if (cudaFuncSetAttribute(tma_kernel<KM, NW>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(bytes)) != cudaSuccess)
+      return false;
+    const unsigned thr = (NW + 1) * 32;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma_kernel<KM, NW>(), int(thr), bytes) !=
+            cudaSuccess ||
+        nb < 1)
+      return false;
+    *smem = bytes;
+    *threads = thr;
+    *bps = nb;
+    return true;
+  }
+  static bool tma_config(int kmode, bool solute, unsigned nx, size_t *smem, unsigned *threads,
+                         int *bps) {
+    if (!solute || kmode == KM_NONE || (nx != 128 && nx != 256)) return false;
+    if (kmode == KM_DIAG)
+      return nx == 128 ? tma_config_t<KM_DIAG, 4>(nx, smem, threads, bps)
+                       : tma_config_t<KM_DIAG, 8>(nx, smem, threads, bps);
+    return nx == 128 ? tma_config_t<KM_SPD, 4>(nx, smem, threads, bps)
+                     : tma_config_t<KM_SPD, 8>(nx, smem, threads, bps);
+  }
+  static cudaError_t tma_step(int kmode, bool solute, const void *args, unsigned grid,
+                              unsigned threads, size_t smem, cudaStream_t s) {
+    const A &a = *static_cast<const A *>(args);
+    if (!solute || kmode == KM_NONE) return cudaErrorInvalidValue;
+    const bool wide = threads == 9 * 32;
+    if (kmode == KM_DIAG) {
+      if (wide)
+        tma_kernel<KM_DIAG, 8>()<<<grid, threads, smem, s>>>(a);
+      else
+        tma_kernel<KM_DIAG, 4>()<<<grid, threads, smem, s>>>(a);
+    } else {
+      if (wide)
+        tma_kernel<KM_SPD, 8>()<<<grid, threads, smem, s>>>(a);
+      else
+        tma_kernel<KM_SPD, 4>()<<<grid, threads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
   static StorageOps make() {
     StorageOps o{};
     o.storage = S::id;
@@ -87,6 +143,12 @@ struct Instance {
     o.from_f64 = &from_f64;
     o.totals = &totals;
     o.fs_step = (S::id == StoreF32::id || S::id == StoreF64::id) ? &fs_step : nullptr;
+    o.tma_config = nullptr;
+    o.tma_step = nullptr;
+    if constexpr (S::id != StoreF64::id) {  // static rows are staged as FP32
+      o.tma_config = &tma_config;
+      o.tma_step = &tma_step;
+    }
     return o;
   }
 };

@@ -126,6 +126,11 @@ __device__ __forceinline__ Real tau_of(const StepArgs<Real> &a, Real C) {
   return a.tau;
 }
 
+// Reciprocal in the collision type: one correctly rounded reciprocal
+// instruction sequence in FP32, exact division in FP64.
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
 // V' = Lambda^-1 (V + eps G / 2), Lambda = I + (eps nu / 2) K^-1, and
 // F^ext = -eps nu K^-1 V' + eps G (Eqs. forcement, expandV, expandVsub).
 template <int KMODE, class Real>
@@ -143,9 +148,9 @@ __device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, un
   } else if (KMODE == KM_DIAG) {
     const Real kx = __ldg(kinv + n), ky = __ldg(kinv + N + n), kz = __ldg(kinv + 2 * size_t(N) + n);
     const Real hs = Real(0.5) * en;
-    Vp[0] = r0 / (Real(1) + hs * kx);
-    Vp[1] = r1 / (Real(1) + hs * ky);
-    Vp[2] = r2 / (Real(1) + hs * kz);
+    Vp[0] = r0 * rcp(Real(1) + hs * kx);
+    Vp[1] = r1 * rcp(Real(1) + hs * ky);
+    Vp[2] = r2 * rcp(Real(1) + hs * kz);
     Fe[0] = -en * kx * Vp[0] + eps * G[0];
     Fe[1] = -en * ky * Vp[1] + eps * G[1];
     Fe[2] = -en * kz * Vp[2] + eps * G[2];
@@ -252,11 +257,6 @@ __device__ __forceinline__ float st_threshold<float>() { return 1e-20f; }
 template <>
 __device__ __forceinline__ double st_threshold<double>() { return 1e-30; }
 
-// Reciprocal in the collision type: one correctly rounded reciprocal
-// instruction sequence in FP32, exact division in FP64.
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-
 // Per-warp FP64 reductions of a step. Solute fluxes through inlet/outlet
 // faces are accumulated into one FP64 slot pair per warp of the launch
 // (each warp owns its slots across steps, so the running sums are
@@ -280,20 +280,158 @@ __device__ __forceinline__ void warp_reductions(const StepArgs<Real> &a, unsigne
   }
 }
 
-// One time step for every non-solid cell: stream f (and h), moments,
-// viscosity, colour gradient, V' and the Darcy force, fluid and solute
-// collision, store; optional fields export and FP64 reductions.
-// Launch: block (BX, BY) with BX a multiple of 32, grid (ceil(nx/BX),
-// ceil(ny/BY), nz); a warp covers 32 consecutive x of one row.
+// The per-cell update of one step from global memory: stream f (and h),
+// moments, viscosity, colour gradient, V' and the Darcy force, fluid and
+// solute collision, store; accumulates the cell's flux and totals.
 template <class S, int KMODE, bool SOLUTE>
-__global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<typename S::Real> a) {
+__device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a, unsigned x,
+                                            unsigned y, unsigned z, unsigned n, uint32_t link,
+                                            typename S::Real &fin_acc,
+                                            typename S::Real &fout_acc, typename S::Real &drho,
+                                            typename S::Real &sC, bool &open_face) {
   using Real = typename S::Real;
   using T = typename S::T;
+  const unsigned N = a.N;
+  const unsigned nx = a.nx, ny = a.ny, nz = a.nz;
+  CellGeo g;
+  {
+    const int sy = int(nx), sz = int(nx * ny);
+    g.dxm = (x == 0) ? int(nx - 1) : -1;
+    g.dxp = (x == nx - 1) ? -int(nx - 1) : 1;
+    g.dym = (y == 0) ? int(ny - 1) * sy : -sy;
+    g.dyp = (y == ny - 1) ? -int(ny - 1) * sy : sy;
+    g.dzm = (z == 0) ? int(nz - 1) * sz : -sz;
+    g.dzp = (z == nz - 1) ? -int(nz - 1) * sz : sz;
+    g.onface = (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
+               (y == ny - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
+  }
+  const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
+  T *__restrict__ fo = static_cast<T *>(a.f_out) + n;
+  Real d[Q];
+  if (link == 0 && !(g.onface & a.f_wall)) {
+    // every source is a cell
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      d[q] = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
+    });
+  } else {
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const bool bb = fluid_class<q>(g, link, a.f_wall) == PULL_BOUNCE;
+      d[q] = S::template ld_f<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g)));
+    });
+  }
+  Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    drho += d[q];
+    if (cx(q)) j0 += Real(cx(q)) * d[q];
+    if (cy(q)) j1 += Real(cy(q)) * d[q];
+    if (cz(q)) j2 += Real(cz(q)) * d[q];
+  });
+  const Real rho = Real(1) + drho;
+  const Real irho = rcp(rho);
+  const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
+  const Real eps = __ldg(a.eps + n);
+  const Real ie = rcp(eps);
+
+  Real hh[SOLUTE ? Q : 1];
+  Real gx = Real(0), gy = Real(0), gz = Real(0);
+  if (SOLUTE) {
+    const T *__restrict__ hb = static_cast<const T *>(a.h_in) + n;
+    gx = __ldg(a.geps + n);
+    gy = __ldg(a.geps + N + n);
+    gz = __ldg(a.geps + 2 * size_t(N) + n);
+    const unsigned s_open = a.s_inlet | a.s_outlet;
+    open_face = (g.onface & s_open) != 0;
+    if (link == 0 && !(g.onface & (a.s_wall | s_open))) {
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+      });
+    } else {
+      const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
+        Real v;
+        if (cls == PULL_CELL) {
+          v = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+        } else if (cls == PULL_BOUNCE) {
+          v = S::template ld_h<opp(q)>(hb + int(opp(q) * N));
+        } else if (cls == PULL_INLET) {
+          // entering through an inlet face: h^eq at C_in with the cell's
+          // bare streamed velocity plus D grad(eps)/eps
+          const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
+          v = wq<Real>(q) * eps * a.C_in * (Real(1) + Real(3) * cv);
+          fin_acc += v - S::template ld_h<opp(q)>(hb + int(opp(q) * N));
+        } else {
+          // outlet: the cell's own post-collision value (zero gradient)
+          v = S::template ld_h<q>(hb + int(q * N));
+          fout_acc += S::template ld_h<opp(q)>(hb + int(opp(q) * N)) - v;
+        }
+        hh[SOLUTE ? q : 0] = v;
+      });
+    }
+    Unroll<0, Q>::run([&](auto qc) { sC += hh[SOLUTE ? decltype(qc)::value : 0]; });
+  }
+  const Real C = sC * ie;
+  const Real tau = tau_of(a, C);
+  const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
+
+  FluidCollide<Real> fc;
+  fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
+  if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
+  velocity_solve<KMODE>(a.kinv, N, n, eps, nu, V, a.G, fc.Vp, fc.Fe);
+  fc.drho = drho;
+  fc.rho = rho;
+  fc.ie = ie;
+  fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
+  fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
+  fc.itau = rcp(tau);
+  fc.omt = Real(1) - fc.itau;
+  fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
+  fc.st = false;
+  fc.Fn = fc.stc = fc.iFn = Real(0);
+  if (a.A != Real(0)) {
+    fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
+    fc.st = fc.Fn > st_threshold<Real>();
+    fc.stc = fc.st ? a.A * eps * tau : Real(0);
+    fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+  }
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    S::template st_f<q>(fo + int(q * N), fc.template post<q>(d[q]));
+  });
+
+  if (SOLUTE) {
+    T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
+    const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
+    const Real itd = a.inv_tau_D;
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+      const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
+      const Real h = hh[SOLUTE ? q : 0];
+      S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd);
+    });
+  }
+  if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
+}
+
+// One time step for every non-solid cell (see update_cell).
+// Launch: block (BX, BY) with BX a multiple of 32, grid (ceil(nx/BX),
+// ceil(ny/BY), nz); a warp covers 32 consecutive x of one row.
+// Three resident blocks per SM (at most 85 registers a thread): measured on
+// GB300 at 128^3 this beats the unconstrained 112-register build (two blocks
+// per SM) by 1.2x, since the kernel is bound by loads in flight.
+template <class S, int KMODE, bool SOLUTE>
+__global__ void __launch_bounds__(BLOCK, 3) step_kernel(const StepArgs<typename S::Real> a) {
+  using Real = typename S::Real;
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
   const unsigned z = blockIdx.z;
-  const unsigned N = a.N;
-  const unsigned nx = a.nx, ny = a.ny, nz = a.nz;
+  const unsigned nx = a.nx, ny = a.ny;
   const unsigned warp_gid =
       ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (BLOCK / 32) +
       ((threadIdx.y * blockDim.x + threadIdx.x) >> 5);
@@ -306,132 +444,7 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<typename S::
   }
   Real fin_acc = Real(0), fout_acc = Real(0), drho = Real(0), sC = Real(0);
   bool open_face = false;
-  if (live) {
-    CellGeo g;
-    {
-      const int sy = int(nx), sz = int(nx * ny);
-      g.dxm = (x == 0) ? int(nx - 1) : -1;
-      g.dxp = (x == nx - 1) ? -int(nx - 1) : 1;
-      g.dym = (y == 0) ? int(ny - 1) * sy : -sy;
-      g.dyp = (y == ny - 1) ? -int(ny - 1) * sy : sy;
-      g.dzm = (z == 0) ? int(nz - 1) * sz : -sz;
-      g.dzp = (z == nz - 1) ? -int(nz - 1) * sz : sz;
-      g.onface = (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
-                 (y == ny - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
-    }
-    const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
-    T *__restrict__ fo = static_cast<T *>(a.f_out) + n;
-    Real d[Q];
-    if (link == 0 && !(g.onface & a.f_wall)) {
-      // every source is a cell
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        d[q] = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
-      });
-    } else {
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        const bool bb = fluid_class<q>(g, link, a.f_wall) == PULL_BOUNCE;
-        d[q] = S::template ld_f<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g)));
-      });
-    }
-    Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
-    Unroll<0, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      drho += d[q];
-      if (cx(q)) j0 += Real(cx(q)) * d[q];
-      if (cy(q)) j1 += Real(cy(q)) * d[q];
-      if (cz(q)) j2 += Real(cz(q)) * d[q];
-    });
-    const Real rho = Real(1) + drho;
-    const Real irho = rcp(rho);
-    const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
-    const Real eps = __ldg(a.eps + n);
-    const Real ie = rcp(eps);
-
-    Real hh[SOLUTE ? Q : 1];
-    Real gx = Real(0), gy = Real(0), gz = Real(0);
-    if (SOLUTE) {
-      const T *__restrict__ hb = static_cast<const T *>(a.h_in) + n;
-      gx = __ldg(a.geps + n);
-      gy = __ldg(a.geps + N + n);
-      gz = __ldg(a.geps + 2 * size_t(N) + n);
-      const unsigned s_open = a.s_inlet | a.s_outlet;
-      open_face = (g.onface & s_open) != 0;
-      if (link == 0 && !(g.onface & (a.s_wall | s_open))) {
-        Unroll<0, Q>::run([&](auto qc) {
-          constexpr int q = decltype(qc)::value;
-          hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
-        });
-      } else {
-        const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
-        Unroll<0, Q>::run([&](auto qc) {
-          constexpr int q = decltype(qc)::value;
-          const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
-          Real v;
-          if (cls == PULL_CELL) {
-            v = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
-          } else if (cls == PULL_BOUNCE) {
-            v = S::template ld_h<opp(q)>(hb + int(opp(q) * N));
-          } else if (cls == PULL_INLET) {
-            // entering through an inlet face: h^eq at C_in with the cell's
-            // bare streamed velocity plus D grad(eps)/eps
-            const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
-            v = wq<Real>(q) * eps * a.C_in * (Real(1) + Real(3) * cv);
-            fin_acc += v - S::template ld_h<opp(q)>(hb + int(opp(q) * N));
-          } else {
-            // outlet: the cell's own post-collision value (zero gradient)
-            v = S::template ld_h<q>(hb + int(q * N));
-            fout_acc += S::template ld_h<opp(q)>(hb + int(opp(q) * N)) - v;
-          }
-          hh[SOLUTE ? q : 0] = v;
-        });
-      }
-      Unroll<0, Q>::run([&](auto qc) { sC += hh[SOLUTE ? decltype(qc)::value : 0]; });
-    }
-    const Real C = sC * ie;
-    const Real tau = tau_of(a, C);
-    const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
-
-    FluidCollide<Real> fc;
-    fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
-    if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
-    velocity_solve<KMODE>(a.kinv, N, n, eps, nu, V, a.G, fc.Vp, fc.Fe);
-    fc.drho = drho;
-    fc.rho = rho;
-    fc.ie = ie;
-    fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
-    fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
-    fc.itau = rcp(tau);
-    fc.omt = Real(1) - fc.itau;
-    fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
-    fc.st = false;
-    fc.Fn = fc.stc = fc.iFn = Real(0);
-    if (a.A != Real(0)) {
-      fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
-      fc.st = fc.Fn > st_threshold<Real>();
-      fc.stc = fc.st ? a.A * eps * tau : Real(0);
-      fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
-    }
-    Unroll<0, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      S::template st_f<q>(fo + int(q * N), fc.template post<q>(d[q]));
-    });
-
-    if (SOLUTE) {
-      T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
-      const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
-      const Real itd = a.inv_tau_D;
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
-        const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
-        const Real h = hh[SOLUTE ? q : 0];
-        S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd);
-      });
-    }
-    if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
-  }
+  if (live) update_cell<S, KMODE, SOLUTE>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
   warp_reductions(a, warp_gid, open_face, fin_acc, fout_acc, drho, sC);
 }
 

@@ -25,6 +25,14 @@ struct StorageOps {
   // one free-surface step (six launches), FsArgs<Real>*; NULL when the
   // storage format has no free-surface build
   cudaError_t (*fs_step)(const void *fs_args, unsigned nblk, cudaStream_t s);
+  // row-pipelined step kernel (NULL when not built for this storage):
+  // tma_config fills the dynamic shared memory, threads per block and
+  // resident blocks per SM for a row of nx cells (returns false if it does
+  // not fit); tma_step launches it
+  bool (*tma_config)(int kmode, bool solute, unsigned nx, size_t *smem, unsigned *threads,
+                     int *blocks_per_sm);
+  cudaError_t (*tma_step)(int kmode, bool solute, const void *args, unsigned grid,
+                          unsigned threads, size_t smem, cudaStream_t s);
 };
 
 const StorageOps &ops_f32();

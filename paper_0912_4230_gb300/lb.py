@@ -49,7 +49,7 @@ class lb_params(ctypes.Structure):
                 ("G", c_double * 3), ("A", c_double), ("wall_rho", c_double),
                 ("forchheimer", c_double), ("solute", c_int32), ("tau_D", c_double),
                 ("C_in", c_double), ("free_surface", c_int32), ("storage", c_int32),
-                ("check_every", c_int32)]
+                ("check_every", c_int32), ("kernel", c_int32)]
 
 
 _lib = None
@@ -225,7 +225,10 @@ def make_domain(prob) -> lb_domain:
     return d
 
 
-def make_params(prob, storage=None, check_every=0) -> lb_params:
+KERNEL = {"auto": 0, "cell": 1, "rows": 2}
+
+
+def make_params(prob, storage=None, check_every=0, kernel="auto") -> lb_params:
     k = prob.params
     p = lb_params()
     p.tau = k.get("tau", 1.0)
@@ -244,6 +247,7 @@ def make_params(prob, storage=None, check_every=0) -> lb_params:
     p.free_surface = int(k.get("free_surface", 0))
     p.storage = STORE[storage or prob.storage]
     p.check_every = check_every
+    p.kernel = KERNEL[kernel]
     return p
 
 
@@ -254,13 +258,14 @@ def _f32(a):
 class Lattice:
     """One library context built from a workload description."""
 
-    def __init__(self, prob, storage=None, check_every=0, stream=None, init=True):
+    def __init__(self, prob, storage=None, check_every=0, stream=None, init=True,
+                 kernel="auto"):
         self.prob = prob
         self.N = prob.N
         self.solute = bool(prob.params.get("solute"))
         self.fs = bool(prob.params.get("free_surface"))
         self._dom = make_domain(prob)
-        self._prm = make_params(prob, storage, check_every)
+        self._prm = make_params(prob, storage, check_every, kernel)
         self.ctx = lb_create(self._dom, _f32(prob.eps), _f32(prob.K6),
                              np.ascontiguousarray(prob.solid, np.uint8), self._prm)
         if stream is not None:
