@@ -218,8 +218,11 @@ __global__ void __launch_bounds__(32 * (NW + 1), MINB)
   const unsigned rowb = nx * sizeof(T), frowb = nx * sizeof(float);
   for (unsigned k = 0; k < my_tiles; ++k) {
     const unsigned s = k % TMA_STAGES;
-    if (!mbar_wait(full + s, (k / TMA_STAGES) & 1u)) {
-      atomicOr(&a.state->status, 2u);
+    // every lane waits (bounded), then the warp decides together, so a wait
+    // that gives up never leaves part of a warp in the warp-wide reductions
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(full + s, (k / TMA_STAGES) & 1u));
+    if (!ok) {
+      if (lane == 0) atomicOr(&a.state->status, 2u);
       return;
     }
     const unsigned r = blockIdx.x + k * gridDim.x;
