@@ -219,6 +219,7 @@ def main():
     ap.add_argument("--e2e-inner", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="miscible")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "rows"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -242,7 +243,8 @@ def main():
         prob = fac(rank)
         args.no_cpu_baseline = True
     stream = torch.cuda.current_stream()
-    lat = lb.Lattice(prob, storage=storage, check_every=1, stream=stream.cuda_stream)
+    lat = lb.Lattice(prob, storage=storage, check_every=1, stream=stream.cuda_stream,
+                     kernel=args.kernel)
     N = prob.N
     for _ in range(args.warmup):
         lat.step(1)
