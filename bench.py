@@ -209,6 +209,46 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving workload: a Poisson stream of miscible-medium solves of sizes
+    32..160 (z-aspect up to 2) under a 120 GB HBM budget, steps scaled down so
+    that the run takes seconds; continuous batching (FP32 and FP16 storage)
+    against the plain per-lattice FP32 path (one request at a time)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0912_4230_gb300 import serve, workloads as W
+    n_req, scale = args.requests, args.steps_scale
+    stream = W.requests(n=n_req, rate=50.0, seed=5)
+    s = torch.cuda.current_stream().cuda_stream
+    res = {}
+    for name, storage, batched, maxres in (("batched_fp32", "fp32", True, None),
+                                           ("batched_fp16", "fp16", True, None),
+                                           ("per_lattice_fp32", "fp32", False, 1)):
+        reqs = serve.make_requests(stream, storage=storage, steps_scale=scale)
+        be = serve.LibraryBackend(storage, stream=s, keep_fields=False, batched=batched)
+        srv = serve.Server(be, budget_bytes=120 * 10 ** 9, chunk=args.chunk, max_resident=maxres)
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            st = srv.run(reqs)
+            torch.cuda.synchronize()
+        st["clocks"] = clk.summary()
+        res[name] = st
+    b = res["batched_fp32"]
+    line = {
+        "metric": "served-solve throughput (MLUPS) and p50/p99 latency", "value": b["mlups"],
+        "unit": "MLUPS", "n_gpus": 1, "steps": sum(r.steps for r in serve.make_requests(stream, steps_scale=scale)),
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n_req} requests, Poisson 50/s, sides 32..160, z-aspect 1..2, "
+                               f"steps U(2000, 20000) x {scale}, 120 GB admission budget, "
+                               f"chunk {args.chunk} steps"},
+        "serving": res,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,11 +260,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="miscible")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "rows"])
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--steps-scale", type=float, default=0.02)
+    ap.add_argument("--chunk", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import torch
     import __graft_entry__

@@ -102,11 +102,12 @@ typedef struct {
   int32_t check_every;  /* every this many steps the step kernel also forms the
                            FP64 mass and solute totals and checks them for
                            NaN/Inf (0 = never) */
-  int32_t kernel;       /* step kernel: 0 automatic, 1 one thread per cell with
-                           direct loads, 2 row-pipelined with shared-memory staging
-                           (needs nx a multiple of 32, nx <= 256, FP32/FP16/BF16
-                           storage, no free surface; else LB_EUNSUPPORTED). Both
-                           compute the same arithmetic. */
+  int32_t kernel;       /* step kernel: 0 automatic (= 1), 1 one thread per cell
+                           with direct loads, 2 row-pipelined with shared-memory
+                           staging by bulk asynchronous copies (needs the solute
+                           lattice, a permeability field, nx = 128 or 256,
+                           FP32/FP16/BF16 storage, no free surface; else
+                           LB_EUNSUPPORTED). Both compute the same arithmetic. */
 } lb_params;
 
 /* Create a lattice (flowchart of Section 4: the porosity field, the
@@ -154,6 +155,16 @@ int lb_get_populations(lb_ctx *ctx, double *f, double *h);
  * exchange, empty-neighbour reconstruction and cell re-typing (Section 3).
  * Enqueued asynchronously; launch errors return LB_ECUDA. */
 int lb_step(lb_ctx *ctx, int64_t n);
+
+/* Advance several lattices by the same n steps in one persistent launch per
+ * step (a work list of every lattice's cell blocks), captured in a CUDA graph
+ * when the first context's stream is not the legacy default stream. Each
+ * lattice computes exactly what lb_step(n) with the per-cell kernel computes.
+ * All contexts: same storage, same permeability mode (none / diagonal / full),
+ * same solute setting, no free surface, A = 0 (LB_EUNSUPPORTED otherwise).
+ * Work is enqueued on the first context's stream; the contexts' own streams
+ * are not used. */
+int lb_step_batch(lb_ctx *const *ctxs, int32_t n, int64_t steps);
 
 /* Macroscopic fields after the last step (or lb_init): rho, u = V' (3 per
  * cell), C and the kinematic viscosity nu = (tau - 1/2)/3. Any pointer may be

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/lb.h"
+#include "lb_batch.cuh"
 #include "lb_kernels.cuh"
 #include "lb_ops.h"
 
@@ -54,6 +55,9 @@ struct lb_ctx {
   void *lam = nullptr, *share = nullptr;
   uint8_t *flag_a = nullptr, *flag_b = nullptr;
   unsigned *any = nullptr;
+  // table of lb_step_batch calls led by this context
+  void *batch_tab = nullptr;
+  size_t batch_tab_bytes = 0;
   // reusable staging for lb_init and the FP64 population exchange
   void *stage = nullptr;
   size_t stage_bytes = 0;
@@ -369,7 +373,9 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (K6 && !(c->kinv = dev_alloc(c, (c->kmode == KM_SPD ? 6 : 3) * N * rb)))
     return bail(fail(c, LB_ENOMEM, "K inverse"));
   // row-pipelined kernel: eligible shapes only; grid = resident blocks of all SMs
-  if (prm->kernel != 1 && !c->fs && ops->tma_config) {
+  // (automatic selection keeps the per-cell kernel: on GB300 at 128^3 it is
+  // 2x faster than this row-pipelined form, which stays available on request)
+  if (prm->kernel == 2 && !c->fs && ops->tma_config) {
     int bps = 0, sms = 0, dev = 0;
     if (ops->tma_config(c->kmode, c->solute, unsigned(dom->nx), &c->tma_smem, &c->tma_threads,
                         &bps) &&
@@ -506,6 +512,110 @@ int lb_step(lb_ctx *c, int64_t n) {
     c->cur = 1 - c->cur;
   }
   return LB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <class Real>
+int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
+  lb_ctx *c0 = ctxs[0];
+  std::vector<BatchEntry<Real>> tab(n);
+  unsigned total = 0;
+  for (int i = 0; i < n; ++i) {
+    lb_ctx *c = ctxs[i];
+    BatchEntry<Real> &e = tab[i];
+    std::memset(&e, 0, sizeof e);
+    fill_args(c, e.a);
+    e.a.t = c->t + 1;
+    e.check_every = c->prm.check_every;
+    e.a.reduce = (e.check_every > 0 && e.a.t % e.check_every == 0) ? 1 : 0;
+    e.fields = c->fields;
+    e.t_final = c->t + steps;
+    e.a.fields = (e.a.t == e.t_final) ? c->fields : nullptr;
+    e.gx = c->sgrid.x;
+    e.gy = c->sgrid.y;
+    e.bx = c->sblock.x;
+    e.blk_begin = total;
+    total += c->sgrid.x * c->sgrid.y * c->sgrid.z;
+  }
+  const size_t bytes = tab.size() * sizeof(BatchEntry<Real>);
+  if (c0->batch_tab_bytes < bytes) {
+    dev_free(c0, c0->batch_tab);
+    c0->batch_tab = dev_alloc(c0, bytes);
+    c0->batch_tab_bytes = c0->batch_tab ? bytes : 0;
+    if (!c0->batch_tab) return fail(c0, LB_ENOMEM, "batch table");
+  }
+  cudaStream_t s = c0->stream;
+  CK(c0, cudaMemcpyAsync(c0->batch_tab, tab.data(), bytes, cudaMemcpyHostToDevice, s));
+  int dev = 0, sms = 0;
+  CK(c0, cudaGetDevice(&dev));
+  CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = std::min(total, unsigned(3 * sms));
+  const StorageOps *ops = c0->ops;
+  const int km = c0->kmode;
+  const bool sol = c0->solute;
+  auto one = [&]() -> cudaError_t {
+    cudaError_t e = ops->batch_step(km, sol, c0->batch_tab, unsigned(n), total, grid, s);
+    if (e == cudaSuccess) e = ops->batch_advance(c0->batch_tab, unsigned(n), s);
+    return e;
+  };
+  int64_t done = 0;
+  // a graph of G steps, replayed, when the stream can be captured
+  const int64_t G = 16;
+  if (s != nullptr && steps >= 2 * G) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(c0, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int64_t k = 0; k < G && ce == cudaSuccess; ++k) ce = one();
+    cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(c0, LB_ECUDA, std::string("batch graph capture: ") +
+                                    cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(c0, LB_ECUDA, std::string("graph: ") + cudaGetErrorString(ie));
+    for (; done + G <= steps; done += G) {
+      cudaError_t le = cudaGraphLaunch(exec, s);
+      if (le != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return fail(c0, LB_ECUDA, std::string("graph launch: ") + cudaGetErrorString(le));
+      }
+    }
+    cudaGraphExecDestroy(exec);
+  }
+  for (; done < steps; ++done) CK(c0, one());
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->t += steps;
+    if (steps % 2) ctxs[i]->cur = 1 - ctxs[i]->cur;
+  }
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_step_batch(lb_ctx *const *ctxs, int32_t n, int64_t steps) {
+  if (!ctxs || n < 1 || steps < 0) return LB_EINVAL;
+  lb_ctx *c0 = ctxs[0];
+  if (!c0) return LB_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    lb_ctx *c = ctxs[i];
+    if (!c) return fail(c0, LB_EINVAL, "NULL context in batch");
+    if (c->ops != c0->ops || c->kmode != c0->kmode || c->solute != c0->solute)
+      return fail(c0, LB_EUNSUPPORTED, "batch lattices must share storage, permeability mode and solute");
+    if (c->fs || c->prm.A != 0.0)
+      return fail(c0, LB_EUNSUPPORTED, "batch: free surface and surface tension step alone");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(c0, LB_EINVAL, "context twice in one batch");
+  }
+  if (steps == 0) return LB_OK;
+  return c0->ops->fp64 ? step_batch_t<double>(ctxs, n, steps) : step_batch_t<float>(ctxs, n, steps);
 }
 
 int lb_fields(lb_ctx *c, float *rho, float *u, float *C, float *nu) {

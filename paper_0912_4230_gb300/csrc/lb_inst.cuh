@@ -5,6 +5,7 @@
 #include "lb_free_surface.cuh"
 #include "lb_kernels.cuh"
 #include "lb_tma.cuh"
+#include "lb_batch.cuh"
 #include "lb_ops.h"
 
 namespace lbgb {
@@ -131,6 +132,23 @@ struct Instance {
     }
     return cudaGetLastError();
   }
+  static cudaError_t batch_step(int kmode, bool solute, const void *tab, unsigned nd,
+                                unsigned total, unsigned grid, cudaStream_t s) {
+    const BatchEntry<Real> *t = static_cast<const BatchEntry<Real> *>(tab);
+    switch (kmode * 2 + (solute ? 1 : 0)) {
+      case 0: batched_step_kernel<S, KM_NONE, false><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
+      case 1: batched_step_kernel<S, KM_NONE, true><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
+      case 2: batched_step_kernel<S, KM_DIAG, false><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
+      case 3: batched_step_kernel<S, KM_DIAG, true><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
+      case 4: batched_step_kernel<S, KM_SPD, false><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
+      default: batched_step_kernel<S, KM_SPD, true><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t batch_advance(void *tab, unsigned nd, cudaStream_t s) {
+    batch_advance_kernel<Real><<<(nd + 127) / 128, 128, 0, s>>>(static_cast<BatchEntry<Real> *>(tab), nd);
+    return cudaGetLastError();
+  }
   static StorageOps make() {
     StorageOps o{};
     o.storage = S::id;
@@ -143,6 +161,9 @@ struct Instance {
     o.from_f64 = &from_f64;
     o.totals = &totals;
     o.fs_step = (S::id == StoreF32::id || S::id == StoreF64::id) ? &fs_step : nullptr;
+    o.batch_step = &batch_step;
+    o.batch_advance = &batch_advance;
+    o.batch_entry_bytes = sizeof(BatchEntry<Real>);
     o.tma_config = nullptr;
     o.tma_step = nullptr;
     if constexpr (S::id != StoreF64::id) {  // static rows are staged as FP32

@@ -29,7 +29,7 @@ STORE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_get_populations",
            "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
            "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
-           "lb_totals_noalloc"]
+           "lb_totals_noalloc", "lb_step_batch"]
 
 
 class LbError(RuntimeError):
@@ -86,6 +86,7 @@ def load() -> ctypes.CDLL:
     L.lb_set_allocator.argtypes = [ALLOC, FREE, vp]
     L._ALLOC, L._FREE = ALLOC, FREE
     L.lb_totals_noalloc.argtypes = [vp, vp, vp, c_int64, vp, vp]
+    L.lb_step_batch.argtypes = [vp, c_int32, c_int64]
     _lib = L
     return L
 
@@ -134,6 +135,12 @@ def lb_get_populations(ctx, f=None, h=None):
 
 def lb_step(ctx, n: int):
     _check(load().lb_step(ctx, int(n)), ctx)
+
+
+def lb_step_batch(ctxs, n_steps: int):
+    """Advance several contexts by n_steps in one batched launch per step."""
+    arr = (c_void_p * len(ctxs))(*[c.value if isinstance(c, c_void_p) else c for c in ctxs])
+    _check(load().lb_step_batch(arr, len(ctxs), int(n_steps)), ctxs[0])
 
 
 def lb_fields(ctx, rho=None, u=None, C=None, nu=None):

@@ -1,0 +1,181 @@
+"""Serving loop for penetration solves: continuous batching under an HBM budget.
+
+Requests (a porous medium, a lattice size and a number of steps) arrive over
+time. A request is admitted as soon as it has arrived and its device memory
+fits the budget next to the lattices already resident; admitted lattices stay
+on the device and are advanced together, ``chunk`` steps at a time, by one
+batched launch per step (``lb_step_batch``). Between chunks finished requests
+export their fields and release their memory, and newly arrived requests
+join, so work that arrives while others run overlaps with them on the GPU.
+Each lattice is computed independently by the same per-cell arithmetic, so a
+result does not depend on what else is in the batch.
+
+The stepping backend is pluggable: :class:`LibraryBackend` drives the CUDA
+library; tests of the host-side logic use a fake backend on the CPU.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Callable, List, Optional
+
+import numpy as np
+
+Q = 19
+ELT = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}
+
+
+def device_bytes(nx: int, ny: int, nz: int, storage: str = "fp32", solute: bool = True,
+                 kmode_rows: int = 3) -> int:
+    """Device memory of one lattice as the library allocates it: two
+    population buffers per lattice, static fields, exported fields, flux
+    slots, staging for initialisation."""
+    N = nx * ny * nz
+    lattices = 2 if solute else 1
+    pops = lattices * 2 * Q * N * ELT[storage]
+    real = 8 if storage == "fp64" else 4
+    static = N * real * (1 + kmode_rows + (3 if solute else 0)) + 4 * N
+    fields = 6 * N * 4
+    stage = 6 * N * 4 + N
+    slots = (N // 256 + 1) * 8 * 2 * 8 + (N // 256 + 1) * 4 * 8
+    return int(pops + static + fields + stage + slots)
+
+
+@dataclasses.dataclass
+class Request:
+    id: int
+    arrival: float               # seconds after the start of the run
+    steps: int
+    problem: object              # workloads.Problem
+    bytes: int = 0
+    admitted: Optional[float] = None
+    done: Optional[float] = None
+    remaining: int = 0
+    handle: object = None
+    result: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+    @property
+    def wait(self) -> float:
+        return self.admitted - self.arrival
+
+
+class LibraryBackend:
+    """Resident lattices on the GPU through the C ABI."""
+
+    def __init__(self, storage: str = "fp32", stream=None, keep_fields: bool = True,
+                 batched: bool = True):
+        from . import lb
+        self.lb = lb
+        self.storage = storage
+        self.stream = stream
+        self.keep_fields = keep_fields
+        self.batched = batched
+
+    def bytes(self, prob) -> int:
+        kr = 0 if prob.K6 is None else 3
+        return device_bytes(prob.nx, prob.ny, prob.nz, self.storage,
+                            bool(prob.params.get("solute")), kr)
+
+    def admit(self, prob):
+        return self.lb.Lattice(prob, storage=self.storage, kernel="cell", stream=self.stream)
+
+    def step(self, handles, n: int):
+        if self.batched:
+            self.lb.lb_step_batch([h.ctx for h in handles], n)
+        else:
+            for h in handles:   # the plain per-lattice path: one launch per lattice and step
+                h.step(n)
+
+    def finish(self, handle):
+        out = None
+        if self.keep_fields:
+            rho, u, C, nu = handle.fields()
+            out = dict(rho=rho, u=u, C=C, nu=nu, totals=handle.reduce())
+        else:
+            handle.sync()
+        handle.close()
+        return out
+
+
+class Server:
+    """Admission by HBM budget, continuous batching in chunks of steps."""
+
+    def __init__(self, backend, budget_bytes: int, chunk: int = 200,
+                 clock: Callable[[], float] = time.perf_counter, sleep=time.sleep,
+                 max_resident: Optional[int] = None):
+        self.backend = backend
+        self.budget = int(budget_bytes)
+        self.chunk = int(chunk)
+        self.max_resident = max_resident
+        self.clock = clock
+        self.sleep = sleep
+        self.log: List[dict] = []
+
+    def run(self, requests: List[Request]) -> dict:
+        pending = sorted(requests, key=lambda r: (r.arrival, r.id))
+        for r in pending:
+            r.bytes = self.backend.bytes(r.problem)
+            r.remaining = r.steps
+            if r.bytes > self.budget:
+                raise ValueError(f"request {r.id} needs {r.bytes} bytes, above the whole budget")
+        active: List[Request] = []
+        finished: List[Request] = []
+        used = 0
+        t0 = self.clock()
+        lups = 0
+        while pending or active:
+            now = self.clock() - t0
+            # admit, in arrival order, every arrived request that fits
+            while (pending and pending[0].arrival <= now and used + pending[0].bytes <= self.budget
+                   and (self.max_resident is None or len(active) < self.max_resident)):
+                r = pending.pop(0)
+                r.handle = self.backend.admit(r.problem)
+                r.admitted = self.clock() - t0
+                used += r.bytes
+                active.append(r)
+            if not active:
+                # nothing resident: wait for the next arrival
+                self.sleep(max(0.0, pending[0].arrival - now))
+                continue
+            n = min(self.chunk, min(r.remaining for r in active))
+            self.backend.step([r.handle for r in active], n)
+            for r in active:
+                r.remaining -= n
+                lups += n * r.problem.N
+            still = []
+            for r in active:
+                if r.remaining == 0:
+                    r.result = self.backend.finish(r.handle)
+                    r.handle = None
+                    r.done = self.clock() - t0
+                    used -= r.bytes
+                    finished.append(r)
+                else:
+                    still.append(r)
+            self.log.append(dict(t=self.clock() - t0, resident=len(active), steps=n, used=used))
+            active = still
+        wall = self.clock() - t0
+        lat = np.array([r.latency for r in finished])
+        wait = np.array([r.wait for r in finished])
+        return dict(
+            requests=len(finished), wall_s=wall, lups=lups, mlups=lups / wall / 1e6 if wall else 0.0,
+            p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+            wait_p50_s=float(np.percentile(wait, 50)), wait_p99_s=float(np.percentile(wait, 99)),
+            max_resident=max((e["resident"] for e in self.log), default=0),
+        )
+
+
+def make_requests(stream, storage="fp32", steps_scale: float = 1.0) -> List[Request]:
+    """Requests of a serving workload (workloads.requests): the miscible medium
+    at each request's size, seeded by its id; steps scaled by steps_scale."""
+    from . import workloads as W
+    out = []
+    for q in stream:
+        p = W.request_problem(q, storage=storage)
+        steps = max(1, int(round(q["steps"] * steps_scale)))
+        out.append(Request(id=q["id"], arrival=q["arrival"], steps=steps, problem=p))
+    return out

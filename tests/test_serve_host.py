@@ -1,0 +1,107 @@
+"""Host-side logic of the serving loop (CPU only, fake stepping backend):
+admission by HBM budget in arrival order, continuous batching in chunks,
+memory released at completion, latency statistics."""
+import numpy as np
+import pytest
+
+from paper_0912_4230_gb300 import serve, workloads as W
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+class FakeBackend:
+    """Each step of each resident lattice costs N * 1e-9 s on the fake clock."""
+
+    def __init__(self, clock, per_lup=1e-9):
+        self.clock, self.per_lup = clock, per_lup
+        self.resident = set()
+        self.batches = []
+
+    def bytes(self, prob):
+        return prob.N * 100
+
+    def admit(self, prob):
+        h = object()
+        self.resident.add(h)
+        return (h, prob.N)
+
+    def step(self, handles, n):
+        self.batches.append(len(handles))
+        self.clock.t += n * sum(N for _, N in handles) * self.per_lup
+
+    def finish(self, handle):
+        self.resident.discard(handle[0])
+        return "ok"
+
+
+def _reqs(specs):
+    out = []
+    for i, (arr, side, steps) in enumerate(specs):
+        p = W.gaussian_pulse(side, side, side)  # any problem: only its size matters here
+        out.append(serve.Request(id=i, arrival=arr, steps=steps, problem=p))
+    return out
+
+
+def test_admission_respects_budget_and_order():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    reqs = _reqs([(0.0, 10, 300), (0.0, 10, 300), (0.0, 10, 300)])
+    srv = serve.Server(be, budget_bytes=2 * 1000 * 100, chunk=100, clock=clk, sleep=clk.sleep)
+    st = srv.run(reqs)
+    assert st["requests"] == 3
+    assert st["max_resident"] == 2          # the third waits for memory
+    assert all(e["used"] <= 2 * 1000 * 100 for e in srv.log)
+    assert reqs[2].admitted >= reqs[0].done  # admitted only after one finished
+    assert not be.resident                  # everything released
+
+
+def test_late_arrivals_join_running_batches():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    # the first request runs 1000 steps; the second arrives while it runs
+    reqs = _reqs([(0.0, 10, 1000), (2e-6 * 300, 10, 200)])
+    srv = serve.Server(be, budget_bytes=10 ** 9, chunk=100, clock=clk, sleep=clk.sleep)
+    st = srv.run(reqs)
+    assert 2 in be.batches                  # both lattices advanced in one batch
+    assert reqs[1].done < reqs[0].done      # the short late request finished first
+    assert st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_idle_server_waits_for_arrivals():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    reqs = _reqs([(5.0, 8, 10)])
+    st = serve.Server(be, budget_bytes=10 ** 9, chunk=10, clock=clk, sleep=clk.sleep).run(reqs)
+    assert reqs[0].admitted >= 5.0 and st["requests"] == 1
+
+
+def test_request_above_budget_is_refused():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    with pytest.raises(ValueError):
+        serve.Server(be, budget_bytes=10, clock=clk, sleep=clk.sleep).run(_reqs([(0.0, 8, 10)]))
+
+
+def test_device_bytes_scale():
+    b32 = serve.device_bytes(64, 64, 64, "fp32")
+    b16 = serve.device_bytes(64, 64, 64, "fp16")
+    assert b16 < b32 < 2 * b16 + 64 ** 3 * 100
+    assert serve.device_bytes(128, 128, 128) > 600e6   # 2 x 2 x 19 x 4 B x 2.1M cells alone
+
+
+def test_request_stream_matches_the_serving_workload():
+    rs = W.requests(n=256, rate=50.0, seed=5)
+    gaps = np.diff([0.0] + [r["arrival"] for r in rs])
+    assert len(rs) == 256 and abs(gaps.mean() - 1 / 50.0) < 0.3 / 50.0
+    assert {r["nx"] for r in rs} <= {32, 48, 64, 96, 128, 160}
+    assert all(r["nx"] <= r["nz"] <= 2 * r["nx"] + 1 for r in rs)
+    assert all(2000 <= r["steps"] <= 20000 for r in rs)
