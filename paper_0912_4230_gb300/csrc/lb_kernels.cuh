@@ -321,6 +321,26 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
       d[q] = S::template ld_f<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g)));
     });
   }
+  // every load of the interior path is issued before any arithmetic, so a
+  // warp keeps its 38 population rows and static fields in flight together
+  const Real eps = __ldg(a.eps + n);
+  Real hh[SOLUTE ? Q : 1];
+  Real gx = Real(0), gy = Real(0), gz = Real(0);
+  const T *__restrict__ hb = static_cast<const T *>(a.h_in) + n;
+  const unsigned s_open = a.s_inlet | a.s_outlet;
+  const bool h_simple = SOLUTE && link == 0 && !(g.onface & (a.s_wall | s_open));
+  if (SOLUTE) {
+    gx = __ldg(a.geps + n);
+    gy = __ldg(a.geps + N + n);
+    gz = __ldg(a.geps + 2 * size_t(N) + n);
+    open_face = (g.onface & s_open) != 0;
+    if (h_simple) {
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+      });
+    }
+  }
   Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
@@ -332,24 +352,10 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
   const Real rho = Real(1) + drho;
   const Real irho = rcp(rho);
   const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
-  const Real eps = __ldg(a.eps + n);
   const Real ie = rcp(eps);
 
-  Real hh[SOLUTE ? Q : 1];
-  Real gx = Real(0), gy = Real(0), gz = Real(0);
   if (SOLUTE) {
-    const T *__restrict__ hb = static_cast<const T *>(a.h_in) + n;
-    gx = __ldg(a.geps + n);
-    gy = __ldg(a.geps + N + n);
-    gz = __ldg(a.geps + 2 * size_t(N) + n);
-    const unsigned s_open = a.s_inlet | a.s_outlet;
-    open_face = (g.onface & s_open) != 0;
-    if (link == 0 && !(g.onface & (a.s_wall | s_open))) {
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
-      });
-    } else {
+    if (!h_simple) {
       const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
       Unroll<0, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
