@@ -218,15 +218,18 @@ def run_serving(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_0912_4230_gb300 import serve, workloads as W
+    from paper_0912_4230_gb300 import lb
     n_req, scale = args.requests, args.steps_scale
     stream = W.requests(n=n_req, rate=50.0, seed=5)
-    s = torch.cuda.current_stream().cuda_stream
+    lb.use_torch_allocator()   # cached device memory: no cudaMalloc/cudaFree per request
+    step_s, admit_s = torch.cuda.Stream(), torch.cuda.Stream()
     res = {}
     for name, storage, batched, maxres in (("batched_fp32", "fp32", True, None),
                                            ("batched_fp16", "fp16", True, None),
                                            ("per_lattice_fp32", "fp32", False, 1)):
         reqs = serve.make_requests(stream, storage=storage, steps_scale=scale)
-        be = serve.LibraryBackend(storage, stream=s, keep_fields=False, batched=batched)
+        be = serve.LibraryBackend(storage, keep_fields=False, batched=batched,
+                                  admit_stream=admit_s, step_stream=step_s)
         srv = serve.Server(be, budget_bytes=120 * 10 ** 9, chunk=args.chunk, max_resident=maxres)
         torch.cuda.synchronize()
         with ClockSampler(0) as clk:

@@ -128,7 +128,10 @@ typedef struct {
 int lb_create(const lb_domain *domain, const float *porosity, const float *K6,
               const uint8_t *solid, const lb_params *params, lb_ctx **out);
 
-/* Enqueue all further work of the context on this cudaStream_t. */
+/* Enqueue all further work of the context on this cudaStream_t. With
+ * ctx = NULL: the stream on which later lb_create calls of this thread do
+ * their own copies and set-up kernels, and the initial stream of the
+ * contexts they create (default: the legacy default stream). */
 int lb_set_stream(lb_ctx *ctx, void *cuda_stream);
 
 /* Initial fields (flowchart steps a-c, Section 4): f = f^eq (Eqs. equilc1,

@@ -21,6 +21,7 @@ void *(*g_alloc)(size_t, void *) = nullptr;
 void (*g_release)(void *, void *) = nullptr;
 void *g_alloc_user = nullptr;
 thread_local std::string g_create_error;
+thread_local cudaStream_t g_create_stream = nullptr;  // stream of lb_create's own work
 
 }  // namespace
 
@@ -271,6 +272,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   c->dom = *dom;
   c->prm = *prm;
   c->ops = ops;
+  c->stream = g_create_stream;
   c->alloc_fn = g_alloc;
   c->release_fn = g_release;
   c->alloc_user = g_alloc_user;
@@ -279,10 +281,10 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   {
     // step kernel: rows of BX threads (a multiple of 32), BY rows per block
     unsigned bx = 32;
-    while (bx < 128 && bx < unsigned(dom->nx)) bx *= 2;
-    c->sblock = dim3(bx, BLOCK / bx, 1);
+    while (bx < unsigned(STEP_BLOCK) && bx < unsigned(dom->nx)) bx *= 2;
+    c->sblock = dim3(bx, STEP_BLOCK / bx, 1);
     c->sgrid = dim3((dom->nx + bx - 1) / bx, (dom->ny + c->sblock.y - 1) / c->sblock.y, dom->nz);
-    c->nwarps = c->sgrid.x * c->sgrid.y * c->sgrid.z * (BLOCK / 32);
+    c->nwarps = c->sgrid.x * c->sgrid.y * c->sgrid.z * (STEP_BLOCK / 32);
   }
   c->solute = prm->solute != 0;
   c->fs = prm->free_surface != 0;
@@ -403,7 +405,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   dev_free(c, in);
   std::vector<uint8_t> hs(N);
   // count of live cells, for the mass of the in-step check
-  if (cudaMemcpy(hs.data(), solid, N, cudaMemcpyDefault) == cudaSuccess) {
+  if (cudaMemcpyAsync(hs.data(), solid, N, cudaMemcpyDefault, c->stream) == cudaSuccess &&
+      cudaStreamSynchronize(c->stream) == cudaSuccess) {
     long long live = 0;
     for (size_t i = 0; i < N; ++i) live += hs[i] == 0;
     c->n_live = live;
@@ -413,7 +416,10 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
 }
 
 int lb_set_stream(lb_ctx *c, void *stream) {
-  if (!c) return LB_EINVAL;
+  if (!c) {
+    g_create_stream = static_cast<cudaStream_t>(stream);
+    return LB_OK;
+  }
   c->stream = static_cast<cudaStream_t>(stream);
   return LB_OK;
 }
@@ -540,7 +546,15 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
     e.blk_begin = total;
     total += c->sgrid.x * c->sgrid.y * c->sgrid.z;
   }
-  const size_t bytes = tab.size() * sizeof(BatchEntry<Real>);
+  if (n > 65535) return fail(c0, LB_EUNSUPPORTED, "more than 65535 lattices in one batch");
+  std::vector<uint16_t> owner(total);
+  for (int i = 0; i < n; ++i) {
+    const unsigned end = (i + 1 < n) ? tab[i + 1].blk_begin : total;
+    for (unsigned b = tab[i].blk_begin; b < end; ++b) owner[b] = uint16_t(i);
+  }
+  const size_t tbytes = tab.size() * sizeof(BatchEntry<Real>);
+  const size_t obytes = owner.size() * sizeof(uint16_t);
+  const size_t bytes = ((tbytes + 255) & ~size_t(255)) + obytes;
   if (c0->batch_tab_bytes < bytes) {
     dev_free(c0, c0->batch_tab);
     c0->batch_tab = dev_alloc(c0, bytes);
@@ -548,16 +562,19 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
     if (!c0->batch_tab) return fail(c0, LB_ENOMEM, "batch table");
   }
   cudaStream_t s = c0->stream;
-  CK(c0, cudaMemcpyAsync(c0->batch_tab, tab.data(), bytes, cudaMemcpyHostToDevice, s));
+  uint16_t *d_owner = reinterpret_cast<uint16_t *>(static_cast<char *>(c0->batch_tab) +
+                                                   ((tbytes + 255) & ~size_t(255)));
+  CK(c0, cudaMemcpyAsync(c0->batch_tab, tab.data(), tbytes, cudaMemcpyHostToDevice, s));
+  CK(c0, cudaMemcpyAsync(d_owner, owner.data(), obytes, cudaMemcpyHostToDevice, s));
   int dev = 0, sms = 0;
   CK(c0, cudaGetDevice(&dev));
   CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = std::min(total, unsigned(3 * sms));
+  const unsigned grid = std::min(total, unsigned(6 * sms));
   const StorageOps *ops = c0->ops;
   const int km = c0->kmode;
   const bool sol = c0->solute;
   auto one = [&]() -> cudaError_t {
-    cudaError_t e = ops->batch_step(km, sol, c0->batch_tab, unsigned(n), total, grid, s);
+    cudaError_t e = ops->batch_step(km, sol, c0->batch_tab, d_owner, unsigned(n), total, grid, s);
     if (e == cudaSuccess) e = ops->batch_advance(c0->batch_tab, unsigned(n), s);
     return e;
   };

@@ -25,29 +25,22 @@ struct BatchEntry {
 };
 
 template <class S, int KMODE, bool SOLUTE>
-__global__ void __launch_bounds__(BLOCK, 3)
-    batched_step_kernel(const BatchEntry<typename S::Real> *__restrict__ tab, unsigned nd,
-                        unsigned total) {
+__global__ void __launch_bounds__(STEP_BLOCK, 6)
+    batched_step_kernel(const BatchEntry<typename S::Real> *__restrict__ tab,
+                        const uint16_t *__restrict__ owner, unsigned nd, unsigned total) {
   using Real = typename S::Real;
   for (unsigned vb = blockIdx.x; vb < total; vb += gridDim.x) {
-    // lattice of this virtual block (binary search over blk_begin)
-    unsigned lo = 0, hi = nd - 1;
-    while (lo < hi) {
-      const unsigned mid = (lo + hi + 1) / 2;
-      if (__ldg(&tab[mid].blk_begin) <= vb)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    const BatchEntry<Real> &e = tab[lo];
+    // lattice of this virtual block (one entry per block of the work list)
+    const BatchEntry<Real> &e = tab[__ldg(owner + vb)];
     const StepArgs<Real> &a = e.a;
     const unsigned lb = vb - e.blk_begin;
     const unsigned bxi = lb % e.gx, byi = (lb / e.gx) % e.gy, bz = lb / (e.gx * e.gy);
-    const unsigned by = BLOCK / e.bx;
+    const unsigned by = STEP_BLOCK / e.bx;
     const unsigned tx = threadIdx.x % e.bx, ty = threadIdx.x / e.bx;
     const unsigned x = bxi * e.bx + tx, y = byi * by + ty, z = bz;
     const unsigned nx = a.nx, ny = a.ny;
-    const unsigned warp_gid = ((bz * e.gy + byi) * e.gx + bxi) * (BLOCK / 32) + (threadIdx.x >> 5);
+    const unsigned warp_gid =
+        ((bz * e.gy + byi) * e.gx + bxi) * (STEP_BLOCK / 32) + (threadIdx.x >> 5);
     bool live = x < nx && y < ny;
     const unsigned n = x + nx * (y + ny * z);
     uint32_t link = 0;

@@ -10,7 +10,8 @@
 namespace lbgb {
 
 constexpr int Q = 19;
-constexpr int BLOCK = 256;  // threads per block of the per-cell kernels
+constexpr int BLOCK = 256;       // threads per block of the per-cell helper kernels
+constexpr int STEP_BLOCK = 128;  // threads per block of the step kernels
 
 // D3Q19 velocity set in the paper's (orientation i, reference plane p) order
 // (Section 2.1, Fig. d3q19): q = 0 rest; q = 1 + 6p + (i-1) with planes

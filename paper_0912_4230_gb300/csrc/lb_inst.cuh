@@ -132,16 +132,16 @@ struct Instance {
     }
     return cudaGetLastError();
   }
-  static cudaError_t batch_step(int kmode, bool solute, const void *tab, unsigned nd,
-                                unsigned total, unsigned grid, cudaStream_t s) {
+  static cudaError_t batch_step(int kmode, bool solute, const void *tab, const uint16_t *owner,
+                                unsigned nd, unsigned total, unsigned grid, cudaStream_t s) {
     const BatchEntry<Real> *t = static_cast<const BatchEntry<Real> *>(tab);
     switch (kmode * 2 + (solute ? 1 : 0)) {
-      case 0: batched_step_kernel<S, KM_NONE, false><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
-      case 1: batched_step_kernel<S, KM_NONE, true><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
-      case 2: batched_step_kernel<S, KM_DIAG, false><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
-      case 3: batched_step_kernel<S, KM_DIAG, true><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
-      case 4: batched_step_kernel<S, KM_SPD, false><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
-      default: batched_step_kernel<S, KM_SPD, true><<<grid, BLOCK, 0, s>>>(t, nd, total); break;
+      case 0: batched_step_kernel<S, KM_NONE, false><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
+      case 1: batched_step_kernel<S, KM_NONE, true><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
+      case 2: batched_step_kernel<S, KM_DIAG, false><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
+      case 3: batched_step_kernel<S, KM_DIAG, true><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
+      case 4: batched_step_kernel<S, KM_SPD, false><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
+      default: batched_step_kernel<S, KM_SPD, true><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
     }
     return cudaGetLastError();
   }

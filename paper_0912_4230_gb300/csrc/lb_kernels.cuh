@@ -426,20 +426,21 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
 }
 
 // One time step for every non-solid cell (see update_cell).
-// Launch: block (BX, BY) with BX a multiple of 32, grid (ceil(nx/BX),
-// ceil(ny/BY), nz); a warp covers 32 consecutive x of one row.
-// Three resident blocks per SM (at most 85 registers a thread): measured on
-// GB300 at 128^3 this beats the unconstrained 112-register build (two blocks
-// per SM) by 1.2x, since the kernel is bound by loads in flight.
+// Launch: block (BX, BY) of STEP_BLOCK threads with BX a multiple of 32,
+// grid (ceil(nx/BX), ceil(ny/BY), nz); a warp covers 32 consecutive x of one
+// row. Six resident 128-thread blocks per SM (at most 85 registers a
+// thread): measured on GB300 at 128^3 this is 1.1x faster than the
+// unconstrained build (112 registers), since the kernel is bound by loads in
+// flight, and a little faster than 256-thread blocks at the same occupancy.
 template <class S, int KMODE, bool SOLUTE>
-__global__ void __launch_bounds__(BLOCK, 3) step_kernel(const StepArgs<typename S::Real> a) {
+__global__ void __launch_bounds__(STEP_BLOCK, 6) step_kernel(const StepArgs<typename S::Real> a) {
   using Real = typename S::Real;
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned y = blockIdx.y * blockDim.y + threadIdx.y;
   const unsigned z = blockIdx.z;
   const unsigned nx = a.nx, ny = a.ny;
   const unsigned warp_gid =
-      ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (BLOCK / 32) +
+      ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (STEP_BLOCK / 32) +
       ((threadIdx.y * blockDim.x + threadIdx.x) >> 5);
   bool live = x < nx && y < ny;
   const unsigned n = x + nx * (y + ny * z);

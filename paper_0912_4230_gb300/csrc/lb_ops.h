@@ -34,8 +34,8 @@ struct StorageOps {
   cudaError_t (*tma_step)(int kmode, bool solute, const void *args, unsigned grid,
                           unsigned threads, size_t smem, cudaStream_t s);
   // batched step over a table of BatchEntry<Real> (device memory)
-  cudaError_t (*batch_step)(int kmode, bool solute, const void *tab, unsigned nd, unsigned total,
-                            unsigned grid, cudaStream_t s);
+  cudaError_t (*batch_step)(int kmode, bool solute, const void *tab, const uint16_t *owner,
+                            unsigned nd, unsigned total, unsigned grid, cudaStream_t s);
   cudaError_t (*batch_advance)(void *tab, unsigned nd, cudaStream_t s);
   size_t batch_entry_bytes;
 };

@@ -117,6 +117,7 @@ def lb_create(domain: lb_domain, porosity, K6, solid, params: lb_params):
 
 
 def lb_set_stream(ctx, stream_handle: int):
+    """ctx None: stream of later lb_create calls on this thread."""
     _check(load().lb_set_stream(ctx, c_void_p(stream_handle)), ctx)
 
 

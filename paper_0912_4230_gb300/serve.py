@@ -64,16 +64,22 @@ class Request:
 
 
 class LibraryBackend:
-    """Resident lattices on the GPU through the C ABI."""
+    """Resident lattices on the GPU through the C ABI.
+
+    With torch streams given, a new lattice is created and initialised on
+    ``admit_stream`` while earlier lattices step on ``step_stream``; the step
+    stream waits for the admission work before the lattice's first step."""
 
     def __init__(self, storage: str = "fp32", stream=None, keep_fields: bool = True,
-                 batched: bool = True):
+                 batched: bool = True, admit_stream=None, step_stream=None):
         from . import lb
         self.lb = lb
         self.storage = storage
         self.stream = stream
         self.keep_fields = keep_fields
         self.batched = batched
+        self.admit_stream = admit_stream
+        self.step_stream = step_stream
 
     def bytes(self, prob) -> int:
         kr = 0 if prob.K6 is None else 3
@@ -81,7 +87,14 @@ class LibraryBackend:
                             bool(prob.params.get("solute")), kr)
 
     def admit(self, prob):
-        return self.lb.Lattice(prob, storage=self.storage, kernel="cell", stream=self.stream)
+        if self.admit_stream is None:
+            return self.lb.Lattice(prob, storage=self.storage, kernel="cell", stream=self.stream)
+        self.lb.lb_set_stream(None, self.admit_stream.cuda_stream)
+        h = self.lb.Lattice(prob, storage=self.storage, kernel="cell",
+                            stream=self.admit_stream.cuda_stream)
+        self.step_stream.wait_stream(self.admit_stream)
+        self.lb.lb_set_stream(h.ctx, self.step_stream.cuda_stream)
+        return h
 
     def step(self, handles, n: int):
         if self.batched:
