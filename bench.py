@@ -224,8 +224,9 @@ def run_serving(args):
     lb.use_torch_allocator()   # cached device memory: no cudaMalloc/cudaFree per request
     step_s, admit_s = torch.cuda.Stream(), torch.cuda.Stream()
     res = {}
-    for name, storage, batched, maxres in (("batched_fp32", "fp32", True, None),
-                                           ("batched_fp16", "fp16", True, None),
+    cap = args.max_resident or None
+    for name, storage, batched, maxres in (("batched_fp32", "fp32", True, cap),
+                                           ("batched_fp16", "fp16", True, cap),
                                            ("per_lattice_fp32", "fp32", False, 1)):
         reqs = serve.make_requests(stream, storage=storage, steps_scale=scale)
         be = serve.LibraryBackend(storage, keep_fields=False, batched=batched,
@@ -245,7 +246,8 @@ def run_serving(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{n_req} requests, Poisson 50/s, sides 32..160, z-aspect 1..2, "
                                f"steps U(2000, 20000) x {scale}, 120 GB admission budget, "
-                               f"chunk {args.chunk} steps"},
+                               f"chunk {args.chunk} steps, at most "
+                               f"{args.max_resident or 'budget-many'} lattices stepped together"},
         "serving": res,
         "gpu_launches": None,
     }
@@ -266,6 +268,8 @@ def main():
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--steps-scale", type=float, default=0.02)
     ap.add_argument("--chunk", type=int, default=100)
+    ap.add_argument("--max-resident", type=int, default=0,
+                    help="serving: cap on lattices stepped together (0 = HBM budget only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

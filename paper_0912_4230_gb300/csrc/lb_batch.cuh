@@ -23,15 +23,25 @@ struct BatchEntry {
   int check_every;
   int pad;
 };
+static_assert(sizeof(BatchEntry<float>) % 4 == 0 && sizeof(BatchEntry<double>) % 4 == 0,
+              "batch entries are copied as 32-bit words");
 
 template <class S, int KMODE, bool SOLUTE>
 __global__ void __launch_bounds__(STEP_BLOCK, 6)
     batched_step_kernel(const BatchEntry<typename S::Real> *__restrict__ tab,
                         const uint16_t *__restrict__ owner, unsigned nd, unsigned total) {
   using Real = typename S::Real;
+  // the lattice's arguments are copied to shared memory once per work item,
+  // so the per-cell update reads them at shared-memory latency
+  __shared__ BatchEntry<Real> se;
+  constexpr unsigned words = sizeof(BatchEntry<Real>) / 4;
   for (unsigned vb = blockIdx.x; vb < total; vb += gridDim.x) {
-    // lattice of this virtual block (one entry per block of the work list)
-    const BatchEntry<Real> &e = tab[__ldg(owner + vb)];
+    const unsigned d = __ldg(owner + vb);
+    __syncthreads();  // the previous item's readers are done with se
+    for (unsigned w = threadIdx.x; w < words; w += blockDim.x)
+      reinterpret_cast<unsigned *>(&se)[w] = __ldg(reinterpret_cast<const unsigned *>(tab + d) + w);
+    __syncthreads();
+    const BatchEntry<Real> &e = se;
     const StepArgs<Real> &a = e.a;
     const unsigned lb = vb - e.blk_begin;
     const unsigned bxi = lb % e.gx, byi = (lb / e.gx) % e.gy, bz = lb / (e.gx * e.gy);
