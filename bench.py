@@ -52,11 +52,11 @@ def _other_workloads():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources that define and launch the benchmarked step kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0912_4230_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("lb_common.cuh", "lb_kernels.cuh", "lb_inst.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
