@@ -414,13 +414,23 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
     T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
     const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
     const Real itd = a.inv_tau_D;
-    Unroll<0, Q>::run([&](auto qc) {
+    // h^eq of the moving directions; the rest component takes the remainder
+    // so that sum_q h^eq_q = sum_q h_q holds to rounding (the weights rounded
+    // to the collision type sum to 1 + 1.5e-8 in FP32, which would otherwise
+    // create solute at every collision)
+    Real hsum = Real(0);
+    Unroll<1, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
       const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
+      hsum += heq;
       const Real h = hh[SOLUTE ? q : 0];
       S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd);
     });
+    {
+      const Real h = hh[0];
+      S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd);
+    }
   }
   if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
 }

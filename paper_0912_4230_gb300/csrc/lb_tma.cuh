@@ -361,13 +361,20 @@ __global__ void __launch_bounds__(32 * (NW + 1), MINB)
         T *ho = static_cast<T *>(a.h_out) + n;
         const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
         const Real itd = a.inv_tau_D;
-        Unroll<0, Q>::run([&](auto qc) {
+        // rest component of h^eq as the remainder (see update_cell)
+        Real hsum = Real(0);
+        Unroll<1, Q>::run([&](auto qc) {
           constexpr int q = decltype(qc)::value;
           const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
           const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
+          hsum += heq;
           const Real h = hval(qc);
           S::template st_h<q>(ho + size_t(q) * N, h + (heq - h) * itd);
         });
+        {
+          const Real h = hval(std::integral_constant<int, 0>{});
+          S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd);
+        }
       }
       if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
     }
