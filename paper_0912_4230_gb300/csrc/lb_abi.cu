@@ -44,6 +44,8 @@ struct lb_ctx {
   int cur = 0;
   void *f[2] = {nullptr, nullptr};
   void *h[2] = {nullptr, nullptr};
+  float *rf[2] = {nullptr, nullptr};  // FP16/BF16 storage: per-cell references
+  float *rh[2] = {nullptr, nullptr};
   void *eps = nullptr, *kinv = nullptr, *geps = nullptr, *rhohat = nullptr;
   uint32_t *link = nullptr;
   float *fields = nullptr;
@@ -153,6 +155,10 @@ void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
   a.f_out = c->f[1 - c->cur];
   a.h_in = c->h[c->cur];
   a.h_out = c->h[1 - c->cur];
+  a.rf_in = c->rf[c->cur];
+  a.rf_out = c->rf[1 - c->cur];
+  a.rh_in = c->rh[c->cur];
+  a.rh_out = c->rh[1 - c->cur];
   a.eps = static_cast<const Real *>(c->eps);
   a.kinv = static_cast<const Real *>(c->kinv);
   a.geps = static_cast<const Real *>(c->geps);
@@ -304,9 +310,16 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   const size_t rb = ops->fp64 ? 8 : 4;
   const size_t pb = size_t(Q) * N * ops->elt_bytes;
   // device memory
+  const bool shift = (prm->storage == LB_STORE_FP16DEV || prm->storage == LB_STORE_BF16DEV);
   for (int b = 0; b < 2; ++b) {
     if (!(c->f[b] = dev_alloc(c, pb))) return bail(fail(c, LB_ENOMEM, "populations f"));
     if (c->solute && !(c->h[b] = dev_alloc(c, pb))) return bail(fail(c, LB_ENOMEM, "populations h"));
+    if (shift) {
+      c->rf[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
+      if (!c->rf[b]) return bail(fail(c, LB_ENOMEM, "references"));
+      if (c->solute && !(c->rh[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)))))
+        return bail(fail(c, LB_ENOMEM, "references"));
+    }
   }
   c->eps = dev_alloc(c, N * rb);
   c->link = static_cast<uint32_t *>(dev_alloc(c, N * 4));
@@ -654,7 +667,8 @@ int lb_reduce(lb_ctx *c, double *mass, double *solute, double *flux_in, double *
     CK(c, fs_totals(c->N, c->link, c->mass[c->cur], c->partials, c->ops->fp64, c->stream));
   else
     CK(c, c->ops->totals(c->f[c->cur], c->solute ? c->h[c->cur] : nullptr,
-                         c->has_solid ? c->link : nullptr, c->N, c->partials, c->nblk, c->stream));
+                         c->has_solid ? c->link : nullptr, c->N, c->partials, c->nblk,
+                         c->rf[c->cur], c->rh[c->cur], c->stream));
   CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
   CK(c, finish_sum(c->flux_slots, c->nwarps, 2, out + 2, c->stream));
   CK(c, cudaMemcpyAsync(tot, out, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
@@ -676,11 +690,11 @@ int lb_set_populations(lb_ctx *c, const double *f, const double *h) {
   if (!st) return fail(c, LB_ENOMEM, "staging");
   if (f) {
     CK(c, cudaMemcpyAsync(st, f, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
-    CK(c, c->ops->from_f64(st, c->f[c->cur], c->N, 0, c->stream));
+    CK(c, c->ops->from_f64(st, c->f[c->cur], c->N, 0, c->rf[c->cur], c->stream));
   }
   if (h && c->solute) {
     CK(c, cudaMemcpyAsync(st, h, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
-    CK(c, c->ops->from_f64(st, c->h[c->cur], c->N, 1, c->stream));
+    CK(c, c->ops->from_f64(st, c->h[c->cur], c->N, 1, c->rh[c->cur], c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
   return LB_OK;
@@ -692,12 +706,12 @@ int lb_get_populations(lb_ctx *c, double *f, double *h) {
   double *st = static_cast<double *>(stage(c, size_t(Q) * N * sizeof(double)));
   if (!st) return fail(c, LB_ENOMEM, "staging");
   if (f) {
-    CK(c, c->ops->to_f64(c->f[c->cur], st, c->N, 0, c->stream));
+    CK(c, c->ops->to_f64(c->f[c->cur], st, c->N, 0, c->rf[c->cur], c->stream));
     CK(c, cudaMemcpyAsync(f, st, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
   }
   if (h && c->solute) {
-    CK(c, c->ops->to_f64(c->h[c->cur], st, c->N, 1, c->stream));
+    CK(c, c->ops->to_f64(c->h[c->cur], st, c->N, 1, c->rh[c->cur], c->stream));
     CK(c, cudaMemcpyAsync(h, st, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
   }

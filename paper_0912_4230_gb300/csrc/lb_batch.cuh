@@ -78,6 +78,12 @@ __global__ void batch_advance_kernel(BatchEntry<Real> *tab, unsigned nd) {
   const void *hi = a.h_in;
   a.h_in = a.h_out;
   a.h_out = const_cast<void *>(hi);
+  const float *rfi = a.rf_in;
+  a.rf_in = a.rf_out;
+  a.rf_out = const_cast<float *>(rfi);
+  const float *rhi = a.rh_in;
+  a.rh_in = a.rh_out;
+  a.rh_out = const_cast<float *>(rhi);
   a.t += 1;
   const int ce = tab[d].check_every;
   a.reduce = (ce > 0 && a.t % ce == 0) ? 1 : 0;

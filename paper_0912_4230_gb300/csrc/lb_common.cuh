@@ -66,38 +66,46 @@ struct StoreF32 {
   using T = float;
   using Real = float;
   static constexpr int id = 0;
+  static constexpr bool kShift = false;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
   template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
   template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
   template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { __stcs(p, v); }
-  __host__ __device__ static double to_f(T v, int q) { return double(v) + wq<double>(q); }
-  __host__ __device__ static T from_f(double f, int q) { return T(f - wq<double>(q)); }
-  __host__ __device__ static double to_h(T v, int) { return double(v); }
-  __host__ __device__ static T from_h(double h, int) { return T(h); }
+  __host__ __device__ static double to_f(T v, int q, double = 0.0) { return double(v) + wq<double>(q); }
+  __host__ __device__ static T from_f(double f, int q, double = 0.0) { return T(f - wq<double>(q)); }
+  __host__ __device__ static double to_h(T v, int, double = 0.0) { return double(v); }
+  __host__ __device__ static T from_h(double h, int, double = 0.0) { return T(h); }
 };
 
 struct StoreF64 {
   using T = double;
   using Real = double;
   static constexpr int id = 1;
+  static constexpr bool kShift = false;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
   template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
   template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
   template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { __stcs(p, v); }
-  __host__ __device__ static double to_f(T v, int q) { return v + wq<double>(q); }
-  __host__ __device__ static T from_f(double f, int q) { return f - wq<double>(q); }
-  __host__ __device__ static double to_h(T v, int) { return v; }
-  __host__ __device__ static T from_h(double h, int) { return h; }
+  __host__ __device__ static double to_f(T v, int q, double = 0.0) { return v + wq<double>(q); }
+  __host__ __device__ static T from_f(double f, int q, double = 0.0) { return f - wq<double>(q); }
+  __host__ __device__ static double to_h(T v, int, double = 0.0) { return v; }
+  __host__ __device__ static T from_h(double h, int, double = 0.0) { return h; }
 };
 
+// FP16 / BF16: each cell also keeps an FP32 reference per lattice (its density
+// deviation rho - 1 for f, its solute content sum_q h_q for h), and the
+// 16-bit populations hold the remainder g_q = (f_q - w_q)/w_q - ref (resp.
+// h_q/w_q - ref): the conserved parts never pass through the short mantissa.
+// ld_*/st_* below convert w_q g_q; the kernels add / subtract w_q ref.
 struct StoreF16 {
   using T = __half;
   using Real = float;
   static constexpr int id = 2;
+  static constexpr bool kShift = true;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) {
     return __half2float(v) * wq<float>(q);
   }
@@ -116,16 +124,18 @@ struct StoreF16 {
   template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) {
     __stcs(p, __float2half_rn(v * float(inv_wq(q))));
   }
-  __device__ static double to_f(T v, int q) { return double(__half2float(v)) * wq<double>(q) + wq<double>(q); }
-  __device__ static T from_f(double f, int q) { return __float2half_rn(float((f - wq<double>(q)) * inv_wq(q))); }
-  __device__ static double to_h(T v, int q) { return double(__half2float(v)) * wq<double>(q); }
-  __device__ static T from_h(double h, int q) { return __float2half_rn(float(h * inv_wq(q))); }
+  // with ref: f = w (g + ref) + w, h = w (g + ref)
+  __device__ static double to_f(T v, int q, double ref) { return (double(__half2float(v)) + ref) * wq<double>(q) + wq<double>(q); }
+  __device__ static T from_f(double f, int q, double ref) { return __float2half_rn(float((f - wq<double>(q)) * inv_wq(q) - ref)); }
+  __device__ static double to_h(T v, int q, double ref) { return (double(__half2float(v)) + ref) * wq<double>(q); }
+  __device__ static T from_h(double h, int q, double ref) { return __float2half_rn(float(h * inv_wq(q) - ref)); }
 };
 
 struct StoreBF16 {
   using T = __nv_bfloat16;
   using Real = float;
   static constexpr int id = 3;
+  static constexpr bool kShift = true;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) {
     return __bfloat162float(v) * wq<float>(q);
   }
@@ -144,10 +154,10 @@ struct StoreBF16 {
   template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) {
     __stcs(p, __float2bfloat16_rn(v * float(inv_wq(q))));
   }
-  __device__ static double to_f(T v, int q) { return double(__bfloat162float(v)) * wq<double>(q) + wq<double>(q); }
-  __device__ static T from_f(double f, int q) { return __float2bfloat16_rn(float((f - wq<double>(q)) * inv_wq(q))); }
-  __device__ static double to_h(T v, int q) { return double(__bfloat162float(v)) * wq<double>(q); }
-  __device__ static T from_h(double h, int q) { return __float2bfloat16_rn(float(h * inv_wq(q))); }
+  __device__ static double to_f(T v, int q, double ref) { return (double(__bfloat162float(v)) + ref) * wq<double>(q) + wq<double>(q); }
+  __device__ static T from_f(double f, int q, double ref) { return __float2bfloat16_rn(float((f - wq<double>(q)) * inv_wq(q) - ref)); }
+  __device__ static double to_h(T v, int q, double ref) { return (double(__bfloat162float(v)) + ref) * wq<double>(q); }
+  __device__ static T from_h(double h, int q, double ref) { return __float2bfloat16_rn(float(h * inv_wq(q) - ref)); }
 };
 
 // ------------------------------------------------------------------------
@@ -174,6 +184,8 @@ struct StepArgs {
   void *f_out;
   const void *h_in;
   void *h_out;
+  const float *rf_in, *rh_in;  // FP16/BF16: per-cell references of the input populations
+  float *rf_out, *rh_out;      // ... and of the output populations
   const Real *eps;       // N
   const Real *kinv;      // KM_DIAG: 3 x N (xx, yy, zz); KM_SPD: 6 x N (xx, yy, zz, xy, yz, zx)
   const Real *geps;      // 3 x N: D grad(eps)/eps (solute only)

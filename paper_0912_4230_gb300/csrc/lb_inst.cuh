@@ -48,23 +48,28 @@ struct Instance {
     rhohat_kernel<S><<<nblk, BLOCK, 0, s>>>(*static_cast<const A *>(args), static_cast<Real *>(rh));
     return cudaGetLastError();
   }
-  static cudaError_t to_f64(const void *src, double *dst, unsigned N, int lattice, cudaStream_t s) {
+  static cudaError_t to_f64(const void *src, double *dst, unsigned N, int lattice, const float *ref,
+                            cudaStream_t s) {
     const size_t tot = size_t(Q) * N;
     to_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(
-        static_cast<const typename S::T *>(src), dst, N, lattice);
+        static_cast<const typename S::T *>(src), dst, N, lattice, S::kShift ? ref : nullptr);
     return cudaGetLastError();
   }
-  static cudaError_t from_f64(const double *src, void *dst, unsigned N, int lattice, cudaStream_t s) {
+  static cudaError_t from_f64(const double *src, void *dst, unsigned N, int lattice, float *ref,
+                              cudaStream_t s) {
     const size_t tot = size_t(Q) * N;
+    if (S::kShift) ref_from_f64_kernel<<<(N + BLOCK - 1) / BLOCK, BLOCK, 0, s>>>(src, N, lattice, ref);
     from_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(
-        src, static_cast<typename S::T *>(dst), N, lattice);
+        src, static_cast<typename S::T *>(dst), N, lattice, S::kShift ? ref : nullptr);
     return cudaGetLastError();
   }
   static cudaError_t totals(const void *f, const void *h, const uint32_t *link, unsigned N,
-                            double *partials, unsigned nblk, cudaStream_t s) {
+                            double *partials, unsigned nblk, const float *rf, const float *rh,
+                            cudaStream_t s) {
     totals_kernel<S><<<nblk, BLOCK, 0, s>>>(static_cast<const typename S::T *>(f),
                                              static_cast<const typename S::T *>(h), link, N,
-                                             partials);
+                                             partials, S::kShift ? rf : nullptr,
+                                             S::kShift ? rh : nullptr);
     return cudaGetLastError();
   }
   static cudaError_t fs_step(const void *args, unsigned nblk, cudaStream_t s) {
@@ -160,13 +165,14 @@ struct Instance {
     o.to_f64 = &to_f64;
     o.from_f64 = &from_f64;
     o.totals = &totals;
-    o.fs_step = (S::id == StoreF32::id || S::id == StoreF64::id) ? &fs_step : nullptr;
+    o.fs_step = nullptr;
+    if constexpr (S::id == StoreF32::id || S::id == StoreF64::id) o.fs_step = &fs_step;
     o.batch_step = &batch_step;
     o.batch_advance = &batch_advance;
     o.batch_entry_bytes = sizeof(BatchEntry<Real>);
     o.tma_config = nullptr;
     o.tma_step = nullptr;
-    if constexpr (S::id != StoreF64::id) {  // static rows are staged as FP32
+    if constexpr (S::id == StoreF32::id) {  // FP32 populations and static rows
       o.tma_config = &tma_config;
       o.tma_step = &tma_step;
     }

@@ -99,14 +99,16 @@ __device__ __forceinline__ int solute_class(const CellGeo &g, uint32_t link, uns
 template <class S>
 __device__ __forceinline__ void gather_f(const typename S::T *__restrict__ fin, unsigned N,
                                          unsigned n, const CellGeo &g, uint32_t link,
-                                         unsigned f_wall, typename S::Real (&d)[Q]) {
+                                         unsigned f_wall, typename S::Real (&d)[Q],
+                                         const float *rf = nullptr) {
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int cls = fluid_class<q>(g, link, f_wall);
-    const typename S::T *p = (cls == PULL_BOUNCE)
-                                 ? fin + size_t(opp(q)) * N + n
-                                 : fin + size_t(q) * N + (long long)n + src_delta<q>(g);
+    const long long src = (cls == PULL_BOUNCE) ? (long long)n : (long long)n + src_delta<q>(g);
+    const typename S::T *p = (cls == PULL_BOUNCE) ? fin + size_t(opp(q)) * N + n
+                                                  : fin + size_t(q) * N + src;
     d[q] = S::template ld_f<q>(p);
+    if constexpr (S::kShift) d[q] += wq<typename S::Real>(q) * __ldg(rf + src);
   });
 }
 
@@ -313,12 +315,15 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       d[q] = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
+      if constexpr (S::kShift) d[q] += wq<Real>(q) * __ldg(a.rf_in + (long long)n + src_delta<q>(g));
     });
   } else {
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       const bool bb = fluid_class<q>(g, link, a.f_wall) == PULL_BOUNCE;
       d[q] = S::template ld_f<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g)));
+      if constexpr (S::kShift)
+        d[q] += wq<Real>(q) * __ldg(a.rf_in + (long long)n + (bb ? 0 : src_delta<q>(g)));
     });
   }
   // every load of the interior path is issued before any arithmetic, so a
@@ -338,6 +343,8 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
       Unroll<0, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+        if constexpr (S::kShift)
+          hh[SOLUTE ? q : 0] += wq<Real>(q) * __ldg(a.rh_in + (long long)n + src_delta<q>(g));
       });
     }
   }
@@ -361,20 +368,23 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
         constexpr int q = decltype(qc)::value;
         const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
         Real v;
+        // the cell's own reference term (FP16/BF16 storage), for own-cell reads
+        const Real own = S::kShift ? wq<Real>(q) * __ldg(a.rh_in + n) : Real(0);
         if (cls == PULL_CELL) {
           v = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+          if constexpr (S::kShift) v += wq<Real>(q) * __ldg(a.rh_in + (long long)n + src_delta<q>(g));
         } else if (cls == PULL_BOUNCE) {
-          v = S::template ld_h<opp(q)>(hb + int(opp(q) * N));
+          v = S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own;
         } else if (cls == PULL_INLET) {
           // entering through an inlet face: h^eq at C_in with the cell's
           // bare streamed velocity plus D grad(eps)/eps
           const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
           v = wq<Real>(q) * eps * a.C_in * (Real(1) + Real(3) * cv);
-          fin_acc += v - S::template ld_h<opp(q)>(hb + int(opp(q) * N));
+          fin_acc += v - (S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own);
         } else {
           // outlet: the cell's own post-collision value (zero gradient)
-          v = S::template ld_h<q>(hb + int(q * N));
-          fout_acc += S::template ld_h<opp(q)>(hb + int(opp(q) * N)) - v;
+          v = S::template ld_h<q>(hb + int(q * N)) + own;
+          fout_acc += (S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own) - v;
         }
         hh[SOLUTE ? q : 0] = v;
       });
@@ -407,8 +417,11 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
   }
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
-    S::template st_f<q>(fo + int(q * N), fc.template post<q>(d[q]));
+    Real v = fc.template post<q>(d[q]);
+    if constexpr (S::kShift) v -= wq<Real>(q) * drho;
+    S::template st_f<q>(fo + int(q * N), v);
   });
+  if constexpr (S::kShift) a.rf_out[n] = float(drho);
 
   if (SOLUTE) {
     T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
@@ -425,12 +438,15 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
       const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
       hsum += heq;
       const Real h = hh[SOLUTE ? q : 0];
-      S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd);
+      const Real shift = S::kShift ? wq<Real>(q) * sC : Real(0);
+      S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd - shift);
     });
     {
       const Real h = hh[0];
-      S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd);
+      const Real shift = S::kShift ? wq<Real>(0) * sC : Real(0);
+      S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd - shift);
     }
+    if constexpr (S::kShift) a.rh_out[n] = float(sC);
   }
   if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
 }
@@ -480,7 +496,7 @@ __global__ void __launch_bounds__(BLOCK) rhohat_kernel(const StepArgs<typename S
   }
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   Real d[Q];
-  gather_f<S>(static_cast<const typename S::T *>(a.f_in), a.N, n, g, link, a.f_wall, d);
+  gather_f<S>(static_cast<const typename S::T *>(a.f_in), a.N, n, g, link, a.f_wall, d, a.rf_in);
   Real s = Real(0);
   Unroll<0, Q>::run([&](auto qc) { s += d[decltype(qc)::value]; });
   rhohat[n] = Real(1) + s;
@@ -508,12 +524,21 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
   const bool solid = a.link && (__ldg(a.link + n) >> 31);
   const bool empty = in.type && in.type[n] == CELL_EMPTY;
   if (solid || empty) {
+    // absolute populations 0 (FP16/BF16: reference -1, remainders 0)
+    const Real shift = S::kShift ? Real(-1) : Real(0);
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
-      // absolute population 0
-      S::template st_f<q>(fout + size_t(q) * N + n, -wq<Real>(q));
-      S::template st_f<q>(fout2 + size_t(q) * N + n, -wq<Real>(q));
+      S::template st_f<q>(fout + size_t(q) * N + n, -wq<Real>(q) - wq<Real>(q) * shift);
+      S::template st_f<q>(fout2 + size_t(q) * N + n, -wq<Real>(q) - wq<Real>(q) * shift);
     });
+    if constexpr (S::kShift) {
+      a.rf_out[n] = -1.0f;
+      const_cast<float *>(a.rf_in)[n] = -1.0f;
+      if (SOLUTE) {
+        a.rh_out[n] = 0.0f;
+        const_cast<float *>(a.rh_in)[n] = 0.0f;
+      }
+    }
     if (SOLUTE) {
       Unroll<0, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -544,6 +569,8 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
   fc.st = (a.A != Real(0)) && fc.Fn > st_threshold<Real>();
   fc.stc = fc.st ? a.A * eps * tau : Real(0);
   fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+  Real devs[Q];
+  Real dsum = Real(0);
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     Real dev = fc.template feq_dev<q>();
@@ -551,18 +578,39 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
       const Real sc = Real(in.f_scale[size_t(q) * N + n]);
       dev = (dev + wq<Real>(q)) * sc - wq<Real>(q);
     }
-    S::template st_f<q>(fout + size_t(q) * N + n, dev);
-    S::template st_f<q>(fout2 + size_t(q) * N + n, dev);
+    devs[q] = dev;
+    dsum += dev;
   });
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const Real v = devs[q] - (S::kShift ? wq<Real>(q) * dsum : Real(0));
+    S::template st_f<q>(fout + size_t(q) * N + n, v);
+    S::template st_f<q>(fout2 + size_t(q) * N + n, v);
+  });
+  if constexpr (S::kShift) {
+    a.rf_out[n] = float(dsum);
+    const_cast<float *>(a.rf_in)[n] = float(dsum);
+  }
   if (SOLUTE) {
     const Real vs0 = u[0] + a.geps[n], vs1 = u[1] + a.geps[N + n], vs2 = u[2] + a.geps[2 * size_t(N) + n];
+    Real hs[Q];
+    Real hsum = Real(0);
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
-      const Real h = wq<Real>(q) * eps * C * (Real(1) + Real(3) * cv);
+      hs[q] = wq<Real>(q) * eps * C * (Real(1) + Real(3) * cv);
+      hsum += hs[q];
+    });
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real h = hs[q] - (S::kShift ? wq<Real>(q) * hsum : Real(0));
       S::template st_h<q>(static_cast<T *>(a.h_out) + size_t(q) * N + n, h);
       S::template st_h<q>(const_cast<T *>(static_cast<const T *>(a.h_in)) + size_t(q) * N + n, h);
     });
+    if constexpr (S::kShift) {
+      a.rh_out[n] = float(hsum);
+      const_cast<float *>(a.rh_in)[n] = float(hsum);
+    }
   }
   if (a.fields) write_fields(a.fields, N, n, rho, u, C, (tau - Real(0.5)) / Real(3));
 }
@@ -570,34 +618,52 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
 // ------------------------------------------------------------------------
 // Populations <-> absolute FP64, totals and the neighbour export.
 // ------------------------------------------------------------------------
+// ref: the per-cell references of FP16/BF16 storage (NULL otherwise)
 template <class S>
-__global__ void to_f64_kernel(const typename S::T *src, double *dst, unsigned N, int lattice) {
+__global__ void to_f64_kernel(const typename S::T *src, double *dst, unsigned N, int lattice,
+                              const float *ref) {
   const size_t i = size_t(blockIdx.x) * BLOCK + threadIdx.x;
   if (i >= size_t(Q) * N) return;
   const int q = int(i / N);
-  dst[i] = lattice == 0 ? S::to_f(src[i], q) : S::to_h(src[i], q);
+  const double r = ref ? double(ref[i % N]) : 0.0;
+  dst[i] = lattice == 0 ? S::to_f(src[i], q, r) : S::to_h(src[i], q, r);
+}
+
+// per cell: the reference of given FP64 populations (sum of f_q - w_q, or of h_q)
+static __global__ void ref_from_f64_kernel(const double *src, unsigned N, int lattice, float *ref) {
+  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  if (n >= N) return;
+  double s = 0.0;
+  for (int q = 0; q < Q; ++q) s += src[size_t(q) * N + n] - (lattice == 0 ? wq<double>(q) : 0.0);
+  ref[n] = float(s);
 }
 
 template <class S>
-__global__ void from_f64_kernel(const double *src, typename S::T *dst, unsigned N, int lattice) {
+__global__ void from_f64_kernel(const double *src, typename S::T *dst, unsigned N, int lattice,
+                                const float *ref) {
   const size_t i = size_t(blockIdx.x) * BLOCK + threadIdx.x;
   if (i >= size_t(Q) * N) return;
   const int q = int(i / N);
-  dst[i] = lattice == 0 ? S::from_f(src[i], q) : S::from_h(src[i], q);
+  const double r = ref ? double(ref[i % N]) : 0.0;
+  dst[i] = lattice == 0 ? S::from_f(src[i], q, r) : S::from_h(src[i], q, r);
 }
 
 // Per-block FP64 sums of the fluid mass and the solute over non-solid cells.
 template <class S>
 __global__ void __launch_bounds__(BLOCK) totals_kernel(const typename S::T *f, const typename S::T *h,
                                                        const uint32_t *link, unsigned N,
-                                                       double *partials) {
+                                                       double *partials, const float *rf,
+                                                       const float *rh) {
   __shared__ double sh[BLOCK][2];
   const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
   double m = 0.0, s = 0.0;
   if (n < N && !(link && (link[n] >> 31))) {
-    for (int q = 0; q < Q; ++q) m += S::to_f(f[size_t(q) * N + n], q);
-    if (h)
-      for (int q = 0; q < Q; ++q) s += S::to_h(h[size_t(q) * N + n], q);
+    const double r = rf ? double(rf[n]) : 0.0;
+    for (int q = 0; q < Q; ++q) m += S::to_f(f[size_t(q) * N + n], q, r);
+    if (h) {
+      const double r2 = rh ? double(rh[n]) : 0.0;
+      for (int q = 0; q < Q; ++q) s += S::to_h(h[size_t(q) * N + n], q, r2);
+    }
   }
   sh[threadIdx.x][0] = m;
   sh[threadIdx.x][1] = s;

@@ -18,10 +18,14 @@ struct StorageOps {
   cudaError_t (*init)(int kmode, bool solute, const void *args, const void *init_args,
                       unsigned nblk, cudaStream_t s);
   cudaError_t (*rhohat)(const void *args, void *rhohat, unsigned nblk, cudaStream_t s);
-  cudaError_t (*to_f64)(const void *src, double *dst, unsigned N, int lattice, cudaStream_t s);
-  cudaError_t (*from_f64)(const double *src, void *dst, unsigned N, int lattice, cudaStream_t s);
+  // ref / rf / rh: per-cell references of FP16/BF16 storage (ignored otherwise)
+  cudaError_t (*to_f64)(const void *src, double *dst, unsigned N, int lattice, const float *ref,
+                        cudaStream_t s);
+  cudaError_t (*from_f64)(const double *src, void *dst, unsigned N, int lattice, float *ref,
+                          cudaStream_t s);
   cudaError_t (*totals)(const void *f, const void *h, const uint32_t *link, unsigned N,
-                        double *partials, unsigned nblk, cudaStream_t s);
+                        double *partials, unsigned nblk, const float *rf, const float *rh,
+                        cudaStream_t s);
   // one free-surface step (six launches), FsArgs<Real>*; NULL when the
   // storage format has no free-surface build
   cudaError_t (*fs_step)(const void *fs_args, unsigned nblk, cudaStream_t s);
