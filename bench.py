@@ -231,7 +231,8 @@ def run_serving(args):
         reqs = serve.make_requests(stream, storage=storage, steps_scale=scale)
         be = serve.LibraryBackend(storage, keep_fields=False, batched=batched,
                                   admit_stream=admit_s, step_stream=step_s)
-        srv = serve.Server(be, budget_bytes=120 * 10 ** 9, chunk=args.chunk, max_resident=maxres)
+        srv = serve.Server(be, budget_bytes=120 * 10 ** 9, chunk=args.chunk, max_resident=maxres,
+                           fill_cells=(args.fill_cells or None) if batched else None)
         torch.cuda.synchronize()
         with ClockSampler(0) as clk:
             st = srv.run(reqs)
@@ -247,7 +248,8 @@ def run_serving(args):
         "config": {"workload": f"{n_req} requests, Poisson 50/s, sides 32..160, z-aspect 1..2, "
                                f"steps U(2000, 20000) x {scale}, 120 GB admission budget, "
                                f"chunk {args.chunk} steps, at most "
-                               f"{args.max_resident or 'budget-many'} lattices stepped together"},
+                               f"{args.max_resident or 'budget-many'} resident, oldest stepped "
+                               f"together up to {args.fill_cells or 'all'} cells"},
         "serving": res,
         "gpu_launches": None,
     }
@@ -269,7 +271,9 @@ def main():
     ap.add_argument("--steps-scale", type=float, default=0.02)
     ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--max-resident", type=int, default=0,
-                    help="serving: cap on lattices stepped together (0 = HBM budget only)")
+                    help="serving: cap on resident lattices (0 = HBM budget only)")
+    ap.add_argument("--fill-cells", type=int, default=4 * 1024 * 1024,
+                    help="serving: step the oldest lattices until this many cells (0 = all)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

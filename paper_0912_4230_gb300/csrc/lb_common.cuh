@@ -106,29 +106,32 @@ struct StoreF16 {
   using Real = float;
   static constexpr int id = 2;
   static constexpr bool kShift = true;
+  // remainders are stored times 2^12 (exact), which keeps the small ones of
+  // slow regions out of FP16's subnormal range; |g| up to 16 fits
+  static constexpr float kScale = 4096.0f;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) {
-    return __half2float(v) * wq<float>(q);
+    return __half2float(v) * (wq<float>(q) / kScale);
   }
   template <int q> __device__ __forceinline__ static Real cv_h(T v) {
-    return __half2float(v) * wq<float>(q);
+    return __half2float(v) * (wq<float>(q) / kScale);
   }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) {
-    return __half2float(__ldg(p)) * wq<float>(q);
+    return __half2float(__ldg(p)) * (wq<float>(q) / kScale);
   }
   template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) {
-    __stcs(p, __float2half_rn(v * float(inv_wq(q))));
+    __stcs(p, __float2half_rn(v * (float(inv_wq(q)) * kScale)));
   }
   template <int q> __device__ __forceinline__ static Real ld_h(const T *p) {
-    return __half2float(__ldg(p)) * wq<float>(q);
+    return __half2float(__ldg(p)) * (wq<float>(q) / kScale);
   }
   template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) {
-    __stcs(p, __float2half_rn(v * float(inv_wq(q))));
+    __stcs(p, __float2half_rn(v * (float(inv_wq(q)) * kScale)));
   }
   // with ref: f = w (g + ref) + w, h = w (g + ref)
-  __device__ static double to_f(T v, int q, double ref) { return (double(__half2float(v)) + ref) * wq<double>(q) + wq<double>(q); }
-  __device__ static T from_f(double f, int q, double ref) { return __float2half_rn(float((f - wq<double>(q)) * inv_wq(q) - ref)); }
-  __device__ static double to_h(T v, int q, double ref) { return (double(__half2float(v)) + ref) * wq<double>(q); }
-  __device__ static T from_h(double h, int q, double ref) { return __float2half_rn(float(h * inv_wq(q) - ref)); }
+  __device__ static double to_f(T v, int q, double ref) { return (double(__half2float(v)) / kScale + ref) * wq<double>(q) + wq<double>(q); }
+  __device__ static T from_f(double f, int q, double ref) { return __float2half_rn(float(((f - wq<double>(q)) * inv_wq(q) - ref) * kScale)); }
+  __device__ static double to_h(T v, int q, double ref) { return (double(__half2float(v)) / kScale + ref) * wq<double>(q); }
+  __device__ static T from_h(double h, int q, double ref) { return __float2half_rn(float((h * inv_wq(q) - ref) * kScale)); }
 };
 
 struct StoreBF16 {

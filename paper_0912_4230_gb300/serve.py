@@ -119,11 +119,16 @@ class Server:
 
     def __init__(self, backend, budget_bytes: int, chunk: int = 200,
                  clock: Callable[[], float] = time.perf_counter, sleep=time.sleep,
-                 max_resident: Optional[int] = None):
+                 max_resident: Optional[int] = None, fill_cells: Optional[int] = None):
+        """fill_cells: step, each chunk, only the oldest resident requests
+        whose lattices together reach this many cells (enough to fill the
+        GPU); the younger ones stay resident and join as the older finish.
+        None steps every resident request together."""
         self.backend = backend
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
         self.max_resident = max_resident
+        self.fill_cells = fill_cells
         self.clock = clock
         self.sleep = sleep
         self.log: List[dict] = []
@@ -154,9 +159,17 @@ class Server:
                 # nothing resident: wait for the next arrival
                 self.sleep(max(0.0, pending[0].arrival - now))
                 continue
-            n = min(self.chunk, min(r.remaining for r in active))
-            self.backend.step([r.handle for r in active], n)
-            for r in active:
+            stepping = active
+            if self.fill_cells is not None:
+                stepping, cells = [], 0
+                for r in active:          # arrival order
+                    stepping.append(r)
+                    cells += r.problem.N
+                    if cells >= self.fill_cells:
+                        break
+            n = min(self.chunk, min(r.remaining for r in stepping))
+            self.backend.step([r.handle for r in stepping], n)
+            for r in stepping:
                 r.remaining -= n
                 lups += n * r.problem.N
             still = []
@@ -169,7 +182,8 @@ class Server:
                     finished.append(r)
                 else:
                     still.append(r)
-            self.log.append(dict(t=self.clock() - t0, resident=len(active), steps=n, used=used))
+            self.log.append(dict(t=self.clock() - t0, resident=len(active), stepped=len(stepping),
+                                 steps=n, used=used))
             active = still
         wall = self.clock() - t0
         lat = np.array([r.latency for r in finished])

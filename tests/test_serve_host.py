@@ -105,3 +105,16 @@ def test_request_stream_matches_the_serving_workload():
     assert {r["nx"] for r in rs} <= {32, 48, 64, 96, 128, 160}
     assert all(r["nx"] <= r["nz"] <= 2 * r["nx"] + 1 for r in rs)
     assert all(2000 <= r["steps"] <= 20000 for r in rs)
+
+
+def test_fill_policy_steps_oldest_first():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    # three 1000-cell lattices resident together; fill_cells = 1500 steps two at a time
+    reqs = _reqs([(0.0, 10, 200), (0.0, 10, 200), (0.0, 10, 200)])
+    srv = serve.Server(be, budget_bytes=10 ** 9, chunk=100, clock=clk, sleep=clk.sleep,
+                       fill_cells=1500)
+    st = srv.run(reqs)
+    assert st["requests"] == 3
+    assert max(be.batches) == 2
+    assert reqs[2].done > reqs[0].done and reqs[2].done > reqs[1].done
