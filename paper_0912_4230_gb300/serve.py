@@ -16,6 +16,7 @@ library; tests of the host-side logic use a fake backend on the CPU.
 from __future__ import annotations
 
 import dataclasses
+import threading
 import time
 from typing import Callable, List, Optional
 
@@ -119,16 +120,20 @@ class Server:
 
     def __init__(self, backend, budget_bytes: int, chunk: int = 200,
                  clock: Callable[[], float] = time.perf_counter, sleep=time.sleep,
-                 max_resident: Optional[int] = None, fill_cells: Optional[int] = None):
+                 max_resident: Optional[int] = None, fill_cells: Optional[int] = None,
+                 admit_in_thread: bool = False):
         """fill_cells: step, each chunk, only the oldest resident requests
         whose lattices together reach this many cells (enough to fill the
         GPU); the younger ones stay resident and join as the older finish.
-        None steps every resident request together."""
+        None steps every resident request together.
+        admit_in_thread: create lattices on a background thread while the
+        resident ones step (the library calls release the GIL)."""
         self.backend = backend
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
         self.max_resident = max_resident
         self.fill_cells = fill_cells
+        self.admit_in_thread = admit_in_thread
         self.clock = clock
         self.sleep = sleep
         self.log: List[dict] = []
@@ -142,23 +147,60 @@ class Server:
                 raise ValueError(f"request {r.id} needs {r.bytes} bytes, above the whole budget")
         active: List[Request] = []
         finished: List[Request] = []
-        used = 0
+        self._used = 0
         t0 = self.clock()
         lups = 0
-        while pending or active:
+        lock = threading.Condition()
+        ready: List[Request] = []
+        admitter = None
+        if self.admit_in_thread:
+            def admit_loop():
+                while pending:
+                    r = pending[0]
+                    wait = r.arrival - (self.clock() - t0)
+                    if wait > 0:
+                        self.sleep(wait)
+                    with lock:
+                        while (self._used + r.bytes > self.budget or
+                               (self.max_resident is not None and
+                                len(active) + len(ready) >= self.max_resident)):
+                            lock.wait(0.01)
+                        self._used += r.bytes
+                    r.handle = self.backend.admit(r.problem)
+                    r.admitted = self.clock() - t0
+                    with lock:
+                        pending.pop(0)
+                        ready.append(r)
+                        lock.notify_all()
+            admitter = threading.Thread(target=admit_loop, daemon=True)
+            admitter.start()
+        while True:
             now = self.clock() - t0
-            # admit, in arrival order, every arrived request that fits
-            while (pending and pending[0].arrival <= now and used + pending[0].bytes <= self.budget
-                   and (self.max_resident is None or len(active) < self.max_resident)):
-                r = pending.pop(0)
-                r.handle = self.backend.admit(r.problem)
-                r.admitted = self.clock() - t0
-                used += r.bytes
-                active.append(r)
-            if not active:
-                # nothing resident: wait for the next arrival
-                self.sleep(max(0.0, pending[0].arrival - now))
-                continue
+            if admitter is not None:
+                with lock:
+                    active.extend(ready)
+                    ready.clear()
+                    if not active:
+                        if not pending and not ready:
+                            break
+                        lock.wait(0.005)
+                        continue
+            else:
+                if not pending and not active:
+                    break
+                # admit, in arrival order, every arrived request that fits
+                while (pending and pending[0].arrival <= now
+                       and self._used + pending[0].bytes <= self.budget
+                       and (self.max_resident is None or len(active) < self.max_resident)):
+                    r = pending.pop(0)
+                    r.handle = self.backend.admit(r.problem)
+                    r.admitted = self.clock() - t0
+                    self._used += r.bytes
+                    active.append(r)
+                if not active:
+                    # nothing resident: wait for the next arrival
+                    self.sleep(max(0.0, pending[0].arrival - now))
+                    continue
             stepping = active
             if self.fill_cells is not None:
                 stepping, cells = [], 0
@@ -178,13 +220,18 @@ class Server:
                     r.result = self.backend.finish(r.handle)
                     r.handle = None
                     r.done = self.clock() - t0
-                    used -= r.bytes
+                    with lock:
+                        self._used -= r.bytes
+                        lock.notify_all()
                     finished.append(r)
                 else:
                     still.append(r)
             self.log.append(dict(t=self.clock() - t0, resident=len(active), stepped=len(stepping),
-                                 steps=n, used=used))
-            active = still
+                                 steps=n, used=self._used))
+            with lock:
+                active[:] = still
+        if admitter is not None:
+            admitter.join()
         wall = self.clock() - t0
         lat = np.array([r.latency for r in finished])
         wait = np.array([r.wait for r in finished])

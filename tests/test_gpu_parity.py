@@ -241,3 +241,29 @@ def test_row_pipelined_kernel_rejects_other_shapes():
     with pytest.raises(lb.LbError) as e:
         lb.Lattice(p, storage="fp32", kernel="rows")
     assert e.value.code == lb.LB_EUNSUPPORTED
+
+
+def test_fp32_long_run_parity():
+    """3000 steps of the miscible medium (32x32x48 crop): the FP32 path stays
+    inside the tolerances over a long run (no systematic drift of C)."""
+    p = W.crop(W.miscible(64, 64, 64, seed=0), 16, 0, 0, 32, 32, 48)
+    g, o = run_both(p, 3000, "fp32", threads=0)
+    err = compare(g, o, p, "fp32")
+    assert err["C"] < 2e-6
+
+
+def test_fp16_long_run_error():
+    """FP16 storage with per-cell FP32 references, 2000 steps of the rotated
+    SPD medium (24^3 crop): velocity within 1e-3 of the oracle, mass drift
+    within 1e-6."""
+    big = W.precision(64, 64, 64, storage="fp16")
+    p = W.crop(big, 16, 0, 8, 24, 24, 24)
+    g = lb.Lattice(p, storage="fp16")
+    m0 = g.reduce()[0]
+    g.step(2000)
+    o = O.Oracle(p)
+    o.step(2000)
+    _, u, _, _ = g.fields()
+    _, ru, _, _ = o.fields()
+    assert np.abs(u - ru).max() / np.abs(ru).max() <= 1e-3
+    assert abs(g.reduce()[0] / m0 - 1) <= 1e-6

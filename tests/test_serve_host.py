@@ -118,3 +118,43 @@ def test_fill_policy_steps_oldest_first():
     assert st["requests"] == 3
     assert max(be.batches) == 2
     assert reqs[2].done > reqs[0].done and reqs[2].done > reqs[1].done
+
+
+class SleepBackend:
+    """Real-time fake: admission and steps take wall time."""
+
+    def __init__(self):
+        import threading
+        self.lock = threading.Lock()
+        self.resident = 0
+        self.max_resident = 0
+
+    def bytes(self, prob):
+        return prob.N * 100
+
+    def admit(self, prob):
+        import time
+        time.sleep(0.002)
+        with self.lock:
+            self.resident += 1
+            self.max_resident = max(self.max_resident, self.resident)
+        return prob.N
+
+    def step(self, handles, n):
+        import time
+        time.sleep(1e-5 * n)
+
+    def finish(self, handle):
+        with self.lock:
+            self.resident -= 1
+        return "ok"
+
+
+def test_admission_thread_overlaps_and_respects_budget():
+    be = SleepBackend()
+    reqs = _reqs([(0.0, 10, 300), (0.001, 10, 200), (0.002, 10, 100), (0.05, 10, 100)])
+    srv = serve.Server(be, budget_bytes=2 * 1000 * 100, chunk=50, admit_in_thread=True)
+    st = srv.run(reqs)
+    assert st["requests"] == 4
+    assert be.max_resident <= 2 and be.resident == 0
+    assert all(r.done >= r.admitted >= r.arrival for r in reqs)
