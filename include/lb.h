@@ -161,6 +161,18 @@ int lb_get_populations(lb_ctx *ctx, double *f, double *h);
  * Enqueued asynchronously; launch errors return LB_ECUDA. */
 int lb_step(lb_ctx *ctx, int64_t n);
 
+/* Pick the step kernel's launch shape by timing (no counterpart in the paper):
+ * rows of 32, 64 or 128 threads per block for the per-cell kernel, and the
+ * row-pipelined kernel where the lattice allows it; each candidate runs reps
+ * side-effect-free launches (input buffer to output buffer without swapping,
+ * no flux accumulation, no checks, no field export), so the state and t are
+ * unchanged. The fastest is kept for later lb_step calls. *choice (may be
+ * NULL) receives the row width, or 256 for the row-pipelined kernel, or 0 when
+ * nothing was tuned (free surface or surface tension keep fixed launches).
+ * Results of a step do not depend on the choice beyond the order of the FP64
+ * flux sums. */
+int lb_autotune(lb_ctx *ctx, int32_t reps, int32_t *choice);
+
 /* Advance several lattices by the same n steps in one persistent launch per
  * step (a work list of every lattice's cell blocks), captured in a CUDA graph
  * when the first context's stream is not the legacy default stream. Each

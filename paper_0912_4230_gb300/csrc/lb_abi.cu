@@ -33,7 +33,8 @@ struct lb_ctx {
   unsigned N = 0, nblk = 0;
   dim3 sgrid, sblock;  // launch shape of the per-cell step kernel
   unsigned nwarps = 0;   // flux slots (one per warp of the step launch)
-  bool use_tma = false;  // row-pipelined step kernel
+  bool use_tma = false;  // row-pipelined step kernel in use
+  bool tma_ok = false;   // ... and available for this lattice
   unsigned tma_grid = 0, tma_threads = 0;
   size_t tma_smem = 0;
   int kmode = KM_NONE;
@@ -291,6 +292,13 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     c->sblock = dim3(bx, STEP_BLOCK / bx, 1);
     c->sgrid = dim3((dom->nx + bx - 1) / bx, (dom->ny + c->sblock.y - 1) / c->sblock.y, dom->nz);
     c->nwarps = c->sgrid.x * c->sgrid.y * c->sgrid.z * (STEP_BLOCK / 32);
+    // flux slots for every launch shape the autotuner may pick
+    for (unsigned cbx = 32; cbx <= unsigned(STEP_BLOCK); cbx *= 2) {
+      const unsigned cby = STEP_BLOCK / cbx;
+      const unsigned w = ((dom->nx + cbx - 1) / cbx) * ((dom->ny + cby - 1) / cby) * dom->nz *
+                         (STEP_BLOCK / 32);
+      c->nwarps = std::max(c->nwarps, w);
+    }
   }
   c->solute = prm->solute != 0;
   c->fs = prm->free_surface != 0;
@@ -390,7 +398,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   // row-pipelined kernel: eligible shapes only; grid = resident blocks of all SMs
   // (automatic selection keeps the per-cell kernel: on GB300 at 128^3 it is
   // 2x faster than this row-pipelined form, which stays available on request)
-  if (prm->kernel == 2 && !c->fs && ops->tma_config) {
+  if (prm->kernel != 1 && !c->fs && ops->tma_config) {
     int bps = 0, sms = 0, dev = 0;
     if (ops->tma_config(c->kmode, c->solute, unsigned(dom->nx), &c->tma_smem, &c->tma_threads,
                         &bps) &&
@@ -398,7 +406,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
       const unsigned rows = unsigned(dom->ny) * unsigned(dom->nz);
       c->tma_grid = std::min(rows, unsigned(bps) * unsigned(sms));
-      c->use_tma = true;
+      c->tma_ok = true;
+      c->use_tma = prm->kernel == 2;
       c->nwarps = std::max(c->nwarps, c->tma_grid * unsigned(dom->nx / 32));
     }
     cudaGetLastError();
@@ -646,6 +655,81 @@ int lb_step_batch(lb_ctx *const *ctxs, int32_t n, int64_t steps) {
   }
   if (steps == 0) return LB_OK;
   return c0->ops->fp64 ? step_batch_t<double>(ctxs, n, steps) : step_batch_t<float>(ctxs, n, steps);
+}
+
+int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {
+  if (!c) return LB_EINVAL;
+  if (reps < 1) reps = 1;
+  if (c->fs) {  // the free surface has its own fixed launches
+    if (choice) *choice = 0;
+    return LB_OK;
+  }
+  struct Cand {
+    bool tma;
+    unsigned bx;
+  };
+  std::vector<Cand> cands;
+  for (unsigned bx = 32; bx <= unsigned(STEP_BLOCK); bx *= 2) cands.push_back({false, bx});
+  if (c->tma_ok) cands.push_back({true, 0});
+  cudaEvent_t e0, e1;
+  CK(c, cudaEventCreate(&e0));
+  CK(c, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_i = -1;
+  const dim3 keep_grid = c->sgrid, keep_block = c->sblock;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const Cand &cd = cands[i];
+    const dim3 blk(cd.bx ? cd.bx : 1, cd.bx ? STEP_BLOCK / cd.bx : 1, 1);
+    const dim3 grd(cd.bx ? (c->dom.nx + blk.x - 1) / blk.x : 1,
+                   cd.bx ? (c->dom.ny + blk.y - 1) / blk.y : 1, c->dom.nz);
+    // side-effect free timing launches: input buffer -> output buffer without
+    // swapping, no flux accumulation, no checks, no field export
+    auto launch = [&]() -> int {
+      return with_args(c, [&](void *args, auto &a) {
+        a.t = c->t + 1;
+        a.flux = 0;
+        a.reduce = 0;
+        a.fields = nullptr;
+        if (cd.tma)
+          CK(c, c->ops->tma_step(c->kmode, c->solute, args, c->tma_grid, c->tma_threads,
+                                 c->tma_smem, c->stream));
+        else
+          CK(c, c->ops->step(c->kmode, c->solute, args, grd, blk, c->stream));
+        return int(LB_OK);
+      });
+    };
+    if (c->prm.A != 0.0) break;  // surface tension: the pre-pass shapes stay fixed
+    int rc = launch();  // warm-up
+    if (rc != LB_OK) return rc;
+    CK(c, cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < reps && rc == LB_OK; ++r) rc = launch();
+    if (rc != LB_OK) return rc;
+    CK(c, cudaEventRecord(e1, c->stream));
+    CK(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(c, cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_i = int(i);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_i < 0) {
+    c->sgrid = keep_grid;
+    c->sblock = keep_block;
+    if (choice) *choice = 0;
+    return LB_OK;
+  }
+  const Cand &w = cands[best_i];
+  c->use_tma = w.tma;
+  if (!w.tma) {
+    c->sblock = dim3(w.bx, STEP_BLOCK / w.bx, 1);
+    c->sgrid = dim3((c->dom.nx + w.bx - 1) / w.bx, (c->dom.ny + c->sblock.y - 1) / c->sblock.y,
+                    c->dom.nz);
+  }
+  if (choice) *choice = w.tma ? 256 : int(w.bx);
+  return LB_OK;
 }
 
 int lb_fields(lb_ctx *c, float *rho, float *u, float *C, float *nu) {

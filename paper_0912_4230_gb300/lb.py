@@ -29,7 +29,7 @@ STORE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_get_populations",
            "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
            "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
-           "lb_totals_noalloc", "lb_step_batch"]
+           "lb_totals_noalloc", "lb_step_batch", "lb_autotune"]
 
 
 class LbError(RuntimeError):
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
     L._ALLOC, L._FREE = ALLOC, FREE
     L.lb_totals_noalloc.argtypes = [vp, vp, vp, c_int64, vp, vp]
     L.lb_step_batch.argtypes = [vp, c_int32, c_int64]
+    L.lb_autotune.argtypes = [vp, c_int32, vp]
     _lib = L
     return L
 
@@ -136,6 +137,14 @@ def lb_get_populations(ctx, f=None, h=None):
 
 def lb_step(ctx, n: int):
     _check(load().lb_step(ctx, int(n)), ctx)
+
+
+def lb_autotune(ctx, reps: int = 5) -> int:
+    """Time the candidate launch shapes and keep the fastest; returns the
+    choice (row width, 256 = row-pipelined, 0 = not tuned)."""
+    ch = c_int32()
+    _check(load().lb_autotune(ctx, int(reps), ctypes.byref(ch)), ctx)
+    return ch.value
 
 
 def lb_step_batch(ctxs, n_steps: int):

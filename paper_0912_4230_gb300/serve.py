@@ -88,14 +88,25 @@ class LibraryBackend:
                             bool(prob.params.get("solute")), kr)
 
     def admit(self, prob):
+        """Create and initialise a lattice (may run on a background thread)."""
         if self.admit_stream is None:
             return self.lb.Lattice(prob, storage=self.storage, kernel="cell", stream=self.stream)
+        import torch
         self.lb.lb_set_stream(None, self.admit_stream.cuda_stream)
         h = self.lb.Lattice(prob, storage=self.storage, kernel="cell",
                             stream=self.admit_stream.cuda_stream)
-        self.step_stream.wait_stream(self.admit_stream)
-        self.lb.lb_set_stream(h.ctx, self.step_stream.cuda_stream)
+        h.ready_event = torch.cuda.Event()
+        h.ready_event.record(self.admit_stream)
         return h
+
+    def activate(self, handle):
+        """Before a lattice's first step (on the stepping thread, outside any
+        graph capture): the step stream waits for its initialisation."""
+        ev = getattr(handle, "ready_event", None)
+        if ev is not None:
+            self.step_stream.wait_event(ev)
+            self.lb.lb_set_stream(handle.ctx, self.step_stream.cuda_stream)
+            handle.ready_event = None
 
     def step(self, handles, n: int):
         if self.batched:
@@ -178,6 +189,9 @@ class Server:
             now = self.clock() - t0
             if admitter is not None:
                 with lock:
+                    for r in ready:
+                        if hasattr(self.backend, "activate"):
+                            self.backend.activate(r.handle)
                     active.extend(ready)
                     ready.clear()
                     if not active:
@@ -194,6 +208,8 @@ class Server:
                        and (self.max_resident is None or len(active) < self.max_resident)):
                     r = pending.pop(0)
                     r.handle = self.backend.admit(r.problem)
+                    if hasattr(self.backend, "activate"):
+                        self.backend.activate(r.handle)
                     r.admitted = self.clock() - t0
                     self._used += r.bytes
                     active.append(r)

@@ -267,3 +267,20 @@ def test_fp16_long_run_error():
     _, ru, _, _ = o.fields()
     assert np.abs(u - ru).max() / np.abs(ru).max() <= 1e-3
     assert abs(g.reduce()[0] / m0 - 1) <= 1e-6
+
+
+def test_autotune_leaves_state_and_picks_a_shape():
+    p = W.miscible(128, 16, 12, seed=4)
+    g = lb.Lattice(p, storage="fp32", check_every=1)
+    g.step(3)
+    f0, h0 = g.populations()
+    r0 = g.reduce()
+    choice = lb.lb_autotune(g.ctx, 3)
+    assert choice in (32, 64, 128, 256)
+    f1, h1 = g.populations()
+    assert np.array_equal(f0, f1) and np.array_equal(h0, h1)
+    assert np.array_equal(r0, g.reduce()) and g.t == 3
+    g.step(40)
+    o = O.Oracle(p)
+    o.step(43)
+    compare(g, o, p, "fp32")
