@@ -280,6 +280,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="miscible")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "rows"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--steps-scale", type=float, default=0.02)
     ap.add_argument("--chunk", type=int, default=100)
@@ -315,6 +316,9 @@ def main():
     lat = lb.Lattice(prob, storage=storage, check_every=1, stream=stream.cuda_stream,
                      kernel=args.kernel)
     N = prob.N
+    choice = 0
+    if not args.no_autotune and args.kernel == "auto":
+        choice = lb.lb_autotune(lat.ctx, 5)   # launch shape picked by timing, state unchanged
     for _ in range(args.warmup):
         lat.step(1)
     torch.cuda.synchronize()
@@ -391,7 +395,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind,
-                     "kernel": "step_kernel (one launch per step)",
+                     "kernel": ("tma_step_kernel (row-pipelined)" if choice == 256 else
+                                f"step_kernel, rows of {choice or 'default'} threads"),
                      "kernel_ms": kern_ms, "algorithmic_bytes_per_lup": algo,
                      "units_per_step": units},
         "cpu_baseline": cpu,
