@@ -272,14 +272,14 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-iters", type=int, default=5)
     ap.add_argument("--e2e-inner", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="miscible")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "rows"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "rows", "staged"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--steps-scale", type=float, default=0.02)
@@ -324,22 +324,22 @@ def main():
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(K)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # K steps in one lb_step call: K launches of the step kernel (the
+        # fields are exported by the last one only), nothing else on the stream
         start.record(stream)
-        for k in range(K):
-            ev[k][0].record(stream)
-            lat.step(1)
-            ev[k][1].record(stream)
+        lat.step(K)
         stop.record(stream)
         torch.cuda.synchronize()
     barrier(ws)
     total_ms = start.elapsed_time(stop)
-    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    # the step kernel is the only launch in the region (the free-surface step:
+    # its six kernels), so its average launch duration is at most the region's
+    # time over K; that bound (launch gaps included) is what the roofline uses
+    kern_ms = total_ms / K
     lat.sync()  # raises on a non-finite reduction
     total_ms = max_over_ranks(ws, total_ms)
     kern_ms = max_over_ranks(ws, kern_ms)
@@ -395,8 +395,12 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind,
-                     "kernel": ("tma_step_kernel (row-pipelined)" if choice == 256 else
+                     "kernel": ("six free-surface kernels of one step" if prob.cell_type is not None
+                                else "tma_step_kernel (row-pipelined)" if choice == 256 else
+                                f"pipe_step_kernel (row-staged), rows of {choice - 1000} threads"
+                                if choice > 1000 else
                                 f"step_kernel, rows of {choice or 'default'} threads"),
+                     "kernel_ms_from": "CUDA events around the K launches / K",
                      "kernel_ms": kern_ms, "algorithmic_bytes_per_lup": algo,
                      "units_per_step": units},
         "cpu_baseline": cpu,

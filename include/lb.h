@@ -101,15 +101,19 @@ typedef struct {
   int32_t free_surface; /* 1: free-surface cell types and liquid mass (Section 3);
                            requires solute = 0 and no permeability (K6 = NULL) */
   int32_t storage;      /* LB_STORE_* */
-  int32_t check_every;  /* every this many steps the step kernel also forms the
-                           FP64 mass and solute totals and checks them for
+  int32_t check_every;  /* every this many steps the step kernel also sums each
+                           warp's mass and solute and checks the sums for
                            NaN/Inf (0 = never) */
   int32_t kernel;       /* step kernel: 0 automatic (= 1), 1 one thread per cell
                            with direct loads, 2 row-pipelined with shared-memory
                            staging by bulk asynchronous copies (needs the solute
-                           lattice, a permeability field, nx = 128 or 256,
-                           FP32/FP16/BF16 storage, no free surface; else
-                           LB_EUNSUPPORTED). Both compute the same arithmetic. */
+                           lattice, a permeability field, nx = 128 or 256, FP32
+                           storage, no free surface), 3 row-staged: persistent
+                           blocks of rows, each thread copying its next cell's
+                           inputs to shared memory (cp.async) while it computes
+                           the current one (FP32/FP64 storage, no free surface).
+                           Kernels 2 and 3 return LB_EUNSUPPORTED where they do
+                           not apply. All compute the same arithmetic. */
 } lb_params;
 
 /* Create a lattice (flowchart of Section 4: the porosity field, the
@@ -161,16 +165,18 @@ int lb_get_populations(lb_ctx *ctx, double *f, double *h);
  * Enqueued asynchronously; launch errors return LB_ECUDA. */
 int lb_step(lb_ctx *ctx, int64_t n);
 
-/* Pick the step kernel's launch shape by timing (no counterpart in the paper):
- * rows of 32, 64 or 128 threads per block for the per-cell kernel, and the
- * row-pipelined kernel where the lattice allows it; each candidate runs reps
- * side-effect-free launches (input buffer to output buffer without swapping,
- * no flux accumulation, no checks, no field export), so the state and t are
- * unchanged. The fastest is kept for later lb_step calls. *choice (may be
- * NULL) receives the row width, or 256 for the row-pipelined kernel, or 0 when
- * nothing was tuned (free surface or surface tension keep fixed launches).
- * Results of a step do not depend on the choice beyond the order of the FP64
- * flux sums. */
+/* Pick the step kernel and its launch shape by timing (no counterpart in the
+ * paper): the per-cell kernel with rows of 32, 64 or 128 threads per block,
+ * the row-staged kernel with rows of 32, 64 or 128 threads (FP32/FP64
+ * storage), and the row-pipelined kernel where the lattice allows it. Each
+ * candidate runs reps side-effect-free launches (input buffer to output
+ * buffer without swapping, no flux accumulation, no checks, no field export),
+ * so the state and t are unchanged. The fastest is kept for later lb_step
+ * calls. *choice (may be NULL) receives the row width for the per-cell
+ * kernel, 1000 + the row width for the row-staged kernel, 256 for the
+ * row-pipelined kernel, or 0 when nothing was tuned (free surface or surface
+ * tension keep fixed launches). Results of a step do not depend on the choice
+ * beyond the order of the FP64 flux sums. */
 int lb_autotune(lb_ctx *ctx, int32_t reps, int32_t *choice);
 
 /* Advance several lattices by the same n steps in one persistent launch per

@@ -37,6 +37,11 @@ struct lb_ctx {
   bool tma_ok = false;   // ... and available for this lattice
   unsigned tma_grid = 0, tma_threads = 0;
   size_t tma_smem = 0;
+  // row-staged persistent kernel: in use when pipe.bx != 0
+  struct PipeShape {
+    unsigned bx = 0, grid = 0, gxr = 0, items = 0;
+    size_t smem = 0;
+  } pipe;
   int kmode = KM_NONE;
   bool solute = false, fs = false, has_solid = false, flux = false;
   unsigned f_wall = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
@@ -209,6 +214,25 @@ int check_status(lb_ctx *c) {
   return LB_OK;
 }
 
+// Launch shape of the row-staged kernel for rows of bx threads: the grid is
+// the resident blocks of all SMs, at most one block per row.
+bool pipe_shape(const lb_ctx *c, unsigned bx, lb_ctx::PipeShape *ps) {
+  if (!c->ops->pipe_config) return false;
+  size_t smem = 0;
+  int bps = 0, sms = 0, dev = 0;
+  const bool ok = c->ops->pipe_config(c->kmode, c->solute, bx, &smem, &bps) &&
+                  cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  cudaGetLastError();
+  if (!ok) return false;
+  ps->bx = bx;
+  ps->gxr = (unsigned(c->dom.nx) + bx - 1) / bx;
+  ps->items = ps->gxr * unsigned(c->dom.ny) * unsigned(c->dom.nz);
+  ps->grid = std::min(ps->items, unsigned(bps) * unsigned(sms));
+  ps->smem = smem;
+  return true;
+}
+
 bool valid_faces(const int32_t (&k)[3][2], bool fluid) {
   for (int a = 0; a < 3; ++a) {
     for (int s = 0; s < 2; ++s) {
@@ -262,7 +286,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (prm->free_surface && (prm->solute || K6))
     return fail(nullptr, LB_EUNSUPPORTED, "free surface with solute or permeability");
   if (prm->check_every < 0) return fail(nullptr, LB_EINVAL, "check_every < 0");
-  if (prm->kernel < 0 || prm->kernel > 2) return fail(nullptr, LB_EINVAL, "kernel");
+  if (prm->kernel < 0 || prm->kernel > 3) return fail(nullptr, LB_EINVAL, "kernel");
   const StorageOps *ops = nullptr;
   switch (prm->storage) {
     case LB_STORE_FP32: ops = &ops_f32(); break;
@@ -414,6 +438,18 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   }
   if (prm->kernel == 2 && !c->use_tma)
     return bail(fail(c, LB_EUNSUPPORTED, "row-pipelined kernel: this lattice shape or storage"));
+  // row-staged kernel: flux slots for every row width it may run with
+  if (!c->fs && ops->pipe_config) {
+    for (unsigned bx = 32; bx <= unsigned(STEP_BLOCK); bx *= 2) {
+      lb_ctx::PipeShape ps;
+      if (pipe_shape(c, bx, &ps)) c->nwarps = std::max(c->nwarps, ps.grid * (bx / 32));
+    }
+  }
+  if (prm->kernel == 3) {
+    const unsigned bx = c->sblock.x;
+    if (c->fs || !ops->pipe_config || !pipe_shape(c, bx, &c->pipe))
+      return bail(fail(c, LB_EUNSUPPORTED, "row-staged kernel: this lattice or storage"));
+  }
   c->flux_slots = static_cast<double *>(dev_alloc(c, size_t(c->nwarps) * 2 * sizeof(double)));
   if (!c->flux_slots) return bail(fail(c, LB_ENOMEM, "flux slots"));
   sa.eps = c->eps;
@@ -532,6 +568,9 @@ int lb_step(lb_ctx *c, int64_t n) {
       if (c->use_tma)
         CK(c, c->ops->tma_step(c->kmode, c->solute, args, c->tma_grid, c->tma_threads, c->tma_smem,
                                c->stream));
+      else if (c->pipe.bx)
+        CK(c, c->ops->pipe_step(c->kmode, c->solute, args, c->pipe.grid, c->pipe.bx,
+                                c->pipe.smem, c->pipe.gxr, c->pipe.items, c->stream));
       else
         CK(c, c->ops->step(c->kmode, c->solute, args, c->sgrid, c->sblock, c->stream));
       return int(LB_OK);
@@ -660,26 +699,30 @@ int lb_step_batch(lb_ctx *const *ctxs, int32_t n, int64_t steps) {
 int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {
   if (!c) return LB_EINVAL;
   if (reps < 1) reps = 1;
-  if (c->fs) {  // the free surface has its own fixed launches
-    if (choice) *choice = 0;
-    return LB_OK;
-  }
+  if (choice) *choice = 0;
+  if (c->fs || c->prm.A != 0.0) return LB_OK;  // fixed launches (free surface, surface tension)
+  enum Kind { CELL, ROWS, STAGED };
   struct Cand {
-    bool tma;
+    Kind kind;
     unsigned bx;
+    lb_ctx::PipeShape ps;
   };
   std::vector<Cand> cands;
-  for (unsigned bx = 32; bx <= unsigned(STEP_BLOCK); bx *= 2) cands.push_back({false, bx});
-  if (c->tma_ok) cands.push_back({true, 0});
+  for (unsigned bx = 32; bx <= unsigned(STEP_BLOCK); bx *= 2) cands.push_back({CELL, bx, {}});
+  if (c->tma_ok) cands.push_back({ROWS, 0, {}});
+  for (unsigned bx = 32; bx <= unsigned(STEP_BLOCK); bx *= 2) {
+    Cand cd{STAGED, bx, {}};
+    if (pipe_shape(c, bx, &cd.ps)) cands.push_back(cd);
+  }
   cudaEvent_t e0, e1;
   CK(c, cudaEventCreate(&e0));
   CK(c, cudaEventCreate(&e1));
   float best = 1e30f;
   int best_i = -1;
-  const dim3 keep_grid = c->sgrid, keep_block = c->sblock;
-  for (size_t i = 0; i < cands.size(); ++i) {
+  int rc = LB_OK;
+  for (size_t i = 0; i < cands.size() && rc == LB_OK; ++i) {
     const Cand &cd = cands[i];
-    const dim3 blk(cd.bx ? cd.bx : 1, cd.bx ? STEP_BLOCK / cd.bx : 1, 1);
+    const dim3 blk(cd.bx, STEP_BLOCK / std::max(cd.bx, 1u), 1);
     const dim3 grd(cd.bx ? (c->dom.nx + blk.x - 1) / blk.x : 1,
                    cd.bx ? (c->dom.ny + blk.y - 1) / blk.y : 1, c->dom.nz);
     // side-effect free timing launches: input buffer -> output buffer without
@@ -690,24 +733,31 @@ int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {
         a.flux = 0;
         a.reduce = 0;
         a.fields = nullptr;
-        if (cd.tma)
+        if (cd.kind == ROWS)
           CK(c, c->ops->tma_step(c->kmode, c->solute, args, c->tma_grid, c->tma_threads,
                                  c->tma_smem, c->stream));
+        else if (cd.kind == STAGED)
+          CK(c, c->ops->pipe_step(c->kmode, c->solute, args, cd.ps.grid, cd.ps.bx, cd.ps.smem,
+                                  cd.ps.gxr, cd.ps.items, c->stream));
         else
           CK(c, c->ops->step(c->kmode, c->solute, args, grd, blk, c->stream));
         return int(LB_OK);
       });
     };
-    if (c->prm.A != 0.0) break;  // surface tension: the pre-pass shapes stay fixed
-    int rc = launch();  // warm-up
-    if (rc != LB_OK) return rc;
-    CK(c, cudaEventRecord(e0, c->stream));
+    rc = launch();  // warm-up
+    if (rc != LB_OK) break;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
+      rc = fail(c, LB_ECUDA, "autotune event");
+      break;
+    }
     for (int r = 0; r < reps && rc == LB_OK; ++r) rc = launch();
-    if (rc != LB_OK) return rc;
-    CK(c, cudaEventRecord(e1, c->stream));
-    CK(c, cudaEventSynchronize(e1));
+    if (rc != LB_OK) break;
     float ms = 0.f;
-    CK(c, cudaEventElapsedTime(&ms, e0, e1));
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(c, LB_ECUDA, "autotune timing");
+      break;
+    }
     if (ms < best) {
       best = ms;
       best_i = int(i);
@@ -715,20 +765,16 @@ int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best_i < 0) {
-    c->sgrid = keep_grid;
-    c->sblock = keep_block;
-    if (choice) *choice = 0;
-    return LB_OK;
-  }
+  if (rc != LB_OK || best_i < 0) return rc;
   const Cand &w = cands[best_i];
-  c->use_tma = w.tma;
-  if (!w.tma) {
+  c->use_tma = w.kind == ROWS;
+  c->pipe = w.kind == STAGED ? w.ps : lb_ctx::PipeShape{};
+  if (w.kind == CELL) {
     c->sblock = dim3(w.bx, STEP_BLOCK / w.bx, 1);
     c->sgrid = dim3((c->dom.nx + w.bx - 1) / w.bx, (c->dom.ny + c->sblock.y - 1) / c->sblock.y,
                     c->dom.nz);
   }
-  if (choice) *choice = w.tma ? 256 : int(w.bx);
+  if (choice) *choice = w.kind == ROWS ? 256 : (w.kind == STAGED ? 1000 + int(w.bx) : int(w.bx));
   return LB_OK;
 }
 

@@ -6,6 +6,7 @@
 #include "lb_kernels.cuh"
 #include "lb_tma.cuh"
 #include "lb_batch.cuh"
+#include "lb_pipe.cuh"
 #include "lb_ops.h"
 
 namespace lbgb {
@@ -137,6 +138,54 @@ struct Instance {
     }
     return cudaGetLastError();
   }
+  template <int KM, bool SOL>
+  static bool pipe_config_t(unsigned bx, size_t *smem, int *bps) {
+    const size_t bytes = PipeLayout<S, KM, SOL>::smem_bytes(bx);
+    // the attribute is per kernel, shared by every context: always allow the
+    // widest row, so that no context lowers it below another's launch
+    const size_t widest = PipeLayout<S, KM, SOL>::smem_bytes(STEP_BLOCK);
+    int dev = 0, maxopt = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return false;
+    if (widest > size_t(maxopt)) return false;
+    if (cudaFuncSetAttribute(pipe_step_kernel<S, KM, SOL>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(widest)) != cudaSuccess)
+      return false;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pipe_step_kernel<S, KM, SOL>, int(bx),
+                                                      bytes) != cudaSuccess ||
+        nb < 1)
+      return false;
+    *smem = bytes;
+    *bps = nb;
+    return true;
+  }
+  static bool pipe_config(int kmode, bool solute, unsigned bx, size_t *smem, int *bps) {
+    if (bx != 32 && bx != 64 && bx != 128) return false;
+    switch (kmode * 2 + (solute ? 1 : 0)) {
+      case 0: return pipe_config_t<KM_NONE, false>(bx, smem, bps);
+      case 1: return pipe_config_t<KM_NONE, true>(bx, smem, bps);
+      case 2: return pipe_config_t<KM_DIAG, false>(bx, smem, bps);
+      case 3: return pipe_config_t<KM_DIAG, true>(bx, smem, bps);
+      case 4: return pipe_config_t<KM_SPD, false>(bx, smem, bps);
+      default: return pipe_config_t<KM_SPD, true>(bx, smem, bps);
+    }
+  }
+  static cudaError_t pipe_step(int kmode, bool solute, const void *args, unsigned grid,
+                               unsigned bx, size_t smem, unsigned gxr, unsigned items,
+                               cudaStream_t s) {
+    const A &a = *static_cast<const A *>(args);
+    switch (kmode * 2 + (solute ? 1 : 0)) {
+      case 0: pipe_step_kernel<S, KM_NONE, false><<<grid, bx, smem, s>>>(a, gxr, items); break;
+      case 1: pipe_step_kernel<S, KM_NONE, true><<<grid, bx, smem, s>>>(a, gxr, items); break;
+      case 2: pipe_step_kernel<S, KM_DIAG, false><<<grid, bx, smem, s>>>(a, gxr, items); break;
+      case 3: pipe_step_kernel<S, KM_DIAG, true><<<grid, bx, smem, s>>>(a, gxr, items); break;
+      case 4: pipe_step_kernel<S, KM_SPD, false><<<grid, bx, smem, s>>>(a, gxr, items); break;
+      default: pipe_step_kernel<S, KM_SPD, true><<<grid, bx, smem, s>>>(a, gxr, items); break;
+    }
+    return cudaGetLastError();
+  }
   static cudaError_t batch_step(int kmode, bool solute, const void *tab, const uint16_t *owner,
                                 unsigned nd, unsigned total, unsigned grid, cudaStream_t s) {
     const BatchEntry<Real> *t = static_cast<const BatchEntry<Real> *>(tab);
@@ -172,6 +221,12 @@ struct Instance {
     o.batch_entry_bytes = sizeof(BatchEntry<Real>);
     o.tma_config = nullptr;
     o.tma_step = nullptr;
+    o.pipe_config = nullptr;
+    o.pipe_step = nullptr;
+    if constexpr (sizeof(typename S::T) == sizeof(Real)) {  // FP32 and FP64 storage
+      o.pipe_config = &pipe_config;
+      o.pipe_step = &pipe_step;
+    }
     if constexpr (S::id == StoreF32::id) {  // FP32 populations and static rows
       o.tma_config = &tma_config;
       o.tma_step = &tma_step;

@@ -45,8 +45,8 @@ struct CellGeo {
   unsigned onface;                   // faces_crossed bit layout
 };
 
-__device__ __forceinline__ CellGeo cell_geo(unsigned n, unsigned nx, unsigned ny, unsigned nz) {
-  const unsigned x = n % nx, yz = n / nx, y = yz % ny, z = yz / ny;
+__device__ __forceinline__ CellGeo cell_geo_xyz(unsigned x, unsigned y, unsigned z, unsigned nx,
+                                                unsigned ny, unsigned nz) {
   const int sy = int(nx), sz = int(nx * ny);
   CellGeo g;
   g.dxm = (x == 0) ? int(nx - 1) : -1;
@@ -58,6 +58,11 @@ __device__ __forceinline__ CellGeo cell_geo(unsigned n, unsigned nx, unsigned ny
   g.onface = (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
              (y == ny - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
   return g;
+}
+
+__device__ __forceinline__ CellGeo cell_geo(unsigned n, unsigned nx, unsigned ny, unsigned nz) {
+  const unsigned x = n % nx, yz = n / nx, y = yz % ny, z = yz / ny;
+  return cell_geo_xyz(x, y, z, nx, ny, nz);
 }
 
 // index delta of the pull source n - c_q (wrapped)
@@ -135,11 +140,12 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // V' = Lambda^-1 (V + eps G / 2), Lambda = I + (eps nu / 2) K^-1, and
 // F^ext = -eps nu K^-1 V' + eps G (Eqs. forcement, expandV, expandVsub).
-template <int KMODE, class Real>
-__device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, unsigned N,
-                                               unsigned n, Real eps, Real nu, const Real (&V)[3],
-                                               const Real (&G)[3], Real (&Vp)[3],
-                                               Real (&Fe)[3]) {
+// kv(r) returns row r of the cell's K^-1 (diagonal: xx, yy, zz; full: xx, yy,
+// zz, xy, yz, zx).
+template <int KMODE, class Real, class KV>
+__device__ __forceinline__ void velocity_solve_kv(KV kv, Real eps, Real nu, const Real (&V)[3],
+                                                  const Real (&G)[3], Real (&Vp)[3],
+                                                  Real (&Fe)[3]) {
   const Real r0 = V[0] + Real(0.5) * eps * G[0];
   const Real r1 = V[1] + Real(0.5) * eps * G[1];
   const Real r2 = V[2] + Real(0.5) * eps * G[2];
@@ -148,7 +154,7 @@ __device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, un
     Vp[0] = r0; Vp[1] = r1; Vp[2] = r2;
     Fe[0] = eps * G[0]; Fe[1] = eps * G[1]; Fe[2] = eps * G[2];
   } else if (KMODE == KM_DIAG) {
-    const Real kx = __ldg(kinv + n), ky = __ldg(kinv + N + n), kz = __ldg(kinv + 2 * size_t(N) + n);
+    const Real kx = kv(0), ky = kv(1), kz = kv(2);
     const Real hs = Real(0.5) * en;
     Vp[0] = r0 * rcp(Real(1) + hs * kx);
     Vp[1] = r1 * rcp(Real(1) + hs * ky);
@@ -157,9 +163,8 @@ __device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, un
     Fe[1] = -en * ky * Vp[1] + eps * G[1];
     Fe[2] = -en * kz * Vp[2] + eps * G[2];
   } else {
-    const Real kxx = __ldg(kinv + n), kyy = __ldg(kinv + N + n), kzz = __ldg(kinv + 2 * size_t(N) + n);
-    const Real kxy = __ldg(kinv + 3 * size_t(N) + n), kyz = __ldg(kinv + 4 * size_t(N) + n),
-               kzx = __ldg(kinv + 5 * size_t(N) + n);
+    const Real kxx = kv(0), kyy = kv(1), kzz = kv(2);
+    const Real kxy = kv(3), kyz = kv(4), kzx = kv(5);
     const Real hs = Real(0.5) * en;
     const Real l00 = Real(1) + hs * kxx, l11 = Real(1) + hs * kyy, l22 = Real(1) + hs * kzz;
     const Real l01 = hs * kxy, l12 = hs * kyz, l02 = hs * kzx;
@@ -174,6 +179,15 @@ __device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, un
     Fe[1] = -en * (kxy * Vp[0] + kyy * Vp[1] + kyz * Vp[2]) + eps * G[1];
     Fe[2] = -en * (kzx * Vp[0] + kyz * Vp[1] + kzz * Vp[2]) + eps * G[2];
   }
+}
+
+template <int KMODE, class Real>
+__device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, unsigned N,
+                                               unsigned n, Real eps, Real nu, const Real (&V)[3],
+                                               const Real (&G)[3], Real (&Vp)[3],
+                                               Real (&Fe)[3]) {
+  velocity_solve_kv<KMODE>([&](int r) { return __ldg(kinv + size_t(r) * N + n); }, eps, nu, V, G,
+                           Vp, Fe);
 }
 
 // Colour gradient F = sum_q rhohat(x + c_q) c_q (Eq. macros); a step out
@@ -282,6 +296,102 @@ __device__ __forceinline__ void warp_reductions(const StepArgs<Real> &a, unsigne
   }
 }
 
+// Fluid moments of the arriving populations: drho += sum_q (f_q - w_q) and
+// V = j / rho with j = sum_q c_q (f_q - w_q), rho = 1 + drho.
+template <class Real, class FV>
+__device__ __forceinline__ void fluid_moments(FV fv, Real &drho, Real (&V)[3]) {
+  Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const Real v = fv(qc);
+    drho += v;
+    if (cx(q)) j0 += Real(cx(q)) * v;
+    if (cy(q)) j1 += Real(cy(q)) * v;
+    if (cz(q)) j2 += Real(cz(q)) * v;
+  });
+  const Real irho = rcp(Real(1) + drho);
+  V[0] = j0 * irho;
+  V[1] = j1 * irho;
+  V[2] = j2 * irho;
+}
+
+// The per-cell arithmetic after streaming: concentration and viscosity,
+// colour gradient, V' and the Darcy force, fluid and solute collision,
+// stores and exported fields. fv(q) and hv(q) give the arriving f_q - w_q and
+// h_q, kv(r) the rows of K^-1; drho, rho, V are the fluid moments, sC the
+// solute total of the arriving h.
+template <class S, int KMODE, bool SOLUTE, class FV, class HV, class KV>
+__device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a, unsigned n,
+                                             const CellGeo &g, FV fv, HV hv, KV kv,
+                                             typename S::Real drho, typename S::Real rho,
+                                             const typename S::Real (&V)[3], typename S::Real ie,
+                                             typename S::Real eps, typename S::Real sC,
+                                             typename S::Real gx, typename S::Real gy,
+                                             typename S::Real gz) {
+  using Real = typename S::Real;
+  using T = typename S::T;
+  const unsigned N = a.N;
+  T *__restrict__ fo = static_cast<T *>(a.f_out) + n;
+  const Real C = sC * ie;
+  const Real tau = tau_of(a, C);
+  const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
+
+  FluidCollide<Real> fc;
+  fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
+  if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
+  velocity_solve_kv<KMODE>(kv, eps, nu, V, a.G, fc.Vp, fc.Fe);
+  fc.drho = drho;
+  fc.rho = rho;
+  fc.ie = ie;
+  fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
+  fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
+  fc.itau = rcp(tau);
+  fc.omt = Real(1) - fc.itau;
+  fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
+  fc.st = false;
+  fc.Fn = fc.stc = fc.iFn = Real(0);
+  if (a.A != Real(0)) {
+    fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
+    fc.st = fc.Fn > st_threshold<Real>();
+    fc.stc = fc.st ? a.A * eps * tau : Real(0);
+    fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+  }
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    Real v = fc.template post<q>(fv(qc));
+    if constexpr (S::kShift) v -= wq<Real>(q) * drho;
+    S::template st_f<q>(fo + int(q * N), v);
+  });
+  if constexpr (S::kShift) a.rf_out[n] = float(drho);
+
+  if (SOLUTE) {
+    T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
+    const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
+    const Real itd = a.inv_tau_D;
+    // h^eq of the moving directions; the rest component takes the remainder
+    // so that sum_q h^eq_q = sum_q h_q holds to rounding (the weights rounded
+    // to the collision type sum to 1 + 1.5e-8 in FP32, which would otherwise
+    // create solute at every collision)
+    Real hsum = Real(0);
+    Unroll<1, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+      const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
+      hsum += heq;
+      const Real h = hv(qc);
+      const Real shift = S::kShift ? wq<Real>(q) * sC : Real(0);
+      S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd - shift);
+    });
+    {
+      const Real h = hv(std::integral_constant<int, 0>{});
+      const Real shift = S::kShift ? wq<Real>(0) * sC : Real(0);
+      S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd - shift);
+    }
+    if constexpr (S::kShift) a.rh_out[n] = float(sC);
+  }
+  if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
+}
+
 // The per-cell update of one step from global memory: stream f (and h),
 // moments, viscosity, colour gradient, V' and the Darcy force, fluid and
 // solute collision, store; accumulates the cell's flux and totals.
@@ -294,21 +404,8 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
   using Real = typename S::Real;
   using T = typename S::T;
   const unsigned N = a.N;
-  const unsigned nx = a.nx, ny = a.ny, nz = a.nz;
-  CellGeo g;
-  {
-    const int sy = int(nx), sz = int(nx * ny);
-    g.dxm = (x == 0) ? int(nx - 1) : -1;
-    g.dxp = (x == nx - 1) ? -int(nx - 1) : 1;
-    g.dym = (y == 0) ? int(ny - 1) * sy : -sy;
-    g.dyp = (y == ny - 1) ? -int(ny - 1) * sy : sy;
-    g.dzm = (z == 0) ? int(nz - 1) * sz : -sz;
-    g.dzp = (z == nz - 1) ? -int(nz - 1) * sz : sz;
-    g.onface = (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
-               (y == ny - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
-  }
+  const CellGeo g = cell_geo_xyz(x, y, z, a.nx, a.ny, a.nz);
   const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
-  T *__restrict__ fo = static_cast<T *>(a.f_out) + n;
   Real d[Q];
   if (link == 0 && !(g.onface & a.f_wall)) {
     // every source is a cell
@@ -348,17 +445,9 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
       });
     }
   }
-  Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
-  Unroll<0, Q>::run([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    drho += d[q];
-    if (cx(q)) j0 += Real(cx(q)) * d[q];
-    if (cy(q)) j1 += Real(cy(q)) * d[q];
-    if (cz(q)) j2 += Real(cz(q)) * d[q];
-  });
+  Real V[3];
+  fluid_moments([&](auto qc) { return d[decltype(qc)::value]; }, drho, V);
   const Real rho = Real(1) + drho;
-  const Real irho = rcp(rho);
-  const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
   const Real ie = rcp(eps);
 
   if (SOLUTE) {
@@ -391,64 +480,11 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
     }
     Unroll<0, Q>::run([&](auto qc) { sC += hh[SOLUTE ? decltype(qc)::value : 0]; });
   }
-  const Real C = sC * ie;
-  const Real tau = tau_of(a, C);
-  const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
-
-  FluidCollide<Real> fc;
-  fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
-  if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
-  velocity_solve<KMODE>(a.kinv, N, n, eps, nu, V, a.G, fc.Vp, fc.Fe);
-  fc.drho = drho;
-  fc.rho = rho;
-  fc.ie = ie;
-  fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
-  fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
-  fc.itau = rcp(tau);
-  fc.omt = Real(1) - fc.itau;
-  fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
-  fc.st = false;
-  fc.Fn = fc.stc = fc.iFn = Real(0);
-  if (a.A != Real(0)) {
-    fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
-    fc.st = fc.Fn > st_threshold<Real>();
-    fc.stc = fc.st ? a.A * eps * tau : Real(0);
-    fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
-  }
-  Unroll<0, Q>::run([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    Real v = fc.template post<q>(d[q]);
-    if constexpr (S::kShift) v -= wq<Real>(q) * drho;
-    S::template st_f<q>(fo + int(q * N), v);
-  });
-  if constexpr (S::kShift) a.rf_out[n] = float(drho);
-
-  if (SOLUTE) {
-    T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
-    const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
-    const Real itd = a.inv_tau_D;
-    // h^eq of the moving directions; the rest component takes the remainder
-    // so that sum_q h^eq_q = sum_q h_q holds to rounding (the weights rounded
-    // to the collision type sum to 1 + 1.5e-8 in FP32, which would otherwise
-    // create solute at every collision)
-    Real hsum = Real(0);
-    Unroll<1, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
-      const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
-      hsum += heq;
-      const Real h = hh[SOLUTE ? q : 0];
-      const Real shift = S::kShift ? wq<Real>(q) * sC : Real(0);
-      S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd - shift);
-    });
-    {
-      const Real h = hh[0];
-      const Real shift = S::kShift ? wq<Real>(0) * sC : Real(0);
-      S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd - shift);
-    }
-    if constexpr (S::kShift) a.rh_out[n] = float(sC);
-  }
-  if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
+  collide_tail<S, KMODE, SOLUTE>(
+      a, n, g, [&](auto qc) { return d[decltype(qc)::value]; },
+      [&](auto qc) { return hh[SOLUTE ? decltype(qc)::value : 0]; },
+      [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
+      gz);
 }
 
 // One time step for every non-solid cell (see update_cell).

@@ -37,6 +37,13 @@ struct StorageOps {
                      int *blocks_per_sm);
   cudaError_t (*tma_step)(int kmode, bool solute, const void *args, unsigned grid,
                           unsigned threads, size_t smem, cudaStream_t s);
+  // row-staged persistent step kernel (NULL when not built for this storage):
+  // pipe_config fills the dynamic shared memory and resident blocks per SM
+  // for rows of bx threads (false if it does not fit); pipe_step launches it
+  // over items = gxr * ny * nz rows
+  bool (*pipe_config)(int kmode, bool solute, unsigned bx, size_t *smem, int *blocks_per_sm);
+  cudaError_t (*pipe_step)(int kmode, bool solute, const void *args, unsigned grid, unsigned bx,
+                           size_t smem, unsigned gxr, unsigned items, cudaStream_t s);
   // batched step over a table of BatchEntry<Real> (device memory)
   cudaError_t (*batch_step)(int kmode, bool solute, const void *tab, const uint16_t *owner,
                             unsigned nd, unsigned total, unsigned grid, cudaStream_t s);

@@ -140,8 +140,9 @@ def lb_step(ctx, n: int):
 
 
 def lb_autotune(ctx, reps: int = 5) -> int:
-    """Time the candidate launch shapes and keep the fastest; returns the
-    choice (row width, 256 = row-pipelined, 0 = not tuned)."""
+    """Time the candidate kernels and launch shapes and keep the fastest;
+    returns the choice (per-cell kernel: the row width; row-staged kernel:
+    1000 + the row width; 256 = row-pipelined; 0 = not tuned)."""
     ch = c_int32()
     _check(load().lb_autotune(ctx, int(reps), ctypes.byref(ch)), ctx)
     return ch.value
@@ -242,7 +243,7 @@ def make_domain(prob) -> lb_domain:
     return d
 
 
-KERNEL = {"auto": 0, "cell": 1, "rows": 2}
+KERNEL = {"auto": 0, "cell": 1, "rows": 2, "staged": 3}
 
 
 def make_params(prob, storage=None, check_every=0, kernel="auto") -> lb_params:

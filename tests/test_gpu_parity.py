@@ -129,11 +129,18 @@ def test_miscible_small_parity_and_balances():
     assert err["u"] < 1e-5
 
 
-def test_miscible_full_size_first_steps():
-    """128^3 in the benchmark's launch configuration: three steps from the
-    seeded initial state, every cell against the oracle."""
+@pytest.mark.parametrize("kernel", ["tuned", "cell", "staged"])
+def test_miscible_full_size_first_steps(kernel):
+    """128^3, three steps from the seeded initial state, every cell against
+    the oracle: with the kernel and launch shape the timing autotuner picks
+    (what the benchmark runs), and with each kernel forced."""
     p = W.miscible(128, 128, 128, seed=0)
-    g, o = run_both(p, 3, "fp32")
+    g = lb.Lattice(p, storage="fp32", kernel="auto" if kernel == "tuned" else kernel)
+    if kernel == "tuned":
+        lb.lb_autotune(g.ctx, 3)
+    g.step(3)
+    o = O.Oracle(p)
+    o.step(3)
     compare(g, o, p, "fp32")
 
 
@@ -243,6 +250,56 @@ def test_row_pipelined_kernel_rejects_other_shapes():
     assert e.value.code == lb.LB_EUNSUPPORTED
 
 
+STAGED_CASES = {
+    # every feature (solids, walls, solute inlet/outlet, full K, surface
+    # tension, hardening law); 19-cell rows: 32-thread blocks with a ragged
+    # tail; 2400 rows, more than one resident wave, so blocks walk several rows
+    "random": lambda: W.random_medium(19, 60, 40, seed=21, visc_law=2, A=1e-3),
+    # diagonal K, solute inlet/outlet on the z faces; 40-cell rows: 64-thread blocks
+    "miscible40": lambda: W.miscible(40, 36, 30, seed=3),
+    # 128-thread blocks, 5120 rows
+    "miscible128": lambda: W.miscible(128, 128, 40, seed=2),
+    # no permeability, no solute (solids and walls kept)
+    "plain": lambda: W.random_medium(33, 20, 30, seed=5, spd=False, solute=False).replace(K6=None),
+}
+
+
+@pytest.mark.parametrize("case", list(STAGED_CASES))
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_row_staged_kernel(case, storage):
+    """The row-staged kernel (persistent blocks, cp.async staging of the next
+    row) against the oracle and against the one-thread-per-cell kernel; the
+    two share the per-cell arithmetic, boundary cells take the per-cell path."""
+    p = STAGED_CASES[case]()
+    steps = 25
+    st = lb.Lattice(p, storage=storage, kernel="staged", check_every=1)
+    cell = lb.Lattice(p, storage=storage, kernel="cell", check_every=1)
+    st.step(steps)
+    cell.step(steps)
+    o = O.Oracle(p)
+    o.step(steps)
+    compare(st, o, p, storage)
+    fs, hs = st.populations()
+    fc, hc = cell.populations()
+    live = p.solid == 0
+    tol = 1e-14 if storage == "fp64" else 5e-7
+    assert np.abs(fs[:, live] - fc[:, live]).max() <= tol
+    if hs is not None:
+        assert np.abs(hs[:, live] - hc[:, live]).max() <= tol
+    rs, rc = st.reduce(), cell.reduce()
+    assert rs[0] == pytest.approx(rc[0], rel=1e-9)
+    assert rs[2] == pytest.approx(rc[2], rel=1e-6, abs=1e-12)
+    assert rs[3] == pytest.approx(rc[3], rel=1e-5, abs=1e-12)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_row_staged_kernel_needs_fp32_or_fp64(storage):
+    p = W.miscible(64, 8, 8, seed=1, storage=storage)
+    with pytest.raises(lb.LbError) as e:
+        lb.Lattice(p, storage=storage, kernel="staged")
+    assert e.value.code == lb.LB_EUNSUPPORTED
+
+
 def test_fp32_long_run_parity():
     """3000 steps of the miscible medium (32x32x48 crop): the FP32 path stays
     inside the tolerances over a long run (no systematic drift of C)."""
@@ -276,7 +333,7 @@ def test_autotune_leaves_state_and_picks_a_shape():
     f0, h0 = g.populations()
     r0 = g.reduce()
     choice = lb.lb_autotune(g.ctx, 3)
-    assert choice in (32, 64, 128, 256)
+    assert choice in (32, 64, 128, 256, 1032, 1064, 1128)
     f1, h1 = g.populations()
     assert np.array_equal(f0, f1) and np.array_equal(h0, h1)
     assert np.array_equal(r0, g.reduce()) and g.t == 3
