@@ -258,18 +258,9 @@ __global__ void __launch_bounds__(32 * (NW + 1), MINB)
         const unsigned xs = cx(q) > 0 ? xm : (cx(q) < 0 ? xp : x);
         return S::template cv_h<q>(lds_row<T>(shp + q * nx + xs));
       };
-      Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        const Real v = fval(qc);
-        drho += v;
-        if (cx(q)) j0 += Real(cx(q)) * v;
-        if (cy(q)) j1 += Real(cy(q)) * v;
-        if (cz(q)) j2 += Real(cz(q)) * v;
-      });
+      Real V[3];
+      fluid_moments(fval, drho, V);
       const Real rho = Real(1) + drho;
-      const Real irho = rcp(rho);
-      const Real V[3] = {j0 * irho, j1 * irho, j2 * irho};
       const Real eps = Real(sst[x]);
       const Real ie = rcp(eps);
       Real gx = Real(0), gy = Real(0), gz = Real(0);
@@ -279,104 +270,11 @@ __global__ void __launch_bounds__(32 * (NW + 1), MINB)
         gz = Real(sst[(3 + L::kinv_rows) * nx + x]);
         Unroll<0, Q>::run([&](auto qc) { sC += hval(qc); });
       }
-      const Real C = sC * ie;
-      const Real tau = tau_of(a, C);
-      const Real nu = (tau - Real(0.5)) * Real(1.0 / 3.0);
-      FluidCollide<Real> fc;
-      fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
-      if (a.A != Real(0)) {
-        CellGeo g;
-        const int sy = int(nx), sz = int(nx * ny);
-        g.dxm = (x == 0) ? int(nx - 1) : -1;
-        g.dxp = (x == nx - 1) ? -int(nx - 1) : 1;
-        g.dym = (y == 0) ? int(ny - 1) * sy : -sy;
-        g.dyp = (y == ny - 1) ? -int(ny - 1) * sy : sy;
-        g.dzm = (z == 0) ? int(nz - 1) * sz : -sz;
-        g.dzp = (z == nz - 1) ? -int(nz - 1) * sz : sz;
-        g.onface = yzface | (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u);
-        colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
-      }
-      // velocity correction with K^-1 from shared memory
-      {
-        Real kin[KMODE == KM_SPD ? 6 : 3];
-        if (KMODE != KM_NONE)
-          for (int k2 = 0; k2 < L::kinv_rows; ++k2) kin[k2] = Real(sst[(1 + k2) * nx + x]);
-        const Real r0 = V[0] + Real(0.5) * eps * a.G[0];
-        const Real r1 = V[1] + Real(0.5) * eps * a.G[1];
-        const Real r2 = V[2] + Real(0.5) * eps * a.G[2];
-        const Real en = eps * nu;
-        if (KMODE == KM_NONE) {
-          fc.Vp[0] = r0; fc.Vp[1] = r1; fc.Vp[2] = r2;
-          fc.Fe[0] = eps * a.G[0]; fc.Fe[1] = eps * a.G[1]; fc.Fe[2] = eps * a.G[2];
-        } else if (KMODE == KM_DIAG) {
-          const Real hs = Real(0.5) * en;
-          fc.Vp[0] = r0 * rcp(Real(1) + hs * kin[0]);
-          fc.Vp[1] = r1 * rcp(Real(1) + hs * kin[1]);
-          fc.Vp[2] = r2 * rcp(Real(1) + hs * kin[2]);
-          fc.Fe[0] = -en * kin[0] * fc.Vp[0] + eps * a.G[0];
-          fc.Fe[1] = -en * kin[1] * fc.Vp[1] + eps * a.G[1];
-          fc.Fe[2] = -en * kin[2] * fc.Vp[2] + eps * a.G[2];
-        } else {
-          const Real kxx = kin[0], kyy = kin[1], kzz = kin[KMODE == KM_SPD ? 2 : 0];
-          const Real kxy = kin[KMODE == KM_SPD ? 3 : 0], kyz = kin[KMODE == KM_SPD ? 4 : 0],
-                     kzx = kin[KMODE == KM_SPD ? 5 : 0];
-          const Real hs = Real(0.5) * en;
-          const Real l00 = Real(1) + hs * kxx, l11 = Real(1) + hs * kyy, l22 = Real(1) + hs * kzz;
-          const Real l01 = hs * kxy, l12 = hs * kyz, l02 = hs * kzx;
-          const Real c00 = l11 * l22 - l12 * l12, c01 = l02 * l12 - l01 * l22,
-                     c02 = l01 * l12 - l02 * l11;
-          const Real c11 = l00 * l22 - l02 * l02, c12 = l01 * l02 - l00 * l12,
-                     c22 = l00 * l11 - l01 * l01;
-          const Real idet = Real(1) / (l00 * c00 + l01 * c01 + l02 * c02);
-          fc.Vp[0] = (c00 * r0 + c01 * r1 + c02 * r2) * idet;
-          fc.Vp[1] = (c01 * r0 + c11 * r1 + c12 * r2) * idet;
-          fc.Vp[2] = (c02 * r0 + c12 * r1 + c22 * r2) * idet;
-          fc.Fe[0] = -en * (kxx * fc.Vp[0] + kxy * fc.Vp[1] + kzx * fc.Vp[2]) + eps * a.G[0];
-          fc.Fe[1] = -en * (kxy * fc.Vp[0] + kyy * fc.Vp[1] + kyz * fc.Vp[2]) + eps * a.G[1];
-          fc.Fe[2] = -en * (kzx * fc.Vp[0] + kyz * fc.Vp[1] + kzz * fc.Vp[2]) + eps * a.G[2];
-        }
-      }
-      fc.drho = drho;
-      fc.rho = rho;
-      fc.ie = ie;
-      fc.uu = fc.Vp[0] * fc.Vp[0] + fc.Vp[1] * fc.Vp[1] + fc.Vp[2] * fc.Vp[2];
-      fc.uF = fc.Vp[0] * fc.Fe[0] + fc.Vp[1] * fc.Fe[1] + fc.Vp[2] * fc.Fe[2];
-      fc.itau = rcp(tau);
-      fc.omt = Real(1) - fc.itau;
-      fc.pre = rho * (Real(1) - Real(0.5) * fc.itau);
-      fc.st = false;
-      fc.Fn = fc.stc = fc.iFn = Real(0);
-      if (a.A != Real(0)) {
-        fc.Fn = sqrt(fc.F[0] * fc.F[0] + fc.F[1] * fc.F[1] + fc.F[2] * fc.F[2]);
-        fc.st = fc.Fn > st_threshold<Real>();
-        fc.stc = fc.st ? a.A * eps * tau : Real(0);
-        fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
-      }
-      T *fo = static_cast<T *>(a.f_out) + n;
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        S::template st_f<q>(fo + size_t(q) * N, fc.template post<q>(fval(qc)));
-      });
-      if (SOLUTE) {
-        T *ho = static_cast<T *>(a.h_out) + n;
-        const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
-        const Real itd = a.inv_tau_D;
-        // rest component of h^eq as the remainder (see update_cell)
-        Real hsum = Real(0);
-        Unroll<1, Q>::run([&](auto qc) {
-          constexpr int q = decltype(qc)::value;
-          const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
-          const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
-          hsum += heq;
-          const Real h = hval(qc);
-          S::template st_h<q>(ho + size_t(q) * N, h + (heq - h) * itd);
-        });
-        {
-          const Real h = hval(std::integral_constant<int, 0>{});
-          S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd);
-        }
-      }
-      if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
+      // the collision pass re-reads the staged rows; K^-1 from shared memory
+      collide_tail<S, KMODE, SOLUTE>(
+          a, n, cell_geo_xyz(x, y, z, nx, ny, nz), fval, hval,
+          [&](int k2) { return Real(sst[(1 + k2) * nx + x]); }, drho, rho, V, ie, eps, sC, gx, gy,
+          gz);
     }
     // the stage may be refilled once every compute warp has read it
     __syncwarp();
