@@ -64,6 +64,11 @@ struct lb_ctx {
   void *lam = nullptr, *share = nullptr;
   uint8_t *flag_a = nullptr, *flag_b = nullptr;
   unsigned *any = nullptr;
+  // free surface: active-tile lists (step parity), their lengths, tile stamps
+  uint32_t *tiles[2] = {nullptr, nullptr};
+  unsigned *n_tiles = nullptr;
+  unsigned *stamp = nullptr;
+  unsigned ntx = 0, nty = 0, ntz = 0, fs_grid = 0;
   // table of lb_step_batch calls led by this context
   void *batch_tab = nullptr;
   size_t batch_tab_bytes = 0;
@@ -233,6 +238,38 @@ bool pipe_shape(const lb_ctx *c, unsigned bx, lb_ctx::PipeShape *ps) {
   return true;
 }
 
+// Free-surface arguments of the step that brings the state to step index t
+// (t = 0: the arguments that seed the first step's tiles).
+template <class Real>
+FsArgs<Real> fs_args(lb_ctx *c, const StepArgs<Real> &a, long long t) {
+  FsArgs<Real> fa;
+  fa.a = a;
+  fa.a.fields = c->fields;  // rho and V' of every live cell feed the re-typing
+  fa.a.link = c->link;
+  fa.type_old = c->type[c->cur];
+  fa.type_new = c->type[1 - c->cur];
+  fa.m_old = static_cast<Real *>(c->mass[c->cur]);
+  fa.m_new = static_cast<Real *>(c->mass[1 - c->cur]);
+  fa.lam = static_cast<Real *>(c->lam);
+  fa.rhohat_w = static_cast<Real *>(c->rhohat);
+  fa.flag_a = c->flag_a;
+  fa.flag_b = c->flag_b;
+  fa.share = static_cast<Real *>(c->share);
+  fa.any = c->any;
+  fa.tiles = c->tiles[t & 1];
+  fa.n_tiles = c->n_tiles + (t & 1);
+  fa.next_tiles = c->tiles[(t + 1) & 1];
+  fa.next_n_tiles = c->n_tiles + ((t + 1) & 1);
+  fa.stamp = c->stamp;
+  fa.stamp_next = unsigned(t + 1);
+  fa.ntx = c->ntx;
+  fa.nty = c->nty;
+  fa.ntz = c->ntz;
+  return fa;
+}
+
+unsigned fs_tile_count(const lb_ctx *c) { return c->ntx * c->nty * c->ntz; }
+
 bool valid_faces(const int32_t (&k)[3][2], bool fluid) {
   for (int a = 0; a < 3; ++a) {
     for (int s = 0; s < 2; ++s) {
@@ -374,8 +411,24 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     c->flag_a = static_cast<uint8_t *>(dev_alloc(c, N));
     c->flag_b = static_cast<uint8_t *>(dev_alloc(c, N));
     c->any = static_cast<unsigned *>(dev_alloc(c, sizeof(unsigned)));
-    if (!c->lam || !c->share || !c->flag_a || !c->flag_b || !c->any)
+    c->ntx = (unsigned(dom->nx) + FS_TX - 1) / FS_TX;
+    c->nty = (unsigned(dom->ny) + FS_TY - 1) / FS_TY;
+    c->ntz = (unsigned(dom->nz) + FS_TZ - 1) / FS_TZ;
+    const size_t ntiles = size_t(c->ntx) * c->nty * c->ntz;
+    c->tiles[0] = static_cast<uint32_t *>(dev_alloc(c, ntiles * sizeof(uint32_t)));
+    c->tiles[1] = static_cast<uint32_t *>(dev_alloc(c, ntiles * sizeof(uint32_t)));
+    c->n_tiles = static_cast<unsigned *>(dev_alloc(c, 2 * sizeof(unsigned)));
+    c->stamp = static_cast<unsigned *>(dev_alloc(c, ntiles * sizeof(unsigned)));
+    if (!c->lam || !c->share || !c->flag_a || !c->flag_b || !c->any || !c->tiles[0] ||
+        !c->tiles[1] || !c->n_tiles || !c->stamp)
       return bail(fail(c, LB_ENOMEM, "free surface"));
+    // persistent grid of the tile passes: enough resident blocks to cover
+    // the list of a typical step in one round
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return bail(fail(c, LB_ECUDA, "device attributes"));
+    c->fs_grid = unsigned(std::min<size_t>(ntiles, size_t(8) * unsigned(sms)));
   }
   // inputs -> device (caller pointers may be host or device)
   const size_t in_bytes = N * 4 + (K6 ? 6 * N * 4 : 0) + N + 64;
@@ -515,6 +568,14 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
                   c->mass[0], c->lam, c->ops->fp64, c->stream));
     CK(c, rhohat_init(c->N, c->link, d_rho, c->mass[0], c->prm.wall_rho, c->rhohat, c->ops->fp64,
                       c->stream));
+    // cells outside the active tiles are never written by a step: both mass
+    // buffers and both flag arrays start equal (no flag), no tile is stamped
+    const size_t rb = c->ops->fp64 ? 8 : 4;
+    CK(c, cudaMemcpyAsync(c->mass[1], c->mass[0], N * rb, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->flag_a, 0, N, c->stream));
+    CK(c, cudaMemsetAsync(c->flag_b, 0, N, c->stream));
+    CK(c, cudaMemsetAsync(c->stamp, 0, size_t(fs_tile_count(c)) * sizeof(unsigned), c->stream));
+    CK(c, cudaMemsetAsync(c->n_tiles, 0, 2 * sizeof(unsigned), c->stream));
   } else if (c->prm.A != 0.0) {
     CK(c, rhohat_init(c->N, c->link, d_rho, nullptr, c->prm.wall_rho, c->rhohat, c->ops->fp64,
                       c->stream));
@@ -531,6 +592,11 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
     in.f_scale = f_scale ? d_fs : nullptr;
     in.type = c->fs ? c->type[0] : nullptr;
     CK(c, c->ops->init(c->kmode, c->solute, args, &in, c->nblk, c->stream));
+    if (c->fs) {  // the first step's active tiles
+      const FsArgs<Real> fa = fs_args(c, a, 0);
+      CK(c, c->ops->fs_seed(&fa, fs_tile_count(c), (fs_tile_count(c) + BLOCK - 1) / BLOCK,
+                            c->stream));
+    }
     return int(LB_OK);
   });
 }
@@ -547,21 +613,9 @@ int lb_step(lb_ctx *c, int64_t n) {
       a.reduce = (c->prm.check_every > 0 && c->t % c->prm.check_every == 0) ? 1 : 0;
       a.fields = last ? c->fields : nullptr;
       if (c->fs) {
-        FsArgs<Real> fa;
-        a.fields = c->fields;  // rho and V' of every live cell feed the re-typing
-        a.link = c->link;
-        fa.a = a;
-        fa.type_old = c->type[c->cur];
-        fa.type_new = c->type[1 - c->cur];
-        fa.m_old = static_cast<const Real *>(c->mass[c->cur]);
-        fa.m_new = static_cast<Real *>(c->mass[1 - c->cur]);
-        fa.lam = static_cast<Real *>(c->lam);
-        fa.rhohat_w = static_cast<Real *>(c->rhohat);
-        fa.flag_a = c->flag_a;
-        fa.flag_b = c->flag_b;
-        fa.share = static_cast<Real *>(c->share);
-        fa.any = c->any;
-        CK(c, c->ops->fs_step(&fa, c->nblk, c->stream));
+        a.fields = c->fields;
+        const FsArgs<Real> fa = fs_args(c, a, c->t);
+        CK(c, c->ops->fs_step(&fa, c->fs_grid, (fs_tile_count(c) + BLOCK - 1) / BLOCK, c->stream));
         return int(LB_OK);
       }
       if (c->prm.A != 0.0) CK(c, c->ops->rhohat(args, c->rhohat, c->nblk, c->stream));

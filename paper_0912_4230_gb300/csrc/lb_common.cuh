@@ -215,15 +215,27 @@ enum : uint8_t { FS_NONE = 0, FS_FILL = 1, FS_EMPTYING = 2 };
 template <class Real>
 struct FsArgs {
   StepArgs<Real> a;      // fields must be set: rho and V' of every live cell
-  const uint8_t *type_old;
+  uint8_t *type_old;     // read by the step; the last pass settles it to the new type
   uint8_t *type_new;
-  const Real *m_old;
+  Real *m_old;           // read by the step; the last pass settles it to the new mass
   Real *m_new;
   Real *lam;             // lambda(t) in, lambda(t+1) out
   Real *rhohat_w;        // colour-gradient field written by the mass exchange
   uint8_t *flag_a, *flag_b;
   Real *share;           // excess mass handed to each interface neighbour
   unsigned *any;         // nonzero when some cell fills or empties this step
+  // Active tiles of FS_TX x FS_TY x FS_TZ cells: the tiles within one tile
+  // (26-neighbourhood, wrapped) of a tile holding a liquid or interface cell.
+  // The step runs over this step's list; its last pass stamps the tiles of
+  // the next step and a compaction pass lists them.
+  const uint32_t *tiles;
+  const unsigned *n_tiles;
+  uint32_t *next_tiles;
+  unsigned *next_n_tiles;
+  unsigned *stamp;       // per tile: the step whose list holds it
+  unsigned stamp_next;   // the next step's stamp
+  unsigned ntx, nty, ntz;
 };
+constexpr unsigned FS_TX = 32, FS_TY = 4, FS_TZ = 2;  // one BLOCK of cells
 
 }  // namespace lbgb

@@ -1,9 +1,11 @@
 // Free-surface kernels (Section 3 of the paper): liquid-mass exchange,
 // stream/collide of liquid and interface cells with the reconstruction of
 // populations coming from empty cells, and the re-typing of cells whose
-// liquid fraction leaves [0, 1]. One step is six dense launches over the
-// lattice; the re-typing passes return at once unless some cell flagged a
-// conversion in this step.
+// liquid fraction leaves [0, 1]. One step is six passes over the active
+// tiles (tiles within one tile of a liquid or interface cell; every cell
+// outside them is empty with nothing to do) and one compaction of the next
+// step's tiles. The re-typing passes return at once unless some cell flagged
+// a conversion in this step.
 #pragma once
 
 #include "lb_kernels.cuh"
@@ -19,6 +21,68 @@ __device__ __forceinline__ long long fs_neighbor(const CellGeo &g, unsigned n, u
   if (faces_ahead(q) & g.onface & f_wall) return -1;
   if ((link >> opp(q)) & 1u) return -1;
   return (long long)n + ahead_delta<q>(g);
+}
+
+static_assert(FS_TX * FS_TY * FS_TZ == BLOCK, "one tile per block of BLOCK threads");
+
+// Cells of this step's active tiles: block b takes list entries b, b +
+// gridDim.x, ...; thread k is cell (k % FS_TX, (k / FS_TX) % FS_TY, k /
+// (FS_TX FS_TY)) of the tile. cell(n) runs for cells inside the lattice and
+// returns whether the cell is liquid or interface after the step; with MARK
+// the tiles around a tile holding such a cell are stamped for the next step
+// (the trip count is uniform in the block, so every thread reaches the vote).
+template <bool MARK, class Real, class F>
+__device__ __forceinline__ void fs_tile_loop(const FsArgs<Real> &s, F &&cell) {
+  const unsigned cnt = *s.n_tiles;
+  const unsigned tx = threadIdx.x % FS_TX, ty = (threadIdx.x / FS_TX) % FS_TY,
+                 tz = threadIdx.x / (FS_TX * FS_TY);
+  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const unsigned tile = s.tiles[i];
+    const unsigned bx = tile % s.ntx, r = tile / s.ntx, by = r % s.nty, bz = r / s.nty;
+    const unsigned x = bx * FS_TX + tx, y = by * FS_TY + ty, z = bz * FS_TZ + tz;
+    bool keep = false;
+    if (x < s.a.nx && y < s.a.ny && z < s.a.nz) keep = cell(x + s.a.nx * (y + s.a.ny * z));
+    if (MARK && __syncthreads_or(keep) && threadIdx.x < 27) {
+      const unsigned k = threadIdx.x;
+      const unsigned mx = (bx + s.ntx + k % 3 - 1) % s.ntx;
+      const unsigned my = (by + s.nty + (k / 3) % 3 - 1) % s.nty;
+      const unsigned mz = (bz + s.ntz + k / 9 - 1) % s.ntz;
+      s.stamp[mx + s.ntx * (my + s.nty * mz)] = s.stamp_next;
+    }
+  }
+}
+
+// Lists the tiles stamped for the next step (order is immaterial: every
+// cell's update depends only on the previous step's values).
+template <class Real>
+__global__ void __launch_bounds__(BLOCK) fs_compact_kernel(const FsArgs<Real> s) {
+  const unsigned t = blockIdx.x * BLOCK + threadIdx.x;
+  if (t >= s.ntx * s.nty * s.ntz) return;
+  if (s.stamp[t] == s.stamp_next) s.next_tiles[atomicAdd(s.next_n_tiles, 1u)] = t;
+}
+
+// After initialisation: one block per tile stamps the tiles around every
+// tile that holds a liquid or interface cell.
+template <class Real>
+__global__ void __launch_bounds__(BLOCK) fs_seed_kernel(const FsArgs<Real> s) {
+  const unsigned tile = blockIdx.x;
+  const unsigned bx = tile % s.ntx, r = tile / s.ntx, by = r % s.nty, bz = r / s.nty;
+  const unsigned x = bx * FS_TX + threadIdx.x % FS_TX;
+  const unsigned y = by * FS_TY + (threadIdx.x / FS_TX) % FS_TY;
+  const unsigned z = bz * FS_TZ + threadIdx.x / (FS_TX * FS_TY);
+  bool keep = false;
+  if (x < s.a.nx && y < s.a.ny && z < s.a.nz) {
+    const unsigned n = x + s.a.nx * (y + s.a.ny * z);
+    const uint32_t link = s.a.link ? s.a.link[n] : 0u;
+    keep = !(link >> 31) && s.type_old[n] != CELL_EMPTY;
+  }
+  if (__syncthreads_or(keep) && threadIdx.x < 27) {
+    const unsigned k = threadIdx.x;
+    const unsigned mx = (bx + s.ntx + k % 3 - 1) % s.ntx;
+    const unsigned my = (by + s.nty + (k / 3) % 3 - 1) % s.nty;
+    const unsigned mz = (bz + s.ntz + k / 9 - 1) % s.ntz;
+    s.stamp[mx + s.ntx * (my + s.nty * mz)] = s.stamp_next;
+  }
 }
 
 // Density of a live cell from its populations of the step being completed
@@ -46,20 +110,22 @@ __global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S:
   using Real = typename S::Real;
   using T = typename S::T;
   const StepArgs<Real> &a = s.a;
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *s.any = 0u;
-  if (n >= a.N) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *s.any = 0u;
+    *s.next_n_tiles = 0u;
+  }
+  fs_tile_loop<false>(s, [&](unsigned n) {
   const uint32_t link = a.link ? __ldg(a.link + n) : 0u;
   if (link >> 31) {
     s.m_new[n] = Real(0);
     s.rhohat_w[n] = a.wall_rho;
-    return;
+    return false;
   }
   const uint8_t t = s.type_old[n];
   if (t == CELL_EMPTY) {
     s.m_new[n] = s.m_old[n];
     s.rhohat_w[n] = Real(0);
-    return;
+    return false;
   }
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   const T *fin = static_cast<const T *>(a.f_in);
@@ -82,6 +148,8 @@ __global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S:
   });
   s.m_new[n] = m;
   s.rhohat_w[n] = m;
+  return false;
+  });
 }
 
 // Flowchart steps f, h, e, i for liquid and interface cells: pull-stream with
@@ -95,14 +163,13 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
   using Real = typename S::Real;
   using T = typename S::T;
   const StepArgs<Real> &a = s.a;
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
   const unsigned N = a.N;
-  if (n >= N) return;
+  fs_tile_loop<false>(s, [&](unsigned n) {
   const uint32_t link = a.link ? __ldg(a.link + n) : 0u;
   const uint8_t t = s.type_old[n];
   if ((link >> 31) || t == CELL_EMPTY) {
     s.flag_a[n] = FS_NONE;
-    return;
+    return false;
   }
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   const T *__restrict__ fin = static_cast<const T *>(a.f_in);
@@ -196,14 +263,16 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
   }
   s.flag_a[n] = flag;
   if (flag) atomicOr(s.any, 1u);
+  return false;
+  });
 }
 
 // An emptying cell next to a filling cell stays an interface cell.
 template <class Real>
 __global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) {
   const StepArgs<Real> &a = s.a;
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
-  if (n >= a.N || *s.any == 0u) return;
+  if (*s.any == 0u) return;
+  fs_tile_loop<false>(s, [&](unsigned n) {
   uint8_t f = s.flag_a[n];
   if (f == FS_EMPTYING) {
     const uint32_t link = a.link ? a.link[n] : 0u;
@@ -217,6 +286,8 @@ __global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) 
     if (near_fill) f = FS_NONE;
   }
   s.flag_b[n] = f;
+  return false;
+  });
 }
 
 // New cell types: filled -> liquid, emptied -> empty, empty next to a filled
@@ -224,8 +295,7 @@ __global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) 
 template <class Real>
 __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) {
   const StepArgs<Real> &a = s.a;
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
-  if (n >= a.N) return;
+  fs_tile_loop<false>(s, [&](unsigned n) {
   uint8_t t = s.type_old[n];
   const uint32_t link = a.link ? a.link[n] : 0u;
   if (*s.any != 0u && !(link >> 31)) {
@@ -247,6 +317,8 @@ __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) 
     }
   }
   s.type_new[n] = t;
+  return false;
+  });
 }
 
 // New interface cells take f = f^eq(mean rho, mean V') of their liquid and
@@ -258,12 +330,12 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
   using Real = typename S::Real;
   using T = typename S::T;
   const StepArgs<Real> &a = s.a;
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
   const unsigned N = a.N;
-  if (n >= N || *s.any == 0u) return;
+  if (*s.any == 0u) return;
+  fs_tile_loop<false>(s, [&](unsigned n) {
   const uint8_t tn = s.type_new[n];
   const uint8_t f = s.flag_b[n];
-  if (tn != CELL_NEW_INTERFACE && f == FS_NONE) return;
+  if (tn != CELL_NEW_INTERFACE && f == FS_NONE) return false;
   const uint32_t link = a.link ? a.link[n] : 0u;
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   const float *fl = a.fields;
@@ -331,6 +403,8 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
     }
     s.share[n] = share;
   }
+  return false;
+  });
 }
 
 // Excess mass arrives at interface cells; types settle; lambda = m / rho.
@@ -338,13 +412,12 @@ template <class S>
 __global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
   const StepArgs<Real> &a = s.a;
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
   const unsigned N = a.N;
-  if (n >= N) return;
+  fs_tile_loop<true>(s, [&](unsigned n) {
   const uint32_t link = a.link ? a.link[n] : 0u;
   if (link >> 31) {
     s.lam[n] = Real(0);
-    return;
+    return false;
   }
   uint8_t tn = s.type_new[n];
   Real m = s.m_new[n];
@@ -365,6 +438,12 @@ __global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename 
     if (tn == CELL_EMPTY && s.flag_b[n] == FS_EMPTYING) zero_fields(a.fields, N, n);
   }
   s.lam[n] = tn == CELL_LIQUID ? Real(1) : (tn == CELL_EMPTY ? Real(0) : m / cell_rho<S>(a, n));
+  // both buffers of the type and the mass agree after the step, so a cell
+  // whose tile leaves the list keeps the same values under either parity
+  s.type_old[n] = tn;
+  s.m_old[n] = m;
+  return tn != CELL_EMPTY;
+  });
 }
 
 }  // namespace lbgb

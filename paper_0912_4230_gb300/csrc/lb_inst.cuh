@@ -73,14 +73,23 @@ struct Instance {
                                              S::kShift ? rh : nullptr);
     return cudaGetLastError();
   }
-  static cudaError_t fs_step(const void *args, unsigned nblk, cudaStream_t s) {
+  static cudaError_t fs_step(const void *args, unsigned grid, unsigned tile_blocks,
+                             cudaStream_t s) {
     const FsArgs<Real> &f = *static_cast<const FsArgs<Real> *>(args);
-    fs_mass_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
-    fs_step_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
-    fs_cancel_kernel<Real><<<nblk, BLOCK, 0, s>>>(f);
-    fs_retype_kernel<Real><<<nblk, BLOCK, 0, s>>>(f);
-    fs_newcell_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
-    fs_finish_kernel<S><<<nblk, BLOCK, 0, s>>>(f);
+    fs_mass_kernel<S><<<grid, BLOCK, 0, s>>>(f);
+    fs_step_kernel<S><<<grid, BLOCK, 0, s>>>(f);
+    fs_cancel_kernel<Real><<<grid, BLOCK, 0, s>>>(f);
+    fs_retype_kernel<Real><<<grid, BLOCK, 0, s>>>(f);
+    fs_newcell_kernel<S><<<grid, BLOCK, 0, s>>>(f);
+    fs_finish_kernel<S><<<grid, BLOCK, 0, s>>>(f);
+    fs_compact_kernel<Real><<<tile_blocks, BLOCK, 0, s>>>(f);
+    return cudaGetLastError();
+  }
+  static cudaError_t fs_seed(const void *args, unsigned tiles, unsigned tile_blocks,
+                             cudaStream_t s) {
+    const FsArgs<Real> &f = *static_cast<const FsArgs<Real> *>(args);
+    fs_seed_kernel<Real><<<tiles, BLOCK, 0, s>>>(f);
+    fs_compact_kernel<Real><<<tile_blocks, BLOCK, 0, s>>>(f);
     return cudaGetLastError();
   }
   // The row-pipelined kernel is built for the coupled lattice (solute on),
@@ -215,7 +224,11 @@ struct Instance {
     o.from_f64 = &from_f64;
     o.totals = &totals;
     o.fs_step = nullptr;
-    if constexpr (S::id == StoreF32::id || S::id == StoreF64::id) o.fs_step = &fs_step;
+    o.fs_seed = nullptr;
+    if constexpr (S::id == StoreF32::id || S::id == StoreF64::id) {
+      o.fs_step = &fs_step;
+      o.fs_seed = &fs_seed;
+    }
     o.batch_step = &batch_step;
     o.batch_advance = &batch_advance;
     o.batch_entry_bytes = sizeof(BatchEntry<Real>);

@@ -26,9 +26,13 @@ struct StorageOps {
   cudaError_t (*totals)(const void *f, const void *h, const uint32_t *link, unsigned N,
                         double *partials, unsigned nblk, const float *rf, const float *rh,
                         cudaStream_t s);
-  // one free-surface step (six launches), FsArgs<Real>*; NULL when the
+  // one free-surface step, FsArgs<Real>*: six passes over the active tiles
+  // (grid blocks each) and the compaction of the next step's tiles
+  // (tile_blocks = ceil(tiles / BLOCK)); fs_seed stamps and lists the first
+  // step's tiles after initialisation (one block per tile). NULL when the
   // storage format has no free-surface build
-  cudaError_t (*fs_step)(const void *fs_args, unsigned nblk, cudaStream_t s);
+  cudaError_t (*fs_step)(const void *fs_args, unsigned grid, unsigned tile_blocks, cudaStream_t s);
+  cudaError_t (*fs_seed)(const void *fs_args, unsigned tiles, unsigned tile_blocks, cudaStream_t s);
   // row-pipelined step kernel (NULL when not built for this storage):
   // tma_config fills the dynamic shared memory, threads per block and
   // resident blocks per SM for a row of nx cells (returns false if it does
