@@ -25,12 +25,52 @@ __device__ __forceinline__ long long fs_neighbor(const CellGeo &g, unsigned n, u
 
 static_assert(FS_TX * FS_TY * FS_TZ == BLOCK, "one tile per block of BLOCK threads");
 
+// Tiles needed by the next step around one cell, as a mask over the 27
+// tile offsets (bit (dx+1) + 3(dy+1) + 9(dz+1)): the cell's own tile when
+// `self`, and with `halo` also the tiles holding its D3Q19 neighbours (a
+// neighbour lies in another tile only when the cell is on that tile face).
+__device__ __forceinline__ unsigned fs_tile_mask(unsigned lx, unsigned ly, unsigned lz, bool self,
+                                                 bool halo) {
+  if (!self && !halo) return 0u;
+  unsigned m = 1u << 13;
+  if (!halo) return m;
+  const int x0 = lx == 0 ? -1 : 0, x1 = lx == FS_TX - 1 ? 1 : 0;
+  const int y0 = ly == 0 ? -1 : 0, y1 = ly == FS_TY - 1 ? 1 : 0;
+  const int z0 = lz == 0 ? -1 : 0, z1 = lz == FS_TZ - 1 ? 1 : 0;
+  for (int dz = z0; dz <= z1; ++dz)
+    for (int dy = y0; dy <= y1; ++dy)
+      for (int dx = x0; dx <= x1; ++dx)
+        if (dx * dx + dy * dy + dz * dz <= 2) m |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+  return m;
+}
+
+// Stamps, for the next step, the tiles of the block-wide OR of the cells'
+// masks around tile (bx, by, bz) (wrapped; every thread of the block calls it).
+template <class Real>
+__device__ __forceinline__ void fs_stamp_tiles(const FsArgs<Real> &s, unsigned bx, unsigned by,
+                                               unsigned bz, unsigned mask) {
+  __shared__ unsigned block_mask;
+  if (threadIdx.x == 0) block_mask = 0u;
+  __syncthreads();
+  mask = __reduce_or_sync(0xffffffffu, mask);
+  if ((threadIdx.x & 31u) == 0 && mask) atomicOr(&block_mask, mask);
+  __syncthreads();
+  const unsigned k = threadIdx.x;
+  if (k < 27 && ((block_mask >> k) & 1u)) {
+    const unsigned mx = (bx + s.ntx + k % 3 - 1) % s.ntx;
+    const unsigned my = (by + s.nty + (k / 3) % 3 - 1) % s.nty;
+    const unsigned mz = (bz + s.ntz + k / 9 - 1) % s.ntz;
+    s.stamp[mx + s.ntx * (my + s.nty * mz)] = s.stamp_next;
+  }
+  __syncthreads();  // block_mask is reset for the next tile only after every read
+}
+
 // Cells of this step's active tiles: block b takes list entries b, b +
 // gridDim.x, ...; thread k is cell (k % FS_TX, (k / FS_TX) % FS_TY, k /
-// (FS_TX FS_TY)) of the tile. cell(n) runs for cells inside the lattice and
-// returns whether the cell is liquid or interface after the step; with MARK
-// the tiles around a tile holding such a cell are stamped for the next step
-// (the trip count is uniform in the block, so every thread reaches the vote).
+// (FS_TX FS_TY)) of the tile. cell(n, lx, ly, lz) runs for cells inside the
+// lattice; with MARK it returns the cell's tile mask (fs_tile_mask) and the
+// tiles of the block's masks are stamped for the next step (the trip count
+// is uniform in the block, so every thread reaches the barriers).
 template <bool MARK, class Real, class F>
 __device__ __forceinline__ void fs_tile_loop(const FsArgs<Real> &s, F &&cell) {
   const unsigned cnt = *s.n_tiles;
@@ -40,15 +80,9 @@ __device__ __forceinline__ void fs_tile_loop(const FsArgs<Real> &s, F &&cell) {
     const unsigned tile = s.tiles[i];
     const unsigned bx = tile % s.ntx, r = tile / s.ntx, by = r % s.nty, bz = r / s.nty;
     const unsigned x = bx * FS_TX + tx, y = by * FS_TY + ty, z = bz * FS_TZ + tz;
-    bool keep = false;
-    if (x < s.a.nx && y < s.a.ny && z < s.a.nz) keep = cell(x + s.a.nx * (y + s.a.ny * z));
-    if (MARK && __syncthreads_or(keep) && threadIdx.x < 27) {
-      const unsigned k = threadIdx.x;
-      const unsigned mx = (bx + s.ntx + k % 3 - 1) % s.ntx;
-      const unsigned my = (by + s.nty + (k / 3) % 3 - 1) % s.nty;
-      const unsigned mz = (bz + s.ntz + k / 9 - 1) % s.ntz;
-      s.stamp[mx + s.ntx * (my + s.nty * mz)] = s.stamp_next;
-    }
+    unsigned mask = 0u;
+    if (x < s.a.nx && y < s.a.ny && z < s.a.nz) mask = cell(x + s.a.nx * (y + s.a.ny * z), tx, ty, tz);
+    if (MARK) fs_stamp_tiles(s, bx, by, bz, mask);
   }
 }
 
@@ -61,28 +95,23 @@ __global__ void __launch_bounds__(BLOCK) fs_compact_kernel(const FsArgs<Real> s)
   if (s.stamp[t] == s.stamp_next) s.next_tiles[atomicAdd(s.next_n_tiles, 1u)] = t;
 }
 
-// After initialisation: one block per tile stamps the tiles around every
-// tile that holds a liquid or interface cell.
+// After initialisation: one block per tile stamps the tiles the first step
+// needs around its liquid and interface cells.
 template <class Real>
 __global__ void __launch_bounds__(BLOCK) fs_seed_kernel(const FsArgs<Real> s) {
   const unsigned tile = blockIdx.x;
   const unsigned bx = tile % s.ntx, r = tile / s.ntx, by = r % s.nty, bz = r / s.nty;
-  const unsigned x = bx * FS_TX + threadIdx.x % FS_TX;
-  const unsigned y = by * FS_TY + (threadIdx.x / FS_TX) % FS_TY;
-  const unsigned z = bz * FS_TZ + threadIdx.x / (FS_TX * FS_TY);
-  bool keep = false;
+  const unsigned tx = threadIdx.x % FS_TX, ty = (threadIdx.x / FS_TX) % FS_TY,
+                 tz = threadIdx.x / (FS_TX * FS_TY);
+  const unsigned x = bx * FS_TX + tx, y = by * FS_TY + ty, z = bz * FS_TZ + tz;
+  unsigned mask = 0u;
   if (x < s.a.nx && y < s.a.ny && z < s.a.nz) {
     const unsigned n = x + s.a.nx * (y + s.a.ny * z);
     const uint32_t link = s.a.link ? s.a.link[n] : 0u;
-    keep = !(link >> 31) && s.type_old[n] != CELL_EMPTY;
+    const bool live = !(link >> 31) && s.type_old[n] != CELL_EMPTY;
+    mask = fs_tile_mask(tx, ty, tz, live, live);
   }
-  if (__syncthreads_or(keep) && threadIdx.x < 27) {
-    const unsigned k = threadIdx.x;
-    const unsigned mx = (bx + s.ntx + k % 3 - 1) % s.ntx;
-    const unsigned my = (by + s.nty + (k / 3) % 3 - 1) % s.nty;
-    const unsigned mz = (bz + s.ntz + k / 9 - 1) % s.ntz;
-    s.stamp[mx + s.ntx * (my + s.nty * mz)] = s.stamp_next;
-  }
+  fs_stamp_tiles(s, bx, by, bz, mask);
 }
 
 // Density of a live cell from its populations of the step being completed
@@ -114,18 +143,18 @@ __global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S:
     *s.any = 0u;
     *s.next_n_tiles = 0u;
   }
-  fs_tile_loop<false>(s, [&](unsigned n) {
+  fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
   const uint32_t link = a.link ? __ldg(a.link + n) : 0u;
   if (link >> 31) {
     s.m_new[n] = Real(0);
     s.rhohat_w[n] = a.wall_rho;
-    return false;
+    return 0u;
   }
   const uint8_t t = s.type_old[n];
   if (t == CELL_EMPTY) {
     s.m_new[n] = s.m_old[n];
     s.rhohat_w[n] = Real(0);
-    return false;
+    return 0u;
   }
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   const T *fin = static_cast<const T *>(a.f_in);
@@ -148,7 +177,7 @@ __global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S:
   });
   s.m_new[n] = m;
   s.rhohat_w[n] = m;
-  return false;
+  return 0u;
   });
 }
 
@@ -164,12 +193,13 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
   using T = typename S::T;
   const StepArgs<Real> &a = s.a;
   const unsigned N = a.N;
-  fs_tile_loop<false>(s, [&](unsigned n) {
+  fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
   const uint32_t link = a.link ? __ldg(a.link + n) : 0u;
   const uint8_t t = s.type_old[n];
+  s.flag_b[n] = FS_NONE;  // the re-typing pass rewrites it when some cell flags
   if ((link >> 31) || t == CELL_EMPTY) {
     s.flag_a[n] = FS_NONE;
-    return false;
+    return 0u;
   }
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   const T *__restrict__ fin = static_cast<const T *>(a.f_in);
@@ -263,7 +293,7 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
   }
   s.flag_a[n] = flag;
   if (flag) atomicOr(s.any, 1u);
-  return false;
+  return 0u;
   });
 }
 
@@ -272,7 +302,7 @@ template <class Real>
 __global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) {
   const StepArgs<Real> &a = s.a;
   if (*s.any == 0u) return;
-  fs_tile_loop<false>(s, [&](unsigned n) {
+  fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
   uint8_t f = s.flag_a[n];
   if (f == FS_EMPTYING) {
     const uint32_t link = a.link ? a.link[n] : 0u;
@@ -286,7 +316,7 @@ __global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) 
     if (near_fill) f = FS_NONE;
   }
   s.flag_b[n] = f;
-  return false;
+  return 0u;
   });
 }
 
@@ -295,7 +325,7 @@ __global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) 
 template <class Real>
 __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) {
   const StepArgs<Real> &a = s.a;
-  fs_tile_loop<false>(s, [&](unsigned n) {
+  fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
   uint8_t t = s.type_old[n];
   const uint32_t link = a.link ? a.link[n] : 0u;
   if (*s.any != 0u && !(link >> 31)) {
@@ -317,7 +347,7 @@ __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) 
     }
   }
   s.type_new[n] = t;
-  return false;
+  return 0u;
   });
 }
 
@@ -332,10 +362,10 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
   const StepArgs<Real> &a = s.a;
   const unsigned N = a.N;
   if (*s.any == 0u) return;
-  fs_tile_loop<false>(s, [&](unsigned n) {
+  fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
   const uint8_t tn = s.type_new[n];
   const uint8_t f = s.flag_b[n];
-  if (tn != CELL_NEW_INTERFACE && f == FS_NONE) return false;
+  if (tn != CELL_NEW_INTERFACE && f == FS_NONE) return 0u;
   const uint32_t link = a.link ? a.link[n] : 0u;
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   const float *fl = a.fields;
@@ -403,7 +433,7 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
     }
     s.share[n] = share;
   }
-  return false;
+  return 0u;
   });
 }
 
@@ -413,11 +443,11 @@ __global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename 
   using Real = typename S::Real;
   const StepArgs<Real> &a = s.a;
   const unsigned N = a.N;
-  fs_tile_loop<true>(s, [&](unsigned n) {
+  fs_tile_loop<true>(s, [&](unsigned n, unsigned lx, unsigned ly, unsigned lz) -> unsigned {
   const uint32_t link = a.link ? a.link[n] : 0u;
   if (link >> 31) {
     s.lam[n] = Real(0);
-    return false;
+    return 0u;
   }
   uint8_t tn = s.type_new[n];
   Real m = s.m_new[n];
@@ -442,7 +472,9 @@ __global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename 
   // whose tile leaves the list keeps the same values under either parity
   s.type_old[n] = tn;
   s.m_old[n] = m;
-  return tn != CELL_EMPTY;
+  // the next step needs every cell within one link of a liquid or interface
+  // cell, and each cell flagged in this step (its flags are cleared then)
+  return fs_tile_mask(lx, ly, lz, s.flag_b[n] != FS_NONE, tn != CELL_EMPTY);
   });
 }
 
