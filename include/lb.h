@@ -179,10 +179,13 @@ int lb_step(lb_ctx *ctx, int64_t n);
  * beyond the order of the FP64 flux sums. */
 int lb_autotune(lb_ctx *ctx, int32_t reps, int32_t *choice);
 
-/* Advance several lattices by the same n steps in one persistent launch per
- * step (a work list of every lattice's cell blocks), captured in a CUDA graph
- * when the first context's stream is not the legacy default stream. Each
- * lattice computes exactly what lb_step(n) with the per-cell kernel computes.
+/* Advance several lattices by the same n steps (continuous batching; no
+ * counterpart in the paper). Per step, a lattice whose per-cell launch alone
+ * fills the GPU (at least 6 blocks per SM) takes that launch; the smaller
+ * lattices share one persistent launch per 64 lattices over a work list of
+ * their cell blocks, their arguments travelling in the launch's parameters.
+ * Each lattice computes exactly what lb_step(n) with the per-cell kernel
+ * computes.
  * All contexts: same storage, same permeability mode (none / diagonal / full),
  * same solute setting, no free surface, A = 0 (LB_EUNSUPPORTED otherwise).
  * Work is enqueued on the first context's stream; the contexts' own streams

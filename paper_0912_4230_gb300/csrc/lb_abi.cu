@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -642,88 +643,83 @@ namespace {
 template <class Real>
 int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
   lb_ctx *c0 = ctxs[0];
-  std::vector<BatchEntry<Real>> tab(n);
-  unsigned total = 0;
-  for (int i = 0; i < n; ++i) {
-    lb_ctx *c = ctxs[i];
-    BatchEntry<Real> &e = tab[i];
-    std::memset(&e, 0, sizeof e);
-    fill_args(c, e.a);
-    e.a.t = c->t + 1;
-    e.check_every = c->prm.check_every;
-    e.a.reduce = (e.check_every > 0 && e.a.t % e.check_every == 0) ? 1 : 0;
-    e.fields = c->fields;
-    e.t_final = c->t + steps;
-    e.a.fields = (e.a.t == e.t_final) ? c->fields : nullptr;
-    e.gx = c->sgrid.x;
-    e.gy = c->sgrid.y;
-    e.bx = c->sblock.x;
-    e.blk_begin = total;
-    total += c->sgrid.x * c->sgrid.y * c->sgrid.z;
-  }
   if (n > 65535) return fail(c0, LB_EUNSUPPORTED, "more than 65535 lattices in one batch");
-  std::vector<uint16_t> owner(total);
-  for (int i = 0; i < n; ++i) {
-    const unsigned end = (i + 1 < n) ? tab[i + 1].blk_begin : total;
-    for (unsigned b = tab[i].blk_begin; b < end; ++b) owner[b] = uint16_t(i);
-  }
-  const size_t tbytes = tab.size() * sizeof(BatchEntry<Real>);
-  const size_t obytes = owner.size() * sizeof(uint16_t);
-  const size_t bytes = ((tbytes + 255) & ~size_t(255)) + obytes;
-  if (c0->batch_tab_bytes < bytes) {
-    dev_free(c0, c0->batch_tab);
-    c0->batch_tab = dev_alloc(c0, bytes);
-    c0->batch_tab_bytes = c0->batch_tab ? bytes : 0;
-    if (!c0->batch_tab) return fail(c0, LB_ENOMEM, "batch table");
-  }
-  cudaStream_t s = c0->stream;
-  uint16_t *d_owner = reinterpret_cast<uint16_t *>(static_cast<char *>(c0->batch_tab) +
-                                                   ((tbytes + 255) & ~size_t(255)));
-  CK(c0, cudaMemcpyAsync(c0->batch_tab, tab.data(), tbytes, cudaMemcpyHostToDevice, s));
-  CK(c0, cudaMemcpyAsync(d_owner, owner.data(), obytes, cudaMemcpyHostToDevice, s));
   int dev = 0, sms = 0;
   CK(c0, cudaGetDevice(&dev));
   CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = std::min(total, unsigned(6 * sms));
-  const StorageOps *ops = c0->ops;
-  const int km = c0->kmode;
-  const bool sol = c0->solute;
-  auto one = [&]() -> cudaError_t {
-    cudaError_t e = ops->batch_step(km, sol, c0->batch_tab, d_owner, unsigned(n), total, grid, s);
-    if (e == cudaSuccess) e = ops->batch_advance(c0->batch_tab, unsigned(n), s);
-    return e;
-  };
-  int64_t done = 0;
-  // a graph of G steps, replayed, when the stream can be captured
-  const int64_t G = 16;
-  if (s != nullptr && steps >= 2 * G) {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    CK(c0, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaSuccess;
-    for (int64_t k = 0; k < G && ce == cudaSuccess; ++k) ce = one();
-    cudaError_t ee = cudaStreamEndCapture(s, &graph);
-    if (ce != cudaSuccess || ee != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return fail(c0, LB_ECUDA, std::string("batch graph capture: ") +
-                                    cudaGetErrorString(ce != cudaSuccess ? ce : ee));
-    }
-    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) return fail(c0, LB_ECUDA, std::string("graph: ") + cudaGetErrorString(ie));
-    for (; done + G <= steps; done += G) {
-      cudaError_t le = cudaGraphLaunch(exec, s);
-      if (le != cudaSuccess) {
-        cudaGraphExecDestroy(exec);
-        return fail(c0, LB_ECUDA, std::string("graph launch: ") + cudaGetErrorString(le));
-      }
-    }
-    cudaGraphExecDestroy(exec);
-  }
-  for (; done < steps; ++done) CK(c0, one());
+  const unsigned wave = unsigned(6 * sms);  // resident blocks of the per-cell kernel
+  // a lattice whose own launch fills the GPU steps alone (its per-cell launch);
+  // the smaller ones share the persistent launches, their blocks concatenated
+  std::vector<int> alone, shared;
   for (int i = 0; i < n; ++i) {
-    ctxs[i]->t += steps;
-    if (steps % 2) ctxs[i]->cur = 1 - ctxs[i]->cur;
+    const dim3 g = ctxs[i]->sgrid;
+    (g.x * g.y * g.z >= wave ? alone : shared).push_back(i);
+  }
+  const int ns = int(shared.size());
+  std::vector<unsigned> begin(size_t(ns) + 1);
+  unsigned total = 0;
+  for (int j = 0; j < ns; ++j) {
+    const dim3 g = ctxs[shared[j]]->sgrid;
+    begin[j] = total;
+    total += g.x * g.y * g.z;
+  }
+  begin[ns] = total;
+  cudaStream_t s = c0->stream;
+  const uint64_t *d_work = nullptr;
+  if (ns > 0) {
+    std::vector<uint64_t> work(total);
+    for (int j = 0; j < ns; ++j) {
+      const dim3 g = ctxs[shared[j]]->sgrid;
+      unsigned b = begin[j];
+      for (unsigned bz = 0; bz < g.z; ++bz)
+        for (unsigned by = 0; by < g.y; ++by)
+          for (unsigned bx = 0; bx < g.x; ++bx) work[b++] = batch_item(unsigned(j), bx, by, bz);
+    }
+    const size_t wbytes = work.size() * sizeof(uint64_t);
+    if (c0->batch_tab_bytes < wbytes) {
+      dev_free(c0, c0->batch_tab);
+      c0->batch_tab = dev_alloc(c0, wbytes);
+      c0->batch_tab_bytes = c0->batch_tab ? wbytes : 0;
+      if (!c0->batch_tab) return fail(c0, LB_ENOMEM, "batch work list");
+    }
+    d_work = static_cast<const uint64_t *>(c0->batch_tab);
+    CK(c0, cudaMemcpyAsync(c0->batch_tab, work.data(), wbytes, cudaMemcpyHostToDevice, s));
+  }
+  // one table per launch of at most BATCH_MAX lattices, filled on the host
+  // for every step (the launch copies it into its parameter space)
+  std::unique_ptr<BatchTable<Real>> tab(new BatchTable<Real>());
+  for (int64_t k = 0; k < steps; ++k) {
+    const bool last = (k == steps - 1);
+    auto step_args = [&](lb_ctx *c, StepArgs<Real> &a) {
+      fill_args(c, a);
+      a.t = c->t + 1;
+      a.reduce = (c->prm.check_every > 0 && a.t % c->prm.check_every == 0) ? 1 : 0;
+      a.fields = last ? c->fields : nullptr;
+    };
+    for (int i : alone) {
+      StepArgs<Real> a;
+      step_args(ctxs[i], a);
+      CK(c0, c0->ops->step(c0->kmode, c0->solute, &a, ctxs[i]->sgrid, ctxs[i]->sblock, s));
+    }
+    for (int g0 = 0; g0 < ns; g0 += BATCH_MAX) {
+      const int g1 = std::min(ns, g0 + BATCH_MAX);
+      std::memset(tab.get(), 0, sizeof(BatchTable<Real>));
+      for (int j = g0; j < g1; ++j) {
+        lb_ctx *c = ctxs[shared[j]];
+        BatchEntry<Real> &e = tab->e[j - g0];
+        step_args(c, e.a);
+        e.gx = c->sgrid.x;
+        e.gy = c->sgrid.y;
+        e.bx = c->sblock.x;
+      }
+      const unsigned blocks = begin[g1] - begin[g0];
+      CK(c0, c0->ops->batch_step(c0->kmode, c0->solute, tab.get(), d_work, unsigned(g0),
+                                 begin[g0], begin[g1], std::min(blocks, wave), s));
+    }
+    for (int i = 0; i < n; ++i) {
+      ctxs[i]->t += 1;
+      ctxs[i]->cur = 1 - ctxs[i]->cur;
+    }
   }
   return LB_OK;
 }

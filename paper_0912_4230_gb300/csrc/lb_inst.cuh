@@ -195,21 +195,18 @@ struct Instance {
     }
     return cudaGetLastError();
   }
-  static cudaError_t batch_step(int kmode, bool solute, const void *tab, const uint16_t *owner,
-                                unsigned nd, unsigned total, unsigned grid, cudaStream_t s) {
-    const BatchEntry<Real> *t = static_cast<const BatchEntry<Real> *>(tab);
+  static cudaError_t batch_step(int kmode, bool solute, const void *tab, const uint64_t *work,
+                                unsigned d_begin, unsigned vb_begin, unsigned vb_end,
+                                unsigned grid, cudaStream_t s) {
+    const BatchTable<Real> &t = *static_cast<const BatchTable<Real> *>(tab);
     switch (kmode * 2 + (solute ? 1 : 0)) {
-      case 0: batched_step_kernel<S, KM_NONE, false><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
-      case 1: batched_step_kernel<S, KM_NONE, true><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
-      case 2: batched_step_kernel<S, KM_DIAG, false><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
-      case 3: batched_step_kernel<S, KM_DIAG, true><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
-      case 4: batched_step_kernel<S, KM_SPD, false><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
-      default: batched_step_kernel<S, KM_SPD, true><<<grid, STEP_BLOCK, 0, s>>>(t, owner, nd, total); break;
+      case 0: batched_step_kernel<S, KM_NONE, false><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
+      case 1: batched_step_kernel<S, KM_NONE, true><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
+      case 2: batched_step_kernel<S, KM_DIAG, false><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
+      case 3: batched_step_kernel<S, KM_DIAG, true><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
+      case 4: batched_step_kernel<S, KM_SPD, false><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
+      default: batched_step_kernel<S, KM_SPD, true><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
     }
-    return cudaGetLastError();
-  }
-  static cudaError_t batch_advance(void *tab, unsigned nd, cudaStream_t s) {
-    batch_advance_kernel<Real><<<(nd + 127) / 128, 128, 0, s>>>(static_cast<BatchEntry<Real> *>(tab), nd);
     return cudaGetLastError();
   }
   static StorageOps make() {
@@ -230,8 +227,6 @@ struct Instance {
       o.fs_seed = &fs_seed;
     }
     o.batch_step = &batch_step;
-    o.batch_advance = &batch_advance;
-    o.batch_entry_bytes = sizeof(BatchEntry<Real>);
     o.tma_config = nullptr;
     o.tma_step = nullptr;
     o.pipe_config = nullptr;

@@ -48,11 +48,11 @@ struct StorageOps {
   bool (*pipe_config)(int kmode, bool solute, unsigned bx, size_t *smem, int *blocks_per_sm);
   cudaError_t (*pipe_step)(int kmode, bool solute, const void *args, unsigned grid, unsigned bx,
                            size_t smem, unsigned gxr, unsigned items, cudaStream_t s);
-  // batched step over a table of BatchEntry<Real> (device memory)
-  cudaError_t (*batch_step)(int kmode, bool solute, const void *tab, const uint16_t *owner,
-                            unsigned nd, unsigned total, unsigned grid, cudaStream_t s);
-  cudaError_t (*batch_advance)(void *tab, unsigned nd, cudaStream_t s);
-  size_t batch_entry_bytes;
+  // one batched step: tab is a host BatchTable<Real> (passed by value in the
+  // launch), work the device work list (batch_item descriptors)
+  cudaError_t (*batch_step)(int kmode, bool solute, const void *tab, const uint64_t *work,
+                            unsigned d_begin, unsigned vb_begin, unsigned vb_end, unsigned grid,
+                            cudaStream_t s);
 };
 
 const StorageOps &ops_f32();

@@ -22,13 +22,15 @@ def _lat(p, storage="fp32", stream=None):
 def test_batched_step_equals_separate_steps(storage):
     torch = pytest.importorskip("torch")
     s = torch.cuda.Stream()
+    # the first three share the persistent launch; the 128 x 64 x 20 lattice
+    # (1280 blocks, more than one resident wave) takes its own launch
     probs = [W.miscible(40, 36, 30, seed=1), W.miscible(64, 20, 17, seed=2),
-             W.miscible(33, 48, 21, seed=3)]
+             W.miscible(33, 48, 21, seed=3), W.miscible(128, 64, 20, seed=4)]
     sep = [_lat(p, storage) for p in probs]
     bat = [_lat(p, storage, stream=s.cuda_stream) for p in probs]
     for g in sep:
         g.step(70)
-    lb.lb_step_batch([g.ctx for g in bat], 70)   # 70 steps: graph of 16 replayed + remainder
+    lb.lb_step_batch([g.ctx for g in bat], 70)
     for p, a, b in zip(probs, sep, bat):
         fa, ha = a.populations()
         fb, hb = b.populations()
@@ -38,6 +40,29 @@ def test_batched_step_equals_separate_steps(storage):
         ua, ub = a.fields()[1], b.fields()[1]
         assert np.array_equal(ua, ub)
         assert a.t == b.t == 70
+
+
+def test_batch_of_more_lattices_than_one_launch_holds():
+    """70 lattices: two launches per step (64 + 6 lattices), each lattice
+    bit-identical to stepping it alone; an odd step count leaves every
+    context on the other buffer."""
+    torch = pytest.importorskip("torch")
+    s = torch.cuda.Stream()
+    probs = [W.miscible(8 + (i % 5), 6 + (i % 3), 5 + (i % 4), seed=100 + i) for i in range(70)]
+    sep = [_lat(p) for p in probs]
+    bat = [_lat(p, stream=s.cuda_stream) for p in probs]
+    for g in sep:
+        g.step(9)
+    lb.lb_step_batch([g.ctx for g in bat], 9)
+    for a, b in zip(sep, bat):
+        fa, ha = a.populations()
+        fb, hb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
+        assert np.array_equal(a.reduce(), b.reduce())
+        assert np.array_equal(a.fields()[1], b.fields()[1])
+        assert a.t == b.t == 9
+    for g in sep + bat:
+        g.close()
 
 
 def test_batched_step_parity_with_oracle():
