@@ -211,6 +211,14 @@ int lb_reduce(lb_ctx *ctx, double *mass, double *solute, double *flux_in,
  * population q of cell n is pulled from, or an LB_SRC_* class. */
 int lb_debug_neighbors(lb_ctx *ctx, int32_t lattice, int32_t *src);
 
+/* Test hook for failure detection (no counterpart in the paper): one warp
+ * waits, with the bounded wait of the step kernels' barrier waits, on a
+ * shared-memory barrier that nothing completes. The wait gives up after
+ * limit_ns (0 < limit_ns <= 2e9), sets the context's timeout status and the
+ * call returns LB_ETIMEOUT, as a step whose wait gave up would at the next
+ * check. The context stays usable; the status is cleared by lb_init. */
+int lb_debug_wait_timeout(lb_ctx *ctx, int64_t limit_ns);
+
 /* Free-surface state: cell types (LB_CELL_*) and liquid mass m per cell
  * (in the collision precision, widened to double). */
 int lb_free_surface_state(lb_ctx *ctx, uint8_t *type, double *mass);

@@ -13,6 +13,7 @@
 #include "lb_batch.cuh"
 #include "lb_kernels.cuh"
 #include "lb_ops.h"
+#include "lb_tma.cuh"
 
 using namespace lbgb;
 
@@ -270,6 +271,19 @@ FsArgs<Real> fs_args(lb_ctx *c, const StepArgs<Real> &a, long long t) {
 }
 
 unsigned fs_tile_count(const lb_ctx *c) { return c->ntx * c->nty * c->ntz; }
+
+// One warp waits, with the step kernels' bounded wait, on a shared-memory
+// barrier that nothing completes; on giving up it sets the timeout bit of the
+// context's status word, as the row-pipelined kernel does.
+__global__ void wait_timeout_kernel(DevState *state, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncwarp();
+  mbar_fence_init();
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar, 0, limit_ns));
+  if (!ok && threadIdx.x == 0) atomicOr(&state->status, 2u);
+}
 
 bool valid_faces(const int32_t (&k)[3][2], bool fluid) {
   for (int a = 0; a < 3; ++a) {
@@ -744,6 +758,14 @@ int lb_step_batch(lb_ctx *const *ctxs, int32_t n, int64_t steps) {
   }
   if (steps == 0) return LB_OK;
   return c0->ops->fp64 ? step_batch_t<double>(ctxs, n, steps) : step_batch_t<float>(ctxs, n, steps);
+}
+
+int lb_debug_wait_timeout(lb_ctx *c, int64_t limit_ns) {
+  if (!c) return LB_EINVAL;
+  if (limit_ns < 1 || limit_ns > 2000000000LL) return fail(c, LB_EINVAL, "limit_ns outside (0, 2 s]");
+  wait_timeout_kernel<<<1, 32, 0, c->stream>>>(c->state, (unsigned long long)limit_ns);
+  CK(c, cudaGetLastError());
+  return check_status(c);
 }
 
 int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {

@@ -22,7 +22,10 @@
 namespace lbgb {
 
 constexpr int TMA_STAGES = 3;
-constexpr unsigned TMA_WAIT_LIMIT = 1u << 26;  // polls before a wait gives up
+// a wait gives up after this long (the global nanosecond timer), or after
+// this many polls should the timer not advance
+constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;
+constexpr unsigned TMA_WAIT_POLLS = 1u << 30;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -52,10 +55,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // bounded wait: false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  for (unsigned i = 0; i < TMA_WAIT_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
+                                          unsigned long long limit_ns = TMA_WAIT_NS) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned i = 0; i < TMA_WAIT_POLLS; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {

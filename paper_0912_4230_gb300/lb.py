@@ -29,7 +29,7 @@ STORE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_get_populations",
            "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
            "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
-           "lb_totals_noalloc", "lb_step_batch", "lb_autotune"]
+           "lb_totals_noalloc", "lb_step_batch", "lb_autotune", "lb_debug_wait_timeout"]
 
 
 class LbError(RuntimeError):
@@ -73,6 +73,7 @@ def load() -> ctypes.CDLL:
     L.lb_fields.argtypes = [vp] * 5
     L.lb_reduce.argtypes = [vp] * 5
     L.lb_debug_neighbors.argtypes = [vp, c_int32, vp]
+    L.lb_debug_wait_timeout.argtypes = [vp, c_int64]
     L.lb_free_surface_state.argtypes = [vp, vp, vp]
     L.lb_sync.argtypes = [vp]
     L.lb_time.argtypes = [vp]
@@ -166,6 +167,10 @@ def lb_reduce(ctx):
 
 def lb_debug_neighbors(ctx, lattice: int, src):
     _check(load().lb_debug_neighbors(ctx, int(lattice), _ptr(src)), ctx)
+
+
+def lb_debug_wait_timeout(ctx, limit_ns: int):
+    _check(load().lb_debug_wait_timeout(ctx, int(limit_ns)), ctx)
 
 
 def lb_free_surface_state(ctx, cell_type=None, mass=None):
