@@ -152,6 +152,40 @@ def test_precision_crop_spd_fp32():
     compare(g, o, p, "fp32")
 
 
+@pytest.fixture(scope="module")
+def precision_full():
+    """256^3 rotated-tensor medium and the oracle's fields after 3 steps."""
+    p = W.precision(256, 256, 256, storage="fp32")
+    o = O.Oracle(p)
+    o.step(3)
+    out = (p, o.fields())
+    del o  # releases the oracle's ~10 GB of FP64 state
+    return out
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_precision_full_size_first_steps(precision_full, storage):
+    """256^3 with a full SPD K per cell, in the benchmark's configuration
+    (autotuned launch), three steps, every cell against the oracle: FP32 to
+    the FP32 tolerances, FP16/BF16 to their long-run bounds."""
+    p, (r_rho, r_u, r_C, r_nu) = precision_full
+    g = lb.Lattice(p, storage=storage, check_every=1)
+    lb.lb_autotune(g.ctx, 2)
+    g.step(3)
+    rho, u, C, nu = g.fields()
+    rel = np.abs(u - r_u).max() / np.abs(r_u).max()
+    if storage == "fp32":
+        tol = TOL["fp32"]
+        assert rel <= tol["u"]
+        assert np.abs(rho - r_rho).max() <= tol["rho"]
+        assert np.abs(C - r_C).max() <= tol["C"]
+        assert np.abs(nu - r_nu).max() <= tol["nu"]
+    else:
+        assert rel <= (1e-3 if storage == "fp16" else 5e-3)
+        assert np.abs(C - r_C).max() <= 1e-3
+    g.close()
+
+
 @pytest.mark.parametrize("storage,bound", [("fp16", 1e-3), ("bf16", 5e-3)])
 def test_reduced_precision_storage_error(storage, bound):
     """FP16 / BF16 deviation storage on the rotated-tensor crop: error of u
