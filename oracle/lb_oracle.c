@@ -152,16 +152,52 @@ void orc_forcing(double rho, double tau, double eps, const double *u,
  * Substituting Eq. forcement into Eq. expandV gives
  *   (I + (eps nu / 2) K^-1) V' = V + (eps / 2) G,
  * so the reading is V' = Lambda^-1 (V + eps G / 2) (the printed Eq. expandVsub
- * drops the eps in front of G). Kinv9 = NULL means K^-1 = 0. */
+ * drops the eps in front of G). Kinv9 = NULL means K^-1 = 0.
+ *
+ * Forchheimer drag (cF != 0; reading R21, the paper names the term but gives
+ * no equation): the porous-flow model the paper builds on (Guo and Zhao) adds
+ * -eps F_eps |V'| K^-1/2 V' to the force, F_eps = cF 1.75 / sqrt(150 eps^3)
+ * (Ergun), with K^-1/2 = diag(sqrt(K^-1_ii)) for a diagonal K. With the same
+ * half-force velocity V' = V + F^ext / 2 this gives, axis by axis,
+ *   V'_i (1 + eps nu k_i / 2 + eps F_eps sqrt(k_i) s / 2) = V_i + eps G_i / 2,
+ * with s = |V'|. The right-hand side of s = |V'(s)| decreases in s, so the
+ * root is unique in [0, |V'(0)|]; it is found by bisection to the last bit. */
 void orc_velocity_solve(const double *V, double eps, double nu,
-                        const double *Kinv9, const double *G, double *Vp,
-                        double *Fext)
+                        const double *Kinv9, const double *G, double cF,
+                        double *Vp, double *Fext)
 {
-  double L[9], Li[9], r[3];
+  double r[3];
+  for (int i = 0; i < 3; i++) r[i] = V[i] + 0.5 * eps * G[i];
+  if (cF != 0.0 && Kinv9) {
+    double Fe = cF * 1.75 / sqrt(150.0 * eps * eps * eps);
+    double a[3], b[3], k[3];
+    for (int i = 0; i < 3; i++) {
+      k[i] = Kinv9[4 * i];  /* diagonal entries */
+      a[i] = 1.0 + 0.5 * eps * nu * k[i];
+      b[i] = 0.5 * eps * Fe * sqrt(k[i]);
+    }
+    double lo = 0.0, hi = 0.0;
+    for (int i = 0; i < 3; i++) hi += (r[i] / a[i]) * (r[i] / a[i]);
+    hi = sqrt(hi);
+    for (int it = 0; it < 200; it++) {
+      double mid = 0.5 * (lo + hi), m2 = 0.0;
+      for (int i = 0; i < 3; i++) {
+        double v = r[i] / (a[i] + b[i] * mid);
+        m2 += v * v;
+      }
+      if (sqrt(m2) > mid) lo = mid; else hi = mid;
+    }
+    double sv = 0.5 * (lo + hi);
+    for (int i = 0; i < 3; i++) Vp[i] = r[i] / (a[i] + b[i] * sv);
+    double speed = sqrt(dot3(Vp, Vp));
+    for (int i = 0; i < 3; i++)
+      Fext[i] = -eps * nu * k[i] * Vp[i] - eps * Fe * sqrt(k[i]) * speed * Vp[i] + eps * G[i];
+    return;
+  }
+  double L[9], Li[9];
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++)
       L[3 * i + j] = (i == j ? 1.0 : 0.0) + (Kinv9 ? 0.5 * eps * nu * Kinv9[3 * i + j] : 0.0);
-  for (int i = 0; i < 3; i++) r[i] = V[i] + 0.5 * eps * G[i];
   inv3(L, Li);
   for (int i = 0; i < 3; i++)
     Vp[i] = Li[3 * i + 0] * r[0] + Li[3 * i + 1] * r[1] + Li[3 * i + 2] * r[2];
@@ -344,6 +380,12 @@ orc *orc_create(const orc_params *p, const double *eps, const double *K6,
   if (p->visc_law != 0 && !p->solute) return NULL;
   if (p->solute && !(p->tau_D > 0.5)) return NULL;
   if (p->free_surface && (p->solute || K6)) return NULL;
+  if (p->forchheimer < 0.0) return NULL;
+  if (p->forchheimer != 0.0 && K6) {  /* the Forchheimer reading needs a diagonal K */
+    int64_t N0 = (int64_t)p->nx * p->ny * p->nz;
+    for (int64_t n = 0; n < N0; n++)
+      if (K6[6 * n + 3] != 0.0 || K6[6 * n + 4] != 0.0 || K6[6 * n + 5] != 0.0) return NULL;
+  }
 
   orc *o = (orc *)zalloc(sizeof(orc));
   o->p = *p;
@@ -641,7 +683,8 @@ static void collide(orc *o, int64_t n)
   double F[3] = {0, 0, 0};
   if (o->p.A != 0.0) colour_gradient(o, n, F);
   double Vp[3], Fe[3], fe[Q], T[Q];
-  orc_velocity_solve(V, eps, nu, o->Kinv ? o->Kinv + 9 * n : NULL, o->p.G, Vp, Fe);
+  orc_velocity_solve(V, eps, nu, o->Kinv ? o->Kinv + 9 * n : NULL, o->p.G, o->p.forchheimer,
+                     Vp, Fe);
   orc_feq(rho, Vp, eps, tau, o->p.A, F, fe);
   orc_forcing(rho, tau, eps, Vp, Fe, T);
   for (int q = 0; q < Q; q++) {

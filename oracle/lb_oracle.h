@@ -42,6 +42,8 @@ typedef struct {
   double C_in;        /* concentration injected at INLET faces */
   int32_t free_surface;
   int32_t threads;    /* OpenMP threads, <= 0 = library default */
+  double forchheimer; /* multiplier c_F of the Ergun coefficient F_eps (0 = no
+                         Forchheimer drag); needs a diagonal or no K */
 } orc_params;
 
 typedef struct orc orc;
@@ -67,8 +69,8 @@ void orc_feq(double rho, const double *u, double eps, double tau, double A,
 void orc_forcing(double rho, double tau, double eps, const double *u,
                  const double *Fext, double *out);
 void orc_velocity_solve(const double *V, double eps, double nu,
-                        const double *Kinv9, const double *G, double *Vp,
-                        double *Fext);
+                        const double *Kinv9, const double *G, double cF,
+                        double *Vp, double *Fext);
 void orc_heq(double eps, double C, const double *Vstar, double *out);
 double orc_tau_of(const orc_params *p, double C, int64_t t);
 

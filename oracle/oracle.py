@@ -43,6 +43,7 @@ class OrcParams(ctypes.Structure):
         ("G", c_double * 3), ("A", c_double), ("wall_rho", c_double),
         ("solute", c_int32), ("tau_D", c_double), ("C_in", c_double),
         ("free_surface", c_int32), ("threads", c_int32),
+        ("forchheimer", c_double),
     ]
 
 
@@ -83,7 +84,7 @@ def lib():
         L.orc_feq.argtypes = [c_double, c_void_p, c_double, c_double, c_double, c_void_p, c_void_p]
         L.orc_forcing.argtypes = [c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]
         L.orc_velocity_solve.argtypes = [c_void_p, c_double, c_double, c_void_p, c_void_p,
-                                         c_void_p, c_void_p]
+                                         c_double, c_void_p, c_void_p]
         L.orc_heq.argtypes = [c_double, c_double, c_void_p, c_void_p]
         L.orc_tau_of.restype = c_double
         L.orc_tau_of.argtypes = [POINTER(OrcParams), c_double, c_int64]
@@ -125,6 +126,7 @@ def make_params(prob, threads: int = 0) -> OrcParams:
     p.C_in = k.get("C_in", 0.0)
     p.free_surface = int(k.get("free_surface", 0))
     p.threads = threads
+    p.forchheimer = k.get("forchheimer", 0.0)
     return p
 
 
@@ -150,11 +152,12 @@ def forcing(rho, tau, eps, u, Fext):
     return out
 
 
-def velocity_solve(V, eps, nu, Kinv9, G):
+def velocity_solve(V, eps, nu, Kinv9, G, cF=0.0):
     Vp = np.zeros(3)
     Fe = np.zeros(3)
     kin = None if Kinv9 is None else _f64(np.asarray(Kinv9).reshape(9))
-    lib().orc_velocity_solve(_ptr(_f64(V)), eps, nu, _ptr(kin), _ptr(_f64(G)), _ptr(Vp), _ptr(Fe))
+    lib().orc_velocity_solve(_ptr(_f64(V)), eps, nu, _ptr(kin), _ptr(_f64(G)), float(cF),
+                             _ptr(Vp), _ptr(Fe))
     return Vp, Fe
 
 

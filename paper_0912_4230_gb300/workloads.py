@@ -139,6 +139,37 @@ def miscible(nx=128, ny=128, nz=128, seed=0, steps=5000, storage="fp32") -> Prob
                  steps=steps, storage=storage, meta=dict(seed=seed))
 
 
+def forchheimer(nx=128, ny=128, nz=128, seed=0, steps=5000, storage="fp32", cF=1.0,
+                G=1e-4) -> Problem:
+    """The miscible medium made coarse enough for inertial drag: diagonal K with
+    K_xx = K_yy = 10^U(-2, 0) per cell and K_zz = 10 K_xx, body force G along
+    z, Forchheimer drag with the Ergun coefficient times cF. Porosity bands,
+    solute inlet/outlet and viscosity law as in the miscible medium."""
+    base = miscible(nx, ny, nz, seed=seed, steps=steps, storage=storage)
+    rng = _rng(seed + 1000)
+    N = nx * ny * nz
+    kxx = 10.0 ** rng.uniform(-2.0, 0.0, N)
+    K6 = np.zeros((N, 6), np.float32)
+    K6[:, 0] = kxx
+    K6[:, 1] = kxx
+    K6[:, 2] = 10.0 * kxx
+    params = dict(base.params, G=(0.0, 0.0, G), forchheimer=cF)
+    return base.replace(name="forchheimer", K6=K6.ravel(), params=params)
+
+
+def forchheimer_bulk(K=(1.0, 1.0, 1.0), eps=0.5, tau=0.8, G=(6e-3, 0.0, 0.0), cF=1.0,
+                     n=4, steps=600) -> Problem:
+    """Uniform periodic medium with diagonal K, body force G and Forchheimer
+    drag: the steady velocity is uniform and solves the Darcy-Forchheimer
+    balance."""
+    N = n * n * n
+    K6 = np.zeros((N, 6), np.float32)
+    K6[:, 0], K6[:, 1], K6[:, 2] = K
+    return _base("forchheimer_bulk", n, n, n, ALL_PERIODIC, ALL_PERIODIC,
+                 dict(tau=tau, G=tuple(G), forchheimer=cF), _uniform(N, eps), K6.ravel(),
+                 steps=steps, storage="fp64")
+
+
 def _random_rotations(nblocks, seed):
     """Haar-random rotation matrices from unit quaternions of 4 normals."""
     rng = _rng(seed)
