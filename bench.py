@@ -48,10 +48,14 @@ def _other_workloads():
                            prec + "BF16 deviation storage"),
         "plain-fp64": (lambda r: W.plain_channel(), "fp64", 337,
                        "plain Brinkman channel 16x16x64, FP64, no solute"),
+        "forchheimer": (lambda r: W.forchheimer(seed=r), "fp32", 321,
+                        "coarse porous medium 128^3 with Forchheimer drag (diagonal K, "
+                        "K_zz = 10 K_xx, G 1e-4), D3Q19 fluid + solute, FP32"),
         # free surface: algorithmic bytes counted per updated (liquid or interface) cell
         "drop": (lambda r: W.drop(seed=r), "fp32", 171,
                  "free-surface drop 192x192x128 (R 24, 40 cells above a solid wall), A 1e-3, "
-                 "FP32, six kernels per step; roofline per updated cell"),
+                 "FP32, six passes over the active tiles and one compaction per step; roofline "
+                 "per updated cell"),
     }
 
 

@@ -93,8 +93,14 @@ typedef struct {
   double A;             /* surface-tension strength, Eqs. equilc1/equilc2 (0 = off) */
   double wall_rho;      /* colour-gradient density seen at solid cells and
                            wall faces (wetting); used when A != 0 */
-  double forchheimer;   /* Forchheimer coefficient: the paper gives no term, so
-                           this build accepts 0 only (else LB_EUNSUPPORTED) */
+  double forchheimer;   /* Forchheimer drag, >= 0 (0 = off). The paper names the
+                           term without an equation; this build takes the
+                           porous-flow model it builds on: F^ext gains
+                           -eps F_eps |V'| K^-1/2 V' with F_eps = forchheimer *
+                           1.75 / sqrt(150 eps^3) (Ergun) and the implicit V'
+                           of Eq. expandV solved with it. Needs a diagonal K
+                           (a full tensor returns LB_EUNSUPPORTED); no effect
+                           without K. */
   int32_t solute;       /* 1: solute lattice on (Section 2.2) */
   double tau_D;         /* solute relaxation time, > 1/2; D = (tau_D - 1/2)/3 */
   double C_in;          /* concentration entering through INLET faces */
@@ -128,9 +134,10 @@ typedef struct {
  *   solid     N bytes, nonzero = impermeable cell (never updated; links into
  *             it bounce back).
  * Returns LB_EINVAL for bad sizes, face kinds, tau <= 1/2, eps out of range or
- * a K that fails a Cholesky test; LB_EUNSUPPORTED for forchheimer != 0 or
- * free_surface together with solute or K6; LB_ENOMEM/LB_ECUDA on device
- * failures. *out is NULL on failure. */
+ * a K that fails a Cholesky test, forchheimer < 0; LB_EUNSUPPORTED for
+ * forchheimer != 0 with a non-diagonal K, or free_surface together with
+ * solute or K6; LB_ENOMEM/LB_ECUDA on device failures. *out is NULL on
+ * failure. */
 int lb_create(const lb_domain *domain, const float *porosity, const float *K6,
               const uint8_t *solid, const lb_params *params, lb_ctx **out);
 

@@ -188,6 +188,7 @@ void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
   a.visc_law = c->prm.visc_law;
   a.A = Real(c->prm.A);
   a.wall_rho = Real(c->prm.wall_rho);
+  a.forch = Real(c->prm.forchheimer);
   if (c->solute) {
     a.inv_tau_D = Real(1.0 / c->prm.tau_D);
     a.D = Real((c->prm.tau_D - 0.5) / 3.0);
@@ -325,8 +326,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     for (int s = 0; s < 2; ++s)
       if (dom->bc[a][s] == LB_BC_WALL && dom->sbc[a][s] != LB_BC_WALL)
         return fail(nullptr, LB_EINVAL, "solute faces must be WALL where the fluid has a wall");
-  if (prm->forchheimer != 0.0)
-    return fail(nullptr, LB_EUNSUPPORTED, "Forchheimer term: the paper gives no equation for it");
+  if (!(prm->forchheimer >= 0.0)) return fail(nullptr, LB_EINVAL, "forchheimer < 0");
   if (prm->visc_law < 0 || prm->visc_law > 2) return fail(nullptr, LB_EINVAL, "visc_law");
   if (prm->visc_law == 0 && !(prm->tau > 0.5)) return fail(nullptr, LB_EINVAL, "tau <= 1/2");
   if (prm->visc_law == 1 && !(prm->tau0 > 0.5 && prm->tau1 > 0.5))
@@ -485,6 +485,9 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (hflags & 2u) return bail(fail(c, LB_EINVAL, "permeability tensor not positive definite"));
   c->has_solid = (hflags & 8u) != 0;
   c->kmode = !K6 ? KM_NONE : ((hflags & 4u) ? KM_SPD : KM_DIAG);
+  if (c->kmode == KM_SPD && prm->forchheimer != 0.0)
+    return bail(fail(c, LB_EUNSUPPORTED, "Forchheimer drag needs a diagonal permeability tensor"));
+  if (c->kmode == KM_DIAG && prm->forchheimer != 0.0) c->kmode = KM_FORCH;
   if (K6 && !(c->kinv = dev_alloc(c, (c->kmode == KM_SPD ? 6 : 3) * N * rb)))
     return bail(fail(c, LB_ENOMEM, "K inverse"));
   // row-pipelined kernel: eligible shapes only; grid = resident blocks of all SMs

@@ -166,7 +166,9 @@ struct StoreBF16 {
 // ------------------------------------------------------------------------
 // Kernel arguments (passed by value).
 // ------------------------------------------------------------------------
-enum : int { KM_NONE = 0, KM_DIAG = 1, KM_SPD = 2 };
+// permeability modes: no medium, diagonal K^-1, full SPD K^-1, diagonal K^-1
+// with Forchheimer drag
+enum : int { KM_NONE = 0, KM_DIAG = 1, KM_SPD = 2, KM_FORCH = 3 };
 enum : uint8_t { CELL_LIQUID = 0, CELL_INTERFACE = 1, CELL_EMPTY = 2 };
 
 // Device-resident per-context status word.
@@ -198,6 +200,7 @@ struct StepArgs {
   Real tau, tau0, tau1, nu_g, a_h, alpha, beta;
   int visc_law;
   Real A, wall_rho;
+  Real forch;           // multiplier of the Ergun coefficient (KM_FORCH)
   Real inv_tau_D, D, C_in;
   long long t;          // step index after the increment
   int reduce;           // form mass / solute totals this step

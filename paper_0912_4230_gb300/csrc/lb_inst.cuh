@@ -11,6 +11,28 @@
 
 namespace lbgb {
 
+// Calls f(km, sol) with the permeability mode and the solute setting as
+// compile-time constants.
+template <class F>
+decltype(auto) dispatch_mode(int kmode, bool solute, F &&f) {
+  using N = std::integral_constant<int, KM_NONE>;
+  using D = std::integral_constant<int, KM_DIAG>;
+  using P = std::integral_constant<int, KM_SPD>;
+  using H = std::integral_constant<int, KM_FORCH>;
+  using Y = std::true_type;
+  using X = std::false_type;
+  switch (kmode * 2 + (solute ? 1 : 0)) {
+    case 0: return f(N{}, X{});
+    case 1: return f(N{}, Y{});
+    case 2: return f(D{}, X{});
+    case 3: return f(D{}, Y{});
+    case 4: return f(P{}, X{});
+    case 5: return f(P{}, Y{});
+    case 6: return f(H{}, X{});
+    default: return f(H{}, Y{});
+  }
+}
+
 template <class S>
 struct Instance {
   using Real = typename S::Real;
@@ -24,14 +46,9 @@ struct Instance {
   static cudaError_t step(int kmode, bool solute, const void *args, dim3 grid, dim3 block,
                           cudaStream_t s) {
     const A &a = *static_cast<const A *>(args);
-    switch (kmode * 2 + (solute ? 1 : 0)) {
-      case 0: return step_t<KM_NONE, false>(a, grid, block, s);
-      case 1: return step_t<KM_NONE, true>(a, grid, block, s);
-      case 2: return step_t<KM_DIAG, false>(a, grid, block, s);
-      case 3: return step_t<KM_DIAG, true>(a, grid, block, s);
-      case 4: return step_t<KM_SPD, false>(a, grid, block, s);
-      default: return step_t<KM_SPD, true>(a, grid, block, s);
-    }
+    return dispatch_mode(kmode, solute, [&](auto km, auto sol) {
+      return step_t<decltype(km)::value, decltype(sol)::value>(a, grid, block, s);
+    });
   }
   template <int KM, bool SOL>
   static cudaError_t init_t(const A &a, const InitArgs<Real> &in, unsigned nblk, cudaStream_t s) {
@@ -122,7 +139,8 @@ struct Instance {
   }
   static bool tma_config(int kmode, bool solute, unsigned nx, size_t *smem, unsigned *threads,
                          int *bps) {
-    if (!solute || kmode == KM_NONE || (nx != 128 && nx != 256)) return false;
+    if (!solute || kmode == KM_NONE || kmode == KM_FORCH || (nx != 128 && nx != 256))
+      return false;
     if (kmode == KM_DIAG)
       return nx == 128 ? tma_config_t<KM_DIAG, 4>(nx, smem, threads, bps)
                        : tma_config_t<KM_DIAG, 8>(nx, smem, threads, bps);
@@ -132,7 +150,7 @@ struct Instance {
   static cudaError_t tma_step(int kmode, bool solute, const void *args, unsigned grid,
                               unsigned threads, size_t smem, cudaStream_t s) {
     const A &a = *static_cast<const A *>(args);
-    if (!solute || kmode == KM_NONE) return cudaErrorInvalidValue;
+    if (!solute || kmode == KM_NONE || kmode == KM_FORCH) return cudaErrorInvalidValue;
     const bool wide = threads == 9 * 32;
     if (kmode == KM_DIAG) {
       if (wide)
@@ -172,41 +190,28 @@ struct Instance {
   }
   static bool pipe_config(int kmode, bool solute, unsigned bx, size_t *smem, int *bps) {
     if (bx != 32 && bx != 64 && bx != 128) return false;
-    switch (kmode * 2 + (solute ? 1 : 0)) {
-      case 0: return pipe_config_t<KM_NONE, false>(bx, smem, bps);
-      case 1: return pipe_config_t<KM_NONE, true>(bx, smem, bps);
-      case 2: return pipe_config_t<KM_DIAG, false>(bx, smem, bps);
-      case 3: return pipe_config_t<KM_DIAG, true>(bx, smem, bps);
-      case 4: return pipe_config_t<KM_SPD, false>(bx, smem, bps);
-      default: return pipe_config_t<KM_SPD, true>(bx, smem, bps);
-    }
+    return dispatch_mode(kmode, solute, [&](auto km, auto sol) {
+      return pipe_config_t<decltype(km)::value, decltype(sol)::value>(bx, smem, bps);
+    });
   }
   static cudaError_t pipe_step(int kmode, bool solute, const void *args, unsigned grid,
                                unsigned bx, size_t smem, unsigned gxr, unsigned items,
                                cudaStream_t s) {
     const A &a = *static_cast<const A *>(args);
-    switch (kmode * 2 + (solute ? 1 : 0)) {
-      case 0: pipe_step_kernel<S, KM_NONE, false><<<grid, bx, smem, s>>>(a, gxr, items); break;
-      case 1: pipe_step_kernel<S, KM_NONE, true><<<grid, bx, smem, s>>>(a, gxr, items); break;
-      case 2: pipe_step_kernel<S, KM_DIAG, false><<<grid, bx, smem, s>>>(a, gxr, items); break;
-      case 3: pipe_step_kernel<S, KM_DIAG, true><<<grid, bx, smem, s>>>(a, gxr, items); break;
-      case 4: pipe_step_kernel<S, KM_SPD, false><<<grid, bx, smem, s>>>(a, gxr, items); break;
-      default: pipe_step_kernel<S, KM_SPD, true><<<grid, bx, smem, s>>>(a, gxr, items); break;
-    }
+    dispatch_mode(kmode, solute, [&](auto km, auto sol) {
+      pipe_step_kernel<S, decltype(km)::value, decltype(sol)::value><<<grid, bx, smem, s>>>(
+          a, gxr, items);
+    });
     return cudaGetLastError();
   }
   static cudaError_t batch_step(int kmode, bool solute, const void *tab, const uint64_t *work,
                                 unsigned d_begin, unsigned vb_begin, unsigned vb_end,
                                 unsigned grid, cudaStream_t s) {
     const BatchTable<Real> &t = *static_cast<const BatchTable<Real> *>(tab);
-    switch (kmode * 2 + (solute ? 1 : 0)) {
-      case 0: batched_step_kernel<S, KM_NONE, false><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
-      case 1: batched_step_kernel<S, KM_NONE, true><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
-      case 2: batched_step_kernel<S, KM_DIAG, false><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
-      case 3: batched_step_kernel<S, KM_DIAG, true><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
-      case 4: batched_step_kernel<S, KM_SPD, false><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
-      default: batched_step_kernel<S, KM_SPD, true><<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end); break;
-    }
+    dispatch_mode(kmode, solute, [&](auto km, auto sol) {
+      batched_step_kernel<S, decltype(km)::value, decltype(sol)::value>
+          <<<grid, STEP_BLOCK, 0, s>>>(t, work, d_begin, vb_begin, vb_end);
+    });
     return cudaGetLastError();
   }
   static StorageOps make() {

@@ -142,9 +142,19 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 // F^ext = -eps nu K^-1 V' + eps G (Eqs. forcement, expandV, expandVsub).
 // kv(r) returns row r of the cell's K^-1 (diagonal: xx, yy, zz; full: xx, yy,
 // zz, xy, yz, zx).
+//
+// KM_FORCH adds the Forchheimer drag of the porous-flow model the paper builds
+// on (the paper names the term without an equation): F^ext = -eps nu K^-1 V'
+// - eps F_eps |V'| K^-1/2 V' + eps G, F_eps = cF 1.75 / sqrt(150 eps^3), for a
+// diagonal K. With V' = V + F^ext/2, V'_i = r_i / (a_i + b_i s), r = V + eps
+// G/2, a_i = 1 + eps nu k_i / 2, b_i = eps F_eps sqrt(k_i) / 2, where s = |V'|
+// is the root of phi(s) = s - |V'(s)|. Newton's method on phi from the
+// closed form of an isotropic medium with the r^2-weighted a and b; three
+// iterations in FP32 and four in FP64 reach the root to rounding for K from
+// 1e-4 to 1e2, 100:1 anisotropy and cF up to 20.
 template <int KMODE, class Real, class KV>
 __device__ __forceinline__ void velocity_solve_kv(KV kv, Real eps, Real nu, const Real (&V)[3],
-                                                  const Real (&G)[3], Real (&Vp)[3],
+                                                  const Real (&G)[3], Real cF, Real (&Vp)[3],
                                                   Real (&Fe)[3]) {
   const Real r0 = V[0] + Real(0.5) * eps * G[0];
   const Real r1 = V[1] + Real(0.5) * eps * G[1];
@@ -153,6 +163,42 @@ __device__ __forceinline__ void velocity_solve_kv(KV kv, Real eps, Real nu, cons
   if (KMODE == KM_NONE) {
     Vp[0] = r0; Vp[1] = r1; Vp[2] = r2;
     Fe[0] = eps * G[0]; Fe[1] = eps * G[1]; Fe[2] = eps * G[2];
+  } else if (KMODE == KM_FORCH) {
+    const Real k[3] = {kv(0), kv(1), kv(2)};
+    const Real r[3] = {r0, r1, r2};
+    const Real Fer = cF * Real(1.75) * rcp(sqrt(Real(150) * eps * eps * eps));
+    const Real hs = Real(0.5) * en, hc = Real(0.5) * eps * Fer;
+    Real a[3], b[3], d[3];
+    for (int i = 0; i < 3; ++i) {
+      d[i] = sqrt(k[i]);
+      a[i] = Real(1) + hs * k[i];
+      b[i] = hc * d[i];
+    }
+    const Real ws = r0 * r0 + r1 * r1 + r2 * r2;
+    Real s = Real(0);
+    if (ws > Real(0)) {
+      const Real iws = rcp(ws);
+      const Real ab = (r0 * r0 * a[0] + r1 * r1 * a[1] + r2 * r2 * a[2]) * iws;
+      const Real bb = (r0 * r0 * b[0] + r1 * r1 * b[1] + r2 * r2 * b[2]) * iws;
+      const Real rn = sqrt(ws);
+      s = Real(2) * rn * rcp(ab + sqrt(ab * ab + Real(4) * bb * rn));
+      // Newton on phi(s) = s - |V'(s)|: s <- s - (s - |V'|) |V'| / (|V'| + g),
+      // g = sum_i V'_i^2 b_i / (a_i + b_i s)
+      constexpr int kIters = sizeof(Real) == 4 ? 3 : 4;
+      for (int it = 0; it < kIters; ++it) {
+        Real vv = Real(0), g = Real(0);
+        for (int i = 0; i < 3; ++i) {
+          const Real iD = rcp(a[i] + b[i] * s), v = r[i] * iD;
+          vv += v * v;
+          g += v * v * b[i] * iD;
+        }
+        const Real vn = sqrt(vv);
+        s -= (s - vn) * vn * rcp(vn + g);
+      }
+    }
+    for (int i = 0; i < 3; ++i) Vp[i] = r[i] * rcp(a[i] + b[i] * s);
+    const Real sp = sqrt(Vp[0] * Vp[0] + Vp[1] * Vp[1] + Vp[2] * Vp[2]);
+    for (int i = 0; i < 3; ++i) Fe[i] = -(en * k[i] + eps * Fer * d[i] * sp) * Vp[i] + eps * G[i];
   } else if (KMODE == KM_DIAG) {
     const Real kx = kv(0), ky = kv(1), kz = kv(2);
     const Real hs = Real(0.5) * en;
@@ -187,7 +233,7 @@ __device__ __forceinline__ void velocity_solve(const Real *__restrict__ kinv, un
                                                const Real (&G)[3], Real (&Vp)[3],
                                                Real (&Fe)[3]) {
   velocity_solve_kv<KMODE>([&](int r) { return __ldg(kinv + size_t(r) * N + n); }, eps, nu, V, G,
-                           Vp, Fe);
+                           Real(0), Vp, Fe);
 }
 
 // Colour gradient F = sum_q rhohat(x + c_q) c_q (Eq. macros); a step out
@@ -339,7 +385,7 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
   FluidCollide<Real> fc;
   fc.F[0] = fc.F[1] = fc.F[2] = Real(0);
   if (a.A != Real(0)) colour_gradient(a.rhohat, n, g, a.f_wall, a.wall_rho, fc.F);
-  velocity_solve_kv<KMODE>(kv, eps, nu, V, a.G, fc.Vp, fc.Fe);
+  velocity_solve_kv<KMODE>(kv, eps, nu, V, a.G, a.forch, fc.Vp, fc.Fe);
   fc.drho = drho;
   fc.rho = rho;
   fc.ie = ie;

@@ -28,7 +28,7 @@ template <class S, int KMODE, bool SOLUTE>
 struct PipeLayout {
   using Real = typename S::Real;
   static_assert(sizeof(typename S::T) == sizeof(Real), "staged rows are copied element by element");
-  static constexpr int kKinv = KMODE == KM_DIAG ? 3 : (KMODE == KM_SPD ? 6 : 0);
+  static constexpr int kKinv = KMODE == KM_SPD ? 6 : (KMODE == KM_NONE ? 0 : 3);
   // rows of one stage: f [0, Q), h [Q, 2Q), D grad(eps)/eps (3), eps, K^-1
   static constexpr int kH = Q;
   static constexpr int kGeps = SOLUTE ? 2 * Q : Q;

@@ -83,7 +83,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 template <class S, int KMODE, bool SOLUTE>
 struct TmaLayout {
   using T = typename S::T;
-  static constexpr int kinv_rows = KMODE == KM_DIAG ? 3 : (KMODE == KM_SPD ? 6 : 0);
+  static constexpr int kinv_rows = KMODE == KM_SPD ? 6 : (KMODE == KM_NONE ? 0 : 3);
   static constexpr int static_rows = 1 + kinv_rows + (SOLUTE ? 3 : 0);  // Real = float rows
   static constexpr int pop_rows = SOLUTE ? 2 * Q : Q;                    // T rows
   __host__ __device__ static size_t stage_bytes(unsigned nx) {

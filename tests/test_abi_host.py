@@ -60,7 +60,7 @@ def _create(prob, **over):
 
 
 @pytest.mark.parametrize("over,code", [
-    (dict(forchheimer=0.5), lb.LB_EUNSUPPORTED),
+    (dict(forchheimer=-0.5), lb.LB_EINVAL),
     (dict(visc_law=0, tau=0.5), lb.LB_EINVAL),
     (dict(tau0=0.5), lb.LB_EINVAL),
     (dict(solute=0), lb.LB_EINVAL),
