@@ -278,29 +278,37 @@ static void cell_coords(const orc *o, int64_t n, int *x, int *y, int *z)
 /* Where the population arriving at cell (x,y,z) along c_q comes from during
  * the stream step (Eq. lbe2: the cell at x - c_q feeds f_q at x). Periodic
  * faces wrap. Reading (walls): a face of kind WALL, or a solid source cell,
- * gives halfway bounce-back; precedence WALL > INLET > OUTLET when a diagonal
- * leaves through two faces. Returns the source index or an ORC_SRC_ class. */
+ * gives halfway bounce-back. Open faces (readings R9, R23): a population that
+ * enters through a face of kind INLET, OUTLET, PRESSURE or VELOCITY takes that
+ * face's rule. Precedence when a diagonal leaves through two faces: WALL >
+ * VELOCITY > PRESSURE > INLET > OUTLET, and between two faces of one kind the
+ * one on the lower axis. Returns the source index or an ORC_SRC_ class; *face
+ * (may be NULL) receives 2 axis + side of the deciding face. */
 static int64_t pull_source(const orc *o, const int32_t kinds[3][2], int x, int y,
-                           int z, int q)
+                           int z, int q, int *face)
 {
   int c[3] = {x - CV[q][0], y - CV[q][1], z - CV[q][2]};
   int n[3] = {o->p.nx, o->p.ny, o->p.nz};
-  int wall = 0, inlet = 0, outlet = 0;
+  /* rank of each kind in the precedence order (0 = none) and its face */
+  static const int rank[6] = {0, 5, 2, 1, 3, 4};
+  static const int64_t cls[6] = {0, ORC_SRC_BOUNCE, ORC_SRC_INLET, ORC_SRC_OUTLET,
+                                 ORC_SRC_PRESSURE, ORC_SRC_VELOCITY};
+  int best = 0, best_face = -1;
   for (int a = 0; a < 3; a++) {
     if (c[a] >= 0 && c[a] < n[a]) continue;
-    int k = kinds[a][c[a] < 0 ? 0 : 1];
-    if (k == ORC_PERIODIC)
+    int side = c[a] < 0 ? 0 : 1;
+    int k = kinds[a][side];
+    if (k == ORC_PERIODIC) {
       c[a] = (c[a] + n[a]) % n[a];
-    else if (k == ORC_WALL)
-      wall = 1;
-    else if (k == ORC_INLET)
-      inlet = 1;
-    else
-      outlet = 1;
+      continue;
+    }
+    if (best == 0 || rank[k] > rank[best]) {
+      best = k;
+      best_face = 2 * a + side;
+    }
   }
-  if (wall) return ORC_SRC_BOUNCE;
-  if (inlet) return ORC_SRC_INLET;
-  if (outlet) return ORC_SRC_OUTLET;
+  if (face) *face = best_face;
+  if (best != 0) return cls[best];
   int64_t s = cell_index(o, c[0], c[1], c[2]);
   if (o->solid[s]) return ORC_SRC_BOUNCE;
   return s;
@@ -320,12 +328,17 @@ static int64_t neighbor(const orc *o, const int32_t kinds[3][2], int x, int y, i
   return cell_index(o, c[0], c[1], c[2]);
 }
 
+/* fluid faces: PERIODIC, WALL, PRESSURE, VELOCITY; solute faces: PERIODIC,
+ * WALL, INLET, OUTLET; a pair of opposite faces is periodic on both sides or
+ * on neither */
 static int valid_faces(const int32_t k[3][2], int fluid)
 {
   for (int a = 0; a < 3; a++) {
     for (int s = 0; s < 2; s++) {
-      if (k[a][s] < 0 || k[a][s] > 3) return 0;
-      if (fluid && k[a][s] > 1) return 0;
+      int v = k[a][s];
+      if (fluid ? !(v == ORC_PERIODIC || v == ORC_WALL || v == ORC_PRESSURE || v == ORC_VELOCITY)
+                : (v < 0 || v > 3))
+        return 0;
     }
     if ((k[a][0] == ORC_PERIODIC) != (k[a][1] == ORC_PERIODIC)) return 0;
   }
@@ -381,6 +394,13 @@ orc *orc_create(const orc_params *p, const double *eps, const double *K6,
   if (p->solute && !(p->tau_D > 0.5)) return NULL;
   if (p->free_surface && (p->solute || K6)) return NULL;
   if (p->forchheimer < 0.0) return NULL;
+  {
+    int open_fluid = 0;
+    for (int a = 0; a < 3; a++)
+      for (int s = 0; s < 2; s++)
+        if (p->bc[a][s] == ORC_PRESSURE || p->bc[a][s] == ORC_VELOCITY) open_fluid = 1;
+    if (open_fluid && (p->free_surface || p->A != 0.0)) return NULL;
+  }
   if (p->forchheimer != 0.0 && K6) {  /* the Forchheimer reading needs a diagonal K */
     int64_t N0 = (int64_t)p->nx * p->ny * p->nz;
     for (int64_t n = 0; n < N0; n++)
@@ -557,6 +577,31 @@ static int active(const orc *o, int64_t n)
   return !o->solid[n] && o->type[n] != ORC_EMPTY;
 }
 
+/* Density and velocity j / rho of the cell's own post-collision populations
+ * (the previous step's output buffer). */
+static void post_collision_moments(const orc *o, int64_t n, double *rho, double *u)
+{
+  double r = 0, j[3] = {0, 0, 0};
+  for (int q = 0; q < Q; q++) {
+    double v = o->f[(int64_t)q * o->N + n];
+    r += v;
+    for (int a = 0; a < 3; a++) j[a] += v * CV[q][a];
+  }
+  *rho = r;
+  for (int a = 0; a < 3; a++) u[a] = j[a] / r;
+}
+
+/* Even part of the porous equilibrium (Eqs. equilc1, equilc2 without the
+ * terms odd in c_q): w_q rho (1 + 4.5 (c_q.u)^2 / eps - 1.5 u.u / eps). */
+static void feq_even(double rho, const double *u, double eps, double *out)
+{
+  double uu = dot3(u, u);
+  for (int q = 0; q < Q; q++) {
+    double cu = cdot(q, u);
+    out[q] = WT[q] * rho * (1.0 + 4.5 * cu * cu / eps - 1.5 * uu / eps);
+  }
+}
+
 /* Flowchart step f for the fluid lattice at one cell. Free surface (Eq.
  * equilempty): a population that would come from an empty cell is rebuilt as
  * f_q = f^eq_q + f^eq_qbar - f~_qbar(x) with the gas density 1 and the cell's
@@ -570,10 +615,27 @@ static void stream_fluid(orc *o, int64_t n)
   int have_gas_eq = 0;
   double ge[Q];
   for (int q = 0; q < Q; q++) {
-    int64_t s = pull_source(o, o->p.bc, x, y, z, q);
+    int face = -1;
+    int64_t s = pull_source(o, o->p.bc, x, y, z, q, &face);
     double v;
     if (s == ORC_SRC_BOUNCE) {
       v = o->f[(int64_t)OPP[q] * N + n];
+    } else if (s == ORC_SRC_PRESSURE) {
+      /* anti-bounce-back on the even part of the porous equilibrium at the
+       * face density rho_b = 3 eps P_b (P = rho c_s^2 / eps, Section 2), with
+       * the velocity of the cell's own post-collision populations */
+      double r, u[3], fe[Q];
+      post_collision_moments(o, n, &r, u);
+      double rb = 3.0 * o->eps[n] * o->p.face_P[face / 2][face % 2];
+      feq_even(rb, u, o->eps[n], fe);
+      v = -o->f[(int64_t)OPP[q] * N + n] + 2.0 * fe[q];
+    } else if (s == ORC_SRC_VELOCITY) {
+      /* bounce-back from a face moving with u_b: f_q = f~_qbar + 6 w_q rho
+       * (c_q . u_b), rho the cell's own post-collision density */
+      double r, u[3];
+      post_collision_moments(o, n, &r, u);
+      const double *ub = o->p.face_u[face / 2][face % 2];
+      v = o->f[(int64_t)OPP[q] * N + n] + 6.0 * WT[q] * r * cdot(q, ub);
     } else if (o->p.free_surface && o->type[s] == ORC_EMPTY) {
       if (!have_gas_eq) {
         double r, u[3];
@@ -614,7 +676,7 @@ static void stream_solute(orc *o, int64_t n)
   for (int a = 0; a < 3; a++) Vin[a] = j[a] / r + D * o->geps[3 * n + a];
   double fin = 0.0, fout = 0.0;
   for (int q = 0; q < Q; q++) {
-    int64_t s = pull_source(o, o->p.sbc, x, y, z, q);
+    int64_t s = pull_source(o, o->p.sbc, x, y, z, q, NULL);
     double v;
     if (s == ORC_SRC_BOUNCE) {
       v = o->h[(int64_t)OPP[q] * N + n];
@@ -974,7 +1036,7 @@ int orc_neighbors(const orc *o, int32_t lattice, int32_t *src)
       if (o->solid[n])
         v = ORC_SRC_NOT_UPDATED;
       else
-        v = (int32_t)pull_source(o, lattice ? o->p.sbc : o->p.bc, x, y, z, q);
+        v = (int32_t)pull_source(o, lattice ? o->p.sbc : o->p.bc, x, y, z, q, NULL);
       src[(int64_t)q * N + n] = v;
     }
   }

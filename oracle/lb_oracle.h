@@ -20,15 +20,18 @@
 extern "C" {
 #endif
 
-enum { ORC_PERIODIC = 0, ORC_WALL = 1, ORC_INLET = 2, ORC_OUTLET = 3 };
+enum { ORC_PERIODIC = 0, ORC_WALL = 1, ORC_INLET = 2, ORC_OUTLET = 3,
+       ORC_PRESSURE = 4, ORC_VELOCITY = 5 };
 enum { ORC_LIQUID = 0, ORC_INTERFACE = 1, ORC_EMPTY = 2 };
 /* classes reported by orc_neighbors for populations that do not come from a cell */
 enum { ORC_SRC_NOT_UPDATED = -1, ORC_SRC_BOUNCE = -2, ORC_SRC_INLET = -3,
-       ORC_SRC_OUTLET = -4, ORC_SRC_EMPTY = -5 };
+       ORC_SRC_OUTLET = -4, ORC_SRC_EMPTY = -5, ORC_SRC_PRESSURE = -6,
+       ORC_SRC_VELOCITY = -7 };
 
 typedef struct {
   int32_t nx, ny, nz;
-  int32_t bc[3][2];   /* fluid lattice, [axis][low/high side]: PERIODIC or WALL */
+  int32_t bc[3][2];   /* fluid lattice, [axis][low/high side]: PERIODIC, WALL,
+                         PRESSURE or VELOCITY */
   int32_t sbc[3][2];  /* solute lattice: PERIODIC, WALL, INLET or OUTLET */
   double tau;         /* relaxation time for visc_law 0 */
   int32_t visc_law;   /* 0 constant tau, 1 tau linear in C, 2 Eq. nuall */
@@ -44,6 +47,8 @@ typedef struct {
   int32_t threads;    /* OpenMP threads, <= 0 = library default */
   double forchheimer; /* multiplier c_F of the Ergun coefficient F_eps (0 = no
                          Forchheimer drag); needs a diagonal or no K */
+  double face_P[3][2];      /* pressure of each PRESSURE face */
+  double face_u[3][2][3];   /* velocity of each VELOCITY face */
 } orc_params;
 
 typedef struct orc orc;

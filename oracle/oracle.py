@@ -44,6 +44,7 @@ class OrcParams(ctypes.Structure):
         ("solute", c_int32), ("tau_D", c_double), ("C_in", c_double),
         ("free_surface", c_int32), ("threads", c_int32),
         ("forchheimer", c_double),
+        ("face_P", (c_double * 2) * 3), ("face_u", ((c_double * 3) * 2) * 3),
     ]
 
 
@@ -127,6 +128,13 @@ def make_params(prob, threads: int = 0) -> OrcParams:
     p.free_surface = int(k.get("free_surface", 0))
     p.threads = threads
     p.forchheimer = k.get("forchheimer", 0.0)
+    fp = k.get("face_P", ((0.0, 0.0),) * 3)
+    fu = k.get("face_u", (((0.0,) * 3,) * 2,) * 3)
+    for a in range(3):
+        for s in range(2):
+            p.face_P[a][s] = fp[a][s]
+            for i in range(3):
+                p.face_u[a][s][i] = fu[a][s][i]
     return p
 
 

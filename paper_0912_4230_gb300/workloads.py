@@ -30,6 +30,7 @@ Q = 19
 PERIODIC, WALL, INLET, OUTLET = 0, 1, 2, 3
 LIQUID, INTERFACE, EMPTY = 0, 1, 2
 
+PRESSURE, VELOCITY = 4, 5     # fluid faces only
 ALL_PERIODIC = ((PERIODIC, PERIODIC),) * 3
 
 
@@ -168,6 +169,60 @@ def forchheimer_bulk(K=(1.0, 1.0, 1.0), eps=0.5, tau=0.8, G=(6e-3, 0.0, 0.0), cF
     return _base("forchheimer_bulk", n, n, n, ALL_PERIODIC, ALL_PERIODIC,
                  dict(tau=tau, G=tuple(G), forchheimer=cF), _uniform(N, eps), K6.ravel(),
                  steps=steps, storage="fp64")
+
+
+def _faces(P=None, u=None):
+    fp = [[0.0, 0.0] for _ in range(3)]
+    fu = [[[0.0] * 3, [0.0] * 3] for _ in range(3)]
+    for (a, side), v in (P or {}).items():
+        fp[a][side] = float(v)
+    for (a, side), v in (u or {}).items():
+        fu[a][side] = [float(c) for c in v]
+    return tuple(tuple(x) for x in fp), tuple(tuple(tuple(y) for y in x) for x in fu)
+
+
+def pressure_darcy(n=64, P_in=1.0 / 3.0 + 2e-4, P_out=1.0 / 3.0 - 2e-4, K=1.0, eps=0.5,
+                   tau=0.8, steps=4000) -> Problem:
+    """Flow through a uniform medium between two PRESSURE faces along x
+    (periodic y and z, one cell thick): the steady mass flux is uniform and
+    the density falls linearly between the face densities 3 eps P."""
+    N = n
+    bc = ((PRESSURE, PRESSURE), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC))
+    fp, fu = _faces(P={(0, 0): P_in, (0, 1): P_out})
+    K6 = np.zeros((N, 6), np.float32)
+    K6[:, 0:3] = K
+    return _base("pressure_darcy", n, 1, 1, bc, ((OUTLET, OUTLET),) + ALL_PERIODIC[1:],
+                 dict(tau=tau, face_P=fp, face_u=fu), _uniform(N, eps), K6.ravel(),
+                 rho0=_uniform(N, 3.0 * eps * 0.5 * (P_in + P_out)), steps=steps,
+                 storage="fp64")
+
+
+def velocity_couette(nz=32, u_b=1e-3, K=16.0, eps=0.6, tau=0.8, steps=6000) -> Problem:
+    """Porous Couette flow: the z-low face moves with u_b along x (VELOCITY),
+    the z-high face is a wall, x and y periodic; the steady profile solves
+    Brinkman's equation nu V'' = eps nu V / K."""
+    N = nz
+    bc = ((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (VELOCITY, WALL))
+    sbc = ((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (WALL, WALL))
+    fp, fu = _faces(u={(2, 0): (u_b, 0.0, 0.0)})
+    K6 = np.zeros((N, 6), np.float32)
+    K6[:, 0:3] = K
+    return _base("velocity_couette", 1, 1, nz, bc, sbc, dict(tau=tau, face_P=fp, face_u=fu),
+                 _uniform(N, eps), K6.ravel(), steps=steps, storage="fp64")
+
+
+def inflow_darcy(n=64, u_in=2e-4, P_out=1.0 / 3.0, K=1.0, eps=0.5, tau=0.8,
+                 steps=4000) -> Problem:
+    """Flow rate imposed at the x-low face (VELOCITY, normal inflow u_in),
+    pressure at the x-high face, uniform medium, periodic y and z."""
+    N = n
+    bc = ((VELOCITY, PRESSURE), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC))
+    fp, fu = _faces(P={(0, 1): P_out}, u={(0, 0): (u_in, 0.0, 0.0)})
+    K6 = np.zeros((N, 6), np.float32)
+    K6[:, 0:3] = K
+    return _base("inflow_darcy", n, 1, 1, bc, ((OUTLET, OUTLET),) + ALL_PERIODIC[1:],
+                 dict(tau=tau, face_P=fp, face_u=fu), _uniform(N, eps), K6.ravel(),
+                 rho0=_uniform(N, 3.0 * eps * P_out), steps=steps, storage="fp64")
 
 
 def _random_rotations(nblocks, seed):
@@ -342,9 +397,12 @@ def eps_bands(nx=32, ny=4, nz=4, C=0.5, tau_D=0.8, smooth=True) -> Problem:
 
 
 def random_medium(nx=8, ny=6, nz=5, seed=1, solid_frac=0.1, walls=True, solute=True,
-                  inlet=True, spd=True, visc_law=1, A=0.0, u_amp=0.02) -> Problem:
+                  inlet=True, spd=True, visc_law=1, A=0.0, u_amp=0.02,
+                  open_faces=False) -> Problem:
     """Small heterogeneous problem exercising every feature at once (random
-    porosity, SPD K, solids, walls, inlet/outlet, random initial velocity)."""
+    porosity, SPD K, solids, walls, inlet/outlet, random initial velocity).
+    open_faces: fluid faces VELOCITY / PRESSURE along x and PRESSURE along z
+    (solute INLET / OUTLET on both), walls along y."""
     rng = _rng(seed)
     N = nx * ny * nz
     eps = rng.uniform(0.3, 1.0, N)
@@ -365,10 +423,19 @@ def random_medium(nx=8, ny=6, nz=5, seed=1, solid_frac=0.1, walls=True, solute=T
         sbc[1] = [WALL, WALL]
     if inlet and solute:
         sbc[2] = [INLET, OUTLET]
+    extra = {}
+    if open_faces:
+        bc[0] = [VELOCITY, PRESSURE]
+        bc[2] = [PRESSURE, PRESSURE]
+        sbc[0] = [INLET, OUTLET]
+        sbc[2] = [INLET, OUTLET]
+        fp, fu = _faces(P={(0, 1): 0.34, (2, 0): 0.345, (2, 1): 0.33},
+                        u={(0, 0): (0.01, 0.004, -0.003)})
+        extra = dict(face_P=fp, face_u=fu)
     params = dict(tau=0.9, visc_law=visc_law if solute else 0, tau0=0.7, tau1=1.3,
                   nu_g=0.1, a=0.05, alpha=0.01, beta=0.5,
                   G=(2e-4, -1e-4, 3e-4), solute=int(solute), tau_D=0.75, C_in=1.0,
-                  A=A, wall_rho=0.3)
+                  A=A, wall_rho=0.3, **extra)
     rho0 = (1.0 + 0.01 * rng.uniform(-1, 1, N)).astype(np.float32)
     u0 = (u_amp * rng.uniform(-1, 1, 3 * N)).astype(np.float32)
     C0 = rng.uniform(0, 1, N).astype(np.float32) if solute else None

@@ -41,6 +41,10 @@ def brute_sources(p, kinds):
                     crossed.add(kind)
             if W.WALL in crossed:
                 out[q, n] = -2
+            elif W.VELOCITY in crossed:
+                out[q, n] = -7
+            elif W.PRESSURE in crossed:
+                out[q, n] = -6
             elif W.INLET in crossed:
                 out[q, n] = -3
             elif W.OUTLET in crossed:
@@ -58,6 +62,17 @@ def test_neighbor_table_brute_force(dims, seed):
     o = O.Oracle(p)
     for lattice, kinds in ((0, p.bc), (1, p.sbc)):
         assert np.array_equal(o.neighbors(lattice), brute_sources(p, kinds))
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 5), (5, 3, 4)])
+def test_neighbor_table_brute_force_open_faces(dims):
+    """Pressure and velocity faces, with their precedence on edges."""
+    p = W.random_medium(*dims, seed=4, solid_frac=0.2, open_faces=True)
+    o = O.Oracle(p)
+    for lattice, kinds in ((0, p.bc), (1, p.sbc)):
+        assert np.array_equal(o.neighbors(lattice), brute_sources(p, kinds))
+    src = o.neighbors(0)
+    assert (src == -6).any() and (src == -7).any()
 
 
 def test_periodic_streaming_is_a_permutation():
