@@ -54,12 +54,21 @@ enum {
   LB_EUNSUPPORTED = -6   /* valid request outside what this build implements */
 };
 
-/* Face kinds, per axis and side. The fluid lattice takes PERIODIC or WALL
- * (halfway bounce-back, "impermeability" in Section 4). The solute lattice
+/* Face kinds, per axis and side. The fluid lattice takes PERIODIC, WALL
+ * (halfway bounce-back, "impermeability" in Section 4), PRESSURE or VELOCITY
+ * (the "pressures, flow rate" of Section 4, which gives no method: a
+ * population entering through a PRESSURE face is -f~_qbar(x) + 2 w_q rho_b (1
+ * + 4.5 (c_q.u)^2/eps - 1.5 u.u/eps), rho_b = 3 eps(x) face_P (P = rho
+ * c_s^2 / eps of Section 2), u the velocity of the cell's own post-collision
+ * populations; through a VELOCITY face it is f~_qbar(x) + 6 w_q rho (c_q .
+ * face_u), rho the cell's own post-collision density). The solute lattice
  * takes PERIODIC, WALL, INLET (populations entering through the face carry
  * the equilibrium of Eq. equild at concentration C_in) or OUTLET
- * (zero-gradient outflow). Both sides of an axis are periodic or neither. */
-enum { LB_BC_PERIODIC = 0, LB_BC_WALL = 1, LB_BC_INLET = 2, LB_BC_OUTLET = 3 };
+ * (zero-gradient outflow). Both sides of an axis are periodic or neither.
+ * A diagonal leaving through two faces takes the first of WALL, VELOCITY,
+ * PRESSURE, INLET, OUTLET, and of two faces of one kind the lower axis. */
+enum { LB_BC_PERIODIC = 0, LB_BC_WALL = 1, LB_BC_INLET = 2, LB_BC_OUTLET = 3,
+       LB_BC_PRESSURE = 4, LB_BC_VELOCITY = 5 };
 
 /* Population storage (the collision always runs in FP32, or FP64 for
  * LB_STORE_FP64). FP32 and FP64 store f_q - w_q and h_q. FP16DEV and BF16DEV
@@ -74,7 +83,8 @@ enum { LB_CELL_LIQUID = 0, LB_CELL_INTERFACE = 1, LB_CELL_EMPTY = 2 };
 
 /* Classes returned by lb_debug_neighbors for populations not pulled from a
  * cell. */
-enum { LB_SRC_NOT_UPDATED = -1, LB_SRC_BOUNCE = -2, LB_SRC_INLET = -3, LB_SRC_OUTLET = -4 };
+enum { LB_SRC_NOT_UPDATED = -1, LB_SRC_BOUNCE = -2, LB_SRC_INLET = -3, LB_SRC_OUTLET = -4,
+       LB_SRC_PRESSURE = -6, LB_SRC_VELOCITY = -7 };
 
 typedef struct {
   int32_t nx, ny, nz;   /* lattice size, each >= 1 */
@@ -119,7 +129,10 @@ typedef struct {
                            inputs to shared memory (cp.async) while it computes
                            the current one (FP32/FP64 storage, no free surface).
                            Kernels 2 and 3 return LB_EUNSUPPORTED where they do
-                           not apply. All compute the same arithmetic. */
+                           not apply (also with PRESSURE or VELOCITY faces). All
+                           compute the same arithmetic. */
+  double face_P[3][2];      /* pressure of each PRESSURE face [axis][side] */
+  double face_u[3][2][3];   /* velocity of each VELOCITY face [axis][side][xyz] */
 } lb_params;
 
 /* Create a lattice (flowchart of Section 4: the porosity field, the
@@ -135,9 +148,9 @@ typedef struct {
  *             it bounce back).
  * Returns LB_EINVAL for bad sizes, face kinds, tau <= 1/2, eps out of range or
  * a K that fails a Cholesky test, forchheimer < 0; LB_EUNSUPPORTED for
- * forchheimer != 0 with a non-diagonal K, or free_surface together with
- * solute or K6; LB_ENOMEM/LB_ECUDA on device failures. *out is NULL on
- * failure. */
+ * forchheimer != 0 with a non-diagonal K, free_surface together with solute
+ * or K6, or PRESSURE/VELOCITY faces together with free_surface or A != 0;
+ * LB_ENOMEM/LB_ECUDA on device failures. *out is NULL on failure. */
 int lb_create(const lb_domain *domain, const float *porosity, const float *K6,
               const uint8_t *solid, const lb_params *params, lb_ctx **out);
 
@@ -188,7 +201,8 @@ int lb_autotune(lb_ctx *ctx, int32_t reps, int32_t *choice);
 
 /* Advance several lattices by the same n steps (continuous batching; no
  * counterpart in the paper). Per step, a lattice whose per-cell launch alone
- * fills the GPU (at least 6 blocks per SM) takes that launch; the smaller
+ * fills the GPU (at least 6 blocks per SM), or that has pressure or velocity
+ * faces, takes that launch; the smaller
  * lattices share one persistent launch per 64 lattices over a work list of
  * their cell blocks, their arguments travelling in the launch's parameters.
  * Each lattice computes exactly what lb_step(n) with the per-cell kernel

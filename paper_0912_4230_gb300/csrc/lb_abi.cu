@@ -46,7 +46,9 @@ struct lb_ctx {
   } pipe;
   int kmode = KM_NONE;
   bool solute = false, fs = false, has_solid = false, flux = false;
-  unsigned f_wall = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
+  unsigned f_wall = 0, f_press = 0, f_vel = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
+  bool open_faces = false;  // pressure or velocity faces: per-cell kernel only
+  void *face = nullptr;  // per-face values of pressure / velocity faces (24 Real)
   long long t = 0;
   long long n_live = 0;
   int cur = 0;
@@ -161,6 +163,9 @@ void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
   a.nz = c->dom.nz;
   a.N = c->N;
   a.f_wall = c->f_wall;
+  a.f_press = c->f_press;
+  a.f_vel = c->f_vel;
+  a.face = static_cast<const Real *>(c->face);
   a.s_wall = c->s_wall;
   a.s_inlet = c->s_inlet;
   a.s_outlet = c->s_outlet;
@@ -225,7 +230,7 @@ int check_status(lb_ctx *c) {
 // Launch shape of the row-staged kernel for rows of bx threads: the grid is
 // the resident blocks of all SMs, at most one block per row.
 bool pipe_shape(const lb_ctx *c, unsigned bx, lb_ctx::PipeShape *ps) {
-  if (!c->ops->pipe_config) return false;
+  if (!c->ops->pipe_config || c->open_faces) return false;
   size_t smem = 0;
   int bps = 0, sms = 0, dev = 0;
   const bool ok = c->ops->pipe_config(c->kmode, c->solute, bx, &smem, &bps) &&
@@ -286,11 +291,16 @@ __global__ void wait_timeout_kernel(DevState *state, unsigned long long limit_ns
   if (!ok && threadIdx.x == 0) atomicOr(&state->status, 2u);
 }
 
+// fluid faces: PERIODIC, WALL, PRESSURE, VELOCITY; solute faces: PERIODIC,
+// WALL, INLET, OUTLET
 bool valid_faces(const int32_t (&k)[3][2], bool fluid) {
   for (int a = 0; a < 3; ++a) {
     for (int s = 0; s < 2; ++s) {
-      if (k[a][s] < 0 || k[a][s] > 3) return false;
-      if (fluid && k[a][s] > 1) return false;
+      const int v = k[a][s];
+      if (fluid ? !(v == LB_BC_PERIODIC || v == LB_BC_WALL || v == LB_BC_PRESSURE ||
+                    v == LB_BC_VELOCITY)
+                : (v < 0 || v > 3))
+        return false;
     }
     if ((k[a][0] == LB_BC_PERIODIC) != (k[a][1] == LB_BC_PERIODIC)) return false;
   }
@@ -337,6 +347,10 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (prm->solute && !(prm->tau_D > 0.5)) return fail(nullptr, LB_EINVAL, "tau_D <= 1/2");
   if (prm->free_surface && (prm->solute || K6))
     return fail(nullptr, LB_EUNSUPPORTED, "free surface with solute or permeability");
+  if ((face_mask(dom->bc, LB_BC_PRESSURE) | face_mask(dom->bc, LB_BC_VELOCITY)) &&
+      (prm->free_surface || prm->A != 0.0))
+    return fail(nullptr, LB_EUNSUPPORTED,
+                "pressure / velocity faces with a free surface or surface tension");
   if (prm->check_every < 0) return fail(nullptr, LB_EINVAL, "check_every < 0");
   if (prm->kernel < 0 || prm->kernel > 3) return fail(nullptr, LB_EINVAL, "kernel");
   const StorageOps *ops = nullptr;
@@ -379,6 +393,9 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   c->solute = prm->solute != 0;
   c->fs = prm->free_surface != 0;
   c->f_wall = face_mask(dom->bc, LB_BC_WALL);
+  c->f_press = face_mask(dom->bc, LB_BC_PRESSURE);
+  c->f_vel = face_mask(dom->bc, LB_BC_VELOCITY);
+  c->open_faces = (c->f_press | c->f_vel) != 0;
   c->s_wall = face_mask(dom->sbc, LB_BC_WALL);
   c->s_inlet = c->solute ? face_mask(dom->sbc, LB_BC_INLET) : 0;
   c->s_outlet = c->solute ? face_mask(dom->sbc, LB_BC_OUTLET) : 0;
@@ -415,6 +432,22 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (c->solute && !(c->geps = dev_alloc(c, 3 * N * rb))) return bail(fail(c, LB_ENOMEM, "geps"));
   if ((prm->A != 0.0 || c->fs) && !(c->rhohat = dev_alloc(c, N * rb)))
     return bail(fail(c, LB_ENOMEM, "rhohat"));
+  {
+    // per-face values: 3 x pressure (the face density over eps), velocity
+    double fv[24] = {};
+    for (int f = 0; f < 6; ++f) {
+      fv[f] = 3.0 * prm->face_P[f / 2][f % 2];
+      for (int i = 0; i < 3; ++i) fv[6 + 3 * f + i] = prm->face_u[f / 2][f % 2][i];
+    }
+    if (!(c->face = dev_alloc(c, 24 * rb))) return bail(fail(c, LB_ENOMEM, "face values"));
+    float ff[24];
+    for (int i = 0; i < 24; ++i) ff[i] = float(fv[i]);
+    cudaError_t e = cudaMemcpyAsync(c->face, rb == 8 ? static_cast<const void *>(fv) : ff,
+                                    24 * rb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host arrays leave scope
+    if (e != cudaSuccess)
+      return bail(fail(c, LB_ECUDA, std::string("face values: ") + cudaGetErrorString(e)));
+  }
   if (c->fs) {
     for (int b = 0; b < 2; ++b) {
       c->type[b] = static_cast<uint8_t *>(dev_alloc(c, N));
@@ -468,7 +501,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   sa.ny = dom->ny;
   sa.nz = dom->nz;
   sa.N = c->N;
-  sa.f_wall = c->f_wall;
+  sa.f_wall = c->f_wall | c->f_press | c->f_vel;  // links only to cells inside or wrapped
   sa.s_wall = c->s_wall;
   sa.s_open = face_mask(dom->sbc, LB_BC_INLET) | face_mask(dom->sbc, LB_BC_OUTLET);
   sa.eps_in = eps_in;
@@ -493,7 +526,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   // row-pipelined kernel: eligible shapes only; grid = resident blocks of all SMs
   // (automatic selection keeps the per-cell kernel: on GB300 at 128^3 it is
   // 2x faster than this row-pipelined form, which stays available on request)
-  if (prm->kernel != 1 && !c->fs && ops->tma_config) {
+  if (prm->kernel != 1 && !c->fs && !c->open_faces && ops->tma_config) {
     int bps = 0, sms = 0, dev = 0;
     if (ops->tma_config(c->kmode, c->solute, unsigned(dom->nx), &c->tma_smem, &c->tma_threads,
                         &bps) &&
@@ -644,7 +677,8 @@ int lb_step(lb_ctx *c, int64_t n) {
         CK(c, c->ops->pipe_step(c->kmode, c->solute, args, c->pipe.grid, c->pipe.bx,
                                 c->pipe.smem, c->pipe.gxr, c->pipe.items, c->stream));
       else
-        CK(c, c->ops->step(c->kmode, c->solute, args, c->sgrid, c->sblock, c->stream));
+        CK(c, c->ops->step(c->kmode, c->solute, c->open_faces, args, c->sgrid, c->sblock,
+                           c->stream));
       return int(LB_OK);
     });
     if (rc != LB_OK) return rc;
@@ -670,7 +704,7 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
   std::vector<int> alone, shared;
   for (int i = 0; i < n; ++i) {
     const dim3 g = ctxs[i]->sgrid;
-    (g.x * g.y * g.z >= wave ? alone : shared).push_back(i);
+    (g.x * g.y * g.z >= wave || ctxs[i]->open_faces ? alone : shared).push_back(i);
   }
   const int ns = int(shared.size());
   std::vector<unsigned> begin(size_t(ns) + 1);
@@ -716,7 +750,8 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
     for (int i : alone) {
       StepArgs<Real> a;
       step_args(ctxs[i], a);
-      CK(c0, c0->ops->step(c0->kmode, c0->solute, &a, ctxs[i]->sgrid, ctxs[i]->sblock, s));
+      CK(c0, c0->ops->step(c0->kmode, c0->solute, ctxs[i]->open_faces, &a, ctxs[i]->sgrid,
+                           ctxs[i]->sblock, s));
     }
     for (int g0 = 0; g0 < ns; g0 += BATCH_MAX) {
       const int g1 = std::min(ns, g0 + BATCH_MAX);
@@ -815,7 +850,7 @@ int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {
           CK(c, c->ops->pipe_step(c->kmode, c->solute, args, cd.ps.grid, cd.ps.bx, cd.ps.smem,
                                   cd.ps.gxr, cd.ps.items, c->stream));
         else
-          CK(c, c->ops->step(c->kmode, c->solute, args, grd, blk, c->stream));
+          CK(c, c->ops->step(c->kmode, c->solute, c->open_faces, args, grd, blk, c->stream));
         return int(LB_OK);
       });
     };

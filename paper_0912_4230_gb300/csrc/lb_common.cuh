@@ -183,7 +183,8 @@ struct StepArgs {
   int nx, ny, nz;
   unsigned N;
   // face-kind masks over the 6 faces (bit layout of faces_crossed)
-  unsigned f_wall;                   // fluid wall faces (others periodic)
+  unsigned f_wall;                   // fluid wall faces
+  unsigned f_press, f_vel;           // fluid pressure / velocity faces (others periodic)
   unsigned s_wall, s_inlet, s_outlet;  // solute faces
   const void *f_in;
   void *f_out;
@@ -196,6 +197,7 @@ struct StepArgs {
   const Real *geps;      // 3 x N: D grad(eps)/eps (solute only)
   const uint32_t *link;  // N: bit q = source x - c_q solid; bit 31 = cell solid (NULL: no solids)
   const Real *rhohat;    // N colour-gradient field (A != 0)
+  const Real *face;      // per face (2 axis + side): [0, 6) 3 x pressure, [6, 24) velocity xyz
   Real G[3];
   Real tau, tau0, tau1, nu_g, a_h, alpha, beta;
   int visc_law;

@@ -38,16 +38,18 @@ struct Instance {
   using Real = typename S::Real;
   using A = StepArgs<Real>;
 
-  template <int KM, bool SOL>
+  template <int KM, bool SOL, bool OPEN>
   static cudaError_t step_t(const A &a, dim3 grid, dim3 block, cudaStream_t s) {
-    step_kernel<S, KM, SOL><<<grid, block, 0, s>>>(a);
+    step_kernel<S, KM, SOL, OPEN><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
   }
-  static cudaError_t step(int kmode, bool solute, const void *args, dim3 grid, dim3 block,
-                          cudaStream_t s) {
+  static cudaError_t step(int kmode, bool solute, bool open, const void *args, dim3 grid,
+                          dim3 block, cudaStream_t s) {
     const A &a = *static_cast<const A *>(args);
     return dispatch_mode(kmode, solute, [&](auto km, auto sol) {
-      return step_t<decltype(km)::value, decltype(sol)::value>(a, grid, block, s);
+      constexpr int K = decltype(km)::value;
+      constexpr bool L = decltype(sol)::value;
+      return open ? step_t<K, L, true>(a, grid, block, s) : step_t<K, L, false>(a, grid, block, s);
     });
   }
   template <int KM, bool SOL>

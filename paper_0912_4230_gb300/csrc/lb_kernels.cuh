@@ -78,15 +78,36 @@ __device__ __forceinline__ int ahead_delta(const CellGeo &g) {
   return src_delta<opp(q)>(g);
 }
 
-// Pull classes (shared by the step kernels and the debug export).
-enum : int { PULL_CELL = 0, PULL_BOUNCE = 1, PULL_INLET = 2, PULL_OUTLET = 3 };
+// Pull classes (shared by the step kernels and the debug export, which
+// reports class c as -(1 + c)).
+enum : int { PULL_CELL = 0, PULL_BOUNCE = 1, PULL_INLET = 2, PULL_OUTLET = 3,
+             PULL_PRESSURE = 5, PULL_VELOCITY = 6 };
 
+// Fluid class of population q: across a wall face or from a solid cell
+// bounce-back; across a velocity face, else a pressure face, that face's
+// rule (walls take precedence on edges, then velocity, then pressure).
 template <int q>
 __device__ __forceinline__ int fluid_class(const CellGeo &g, uint32_t link, unsigned f_wall) {
   if (q == 0) return PULL_CELL;
   const unsigned fc = faces_crossed(q) & g.onface;
   if (fc & f_wall) return PULL_BOUNCE;
   return ((link >> q) & 1u) ? PULL_BOUNCE : PULL_CELL;
+}
+template <int q>
+__device__ __forceinline__ int fluid_class_open(const CellGeo &g, uint32_t link, unsigned f_wall,
+                                                unsigned f_vel, unsigned f_press) {
+  const unsigned fc = faces_crossed(q) & g.onface;
+  if (q != 0 && !(fc & f_wall)) {
+    if (fc & f_vel) return PULL_VELOCITY;
+    if (fc & f_press) return PULL_PRESSURE;
+  }
+  return fluid_class<q>(g, link, f_wall);
+}
+// the face (2 axis + side) of kind `mask` that population q crosses first in
+// axis order
+template <int q>
+__device__ __forceinline__ int crossed_face(const CellGeo &g, unsigned mask) {
+  return __ffs(faces_crossed(q) & g.onface & mask) - 1;
 }
 
 template <int q>
@@ -342,6 +363,68 @@ __device__ __forceinline__ void warp_reductions(const StepArgs<Real> &a, unsigne
   }
 }
 
+// Stream of a cell on a pressure or velocity face of the fluid lattice into
+// d[] (f_q - w_q). The face rules need the cell's own post-collision density
+// and velocity, from its 19 populations of the input buffer: a population
+// entering through a pressure face is -f~_qbar + 2 w_q rho_b (1 + 4.5
+// (c_q.u)^2/eps - 1.5 u.u/eps) with rho_b = 3 eps P_face; through a velocity
+// face f~_qbar + 6 w_q rho (c_q . u_face). Kept out of line: face cells are
+// few, and the hot path keeps its registers.
+template <class Real>
+struct Pops {
+  Real v[Q];
+};
+
+template <class S>
+__device__ __noinline__ Pops<typename S::Real> gather_open_faces(
+    const StepArgs<typename S::Real> &a, const CellGeo &g, unsigned n, uint32_t link) {
+  using Real = typename S::Real;
+  Pops<Real> d;
+  using T = typename S::T;
+  const unsigned N = a.N;
+  const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
+  Real own[Q];
+  Real r = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    Real v = S::template ld_f<q>(fb + int(q * N));
+    if constexpr (S::kShift) v += wq<Real>(q) * __ldg(a.rf_in + n);
+    own[q] = v;
+    r += v;
+    if (cx(q)) j0 += Real(cx(q)) * v;
+    if (cy(q)) j1 += Real(cy(q)) * v;
+    if (cz(q)) j2 += Real(cz(q)) * v;
+  });
+  const Real rho = Real(1) + r, irho = rcp(rho);
+  const Real u0 = j0 * irho, u1 = j1 * irho, u2 = j2 * irho;
+  const Real ie = rcp(__ldg(a.eps + n)), eps = __ldg(a.eps + n);
+  const Real uu = u0 * u0 + u1 * u1 + u2 * u2;
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int cls = fluid_class_open<q>(g, link, a.f_wall, a.f_vel, a.f_press);
+    Real v;
+    if (cls == PULL_BOUNCE) {
+      v = own[opp(q)];
+    } else if (cls == PULL_PRESSURE) {
+      const Real rb = eps * __ldg(a.face + crossed_face<q>(g, a.f_press));
+      const Real cu = Real(cx(q)) * u0 + Real(cy(q)) * u1 + Real(cz(q)) * u2;
+      const Real e = wq<Real>(q) * ((rb - Real(1)) +
+                                    rb * (Real(4.5) * ie * cu * cu - Real(1.5) * ie * uu));
+      v = Real(2) * e - own[opp(q)];
+    } else if (cls == PULL_VELOCITY) {
+      const Real *uf = a.face + 6 + 3 * crossed_face<q>(g, a.f_vel);
+      const Real cub = Real(cx(q)) * __ldg(uf) + Real(cy(q)) * __ldg(uf + 1) +
+                       Real(cz(q)) * __ldg(uf + 2);
+      v = own[opp(q)] + Real(6) * wq<Real>(q) * rho * cub;
+    } else {
+      v = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
+      if constexpr (S::kShift) v += wq<Real>(q) * __ldg(a.rf_in + (long long)n + src_delta<q>(g));
+    }
+    d.v[q] = v;
+  });
+  return d;
+}
+
 // Fluid moments of the arriving populations: drho += sum_q (f_q - w_q) and
 // V = j / rho with j = sum_q c_q (f_q - w_q), rho = 1 + drho.
 template <class Real, class FV>
@@ -441,7 +524,7 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
 // The per-cell update of one step from global memory: stream f (and h),
 // moments, viscosity, colour gradient, V' and the Darcy force, fluid and
 // solute collision, store; accumulates the cell's flux and totals.
-template <class S, int KMODE, bool SOLUTE>
+template <class S, int KMODE, bool SOLUTE, bool OPEN = false>
 __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a, unsigned x,
                                             unsigned y, unsigned z, unsigned n, uint32_t link,
                                             typename S::Real &fin_acc,
@@ -453,14 +536,18 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
   const CellGeo g = cell_geo_xyz(x, y, z, a.nx, a.ny, a.nz);
   const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
   Real d[Q];
-  if (link == 0 && !(g.onface & a.f_wall)) {
-    // every source is a cell
+  // OPEN: the lattice has pressure or velocity faces. A separate
+  // instantiation keeps the code of the lattices without them as it is (any
+  // extra branch in this gather changes the register allocation of the
+  // plain path at its 80-register cap and costs it ~15 %).
+  auto gather_cells = [&]() {
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       d[q] = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
       if constexpr (S::kShift) d[q] += wq<Real>(q) * __ldg(a.rf_in + (long long)n + src_delta<q>(g));
     });
-  } else {
+  };
+  auto gather_bounce = [&]() {
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       const bool bb = fluid_class<q>(g, link, a.f_wall) == PULL_BOUNCE;
@@ -468,6 +555,22 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
       if constexpr (S::kShift)
         d[q] += wq<Real>(q) * __ldg(a.rf_in + (long long)n + (bb ? 0 : src_delta<q>(g)));
     });
+  };
+  if constexpr (!OPEN) {
+    // every source is a cell, or bounce-back
+    if (link == 0 && !(g.onface & a.f_wall))
+      gather_cells();
+    else
+      gather_bounce();
+  } else {
+    if (link == 0 && !(g.onface & (a.f_wall | a.f_press | a.f_vel))) {
+      gather_cells();
+    } else if (g.onface & (a.f_press | a.f_vel)) {
+      const Pops<Real> o = gather_open_faces<S>(a, g, n, link);
+      Unroll<0, Q>::run([&](auto qc) { d[decltype(qc)::value] = o.v[decltype(qc)::value]; });
+    } else {
+      gather_bounce();
+    }
   }
   // every load of the interior path is issued before any arithmetic, so a
   // warp keeps its 38 population rows and static fields in flight together
@@ -540,7 +643,7 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
 // thread): measured on GB300 at 128^3 this is 1.1x faster than the
 // unconstrained build (112 registers), since the kernel is bound by loads in
 // flight, and a little faster than 256-thread blocks at the same occupancy.
-template <class S, int KMODE, bool SOLUTE>
+template <class S, int KMODE, bool SOLUTE, bool OPEN>
 __global__ void __launch_bounds__(STEP_BLOCK, 6) step_kernel(const StepArgs<typename S::Real> a) {
   using Real = typename S::Real;
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -559,7 +662,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, 6) step_kernel(const StepArgs<type
   }
   Real fin_acc = Real(0), fout_acc = Real(0), drho = Real(0), sC = Real(0);
   bool open_face = false;
-  if (live) update_cell<S, KMODE, SOLUTE>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
+  if (live) update_cell<S, KMODE, SOLUTE, OPEN>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
   warp_reductions(a, warp_gid, open_face, fin_acc, fout_acc, drho, sC);
 }
 
@@ -795,7 +898,7 @@ __global__ void neighbors_kernel(const StepArgs<Real> a, int lattice, int32_t *s
     if (link >> 31) {
       v = -1;
     } else {
-      const int cls = lattice == 0 ? fluid_class<q>(g, link, a.f_wall)
+      const int cls = lattice == 0 ? fluid_class_open<q>(g, link, a.f_wall, a.f_vel, a.f_press)
                                    : solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
       v = cls == PULL_CELL ? int32_t((long long)n + src_delta<q>(g)) : -(1 + cls);
     }

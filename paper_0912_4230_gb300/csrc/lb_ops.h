@@ -13,8 +13,9 @@ struct StorageOps {
   size_t elt_bytes;  // bytes per stored population
   bool fp64;         // collision type is double (StepArgs<double>)
   // step / init / rhohat take a StepArgs<Real>* matching fp64
-  cudaError_t (*step)(int kmode, bool solute, const void *args, dim3 grid, dim3 block,
-                      cudaStream_t s);
+  // open: the lattice has pressure or velocity faces (its own instantiation)
+  cudaError_t (*step)(int kmode, bool solute, bool open, const void *args, dim3 grid,
+                      dim3 block, cudaStream_t s);
   cudaError_t (*init)(int kmode, bool solute, const void *args, const void *init_args,
                       unsigned nblk, cudaStream_t s);
   cudaError_t (*rhohat)(const void *args, void *rhohat, unsigned nblk, cudaStream_t s);
@@ -64,7 +65,8 @@ const StorageOps &ops_bf16();
 struct SetupArgs {
   int nx, ny, nz;
   unsigned N;
-  unsigned f_wall, s_wall, s_open;  // face masks; s_open = solute inlet | outlet faces
+  unsigned f_wall, s_wall, s_open;  // face masks: f_wall = every non-periodic fluid face,
+                                    // s_open = solute inlet | outlet faces
   const float *eps_in;   // N
   const float *K6_in;    // 6 x N packed per cell, or NULL
   const uint8_t *solid;  // N

@@ -12,7 +12,8 @@
 // reads only the column it wrote, so cp.async.wait_group alone orders the
 // stages; no block barrier is needed.
 //
-// Cells next to a bounce-back link, a wall face or an open solute face take
+// Not used for lattices with pressure or velocity faces. Cells next to a
+// bounce-back link, a wall face or an open solute face take
 // the per-cell path (update_cell) with its own global loads; the staged
 // values of such cells are not used. Every staged address is the wrapped
 // pull source of a cell inside the lattice, so it is in bounds for any cell.

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblbgb.so")
 Q = 19
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ETIMEOUT, LB_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6
-PERIODIC, WALL, INLET, OUTLET = 0, 1, 2, 3
+PERIODIC, WALL, INLET, OUTLET, PRESSURE, VELOCITY = 0, 1, 2, 3, 4, 5
 STORE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_get_populations",
@@ -49,7 +49,8 @@ class lb_params(ctypes.Structure):
                 ("G", c_double * 3), ("A", c_double), ("wall_rho", c_double),
                 ("forchheimer", c_double), ("solute", c_int32), ("tau_D", c_double),
                 ("C_in", c_double), ("free_surface", c_int32), ("storage", c_int32),
-                ("check_every", c_int32), ("kernel", c_int32)]
+                ("check_every", c_int32), ("kernel", c_int32),
+                ("face_P", (c_double * 2) * 3), ("face_u", ((c_double * 3) * 2) * 3)]
 
 
 _lib = None
@@ -263,6 +264,13 @@ def make_params(prob, storage=None, check_every=0, kernel="auto") -> lb_params:
         p.G[i] = k.get("G", (0.0, 0.0, 0.0))[i]
     p.A = k.get("A", 0.0)
     p.wall_rho = k.get("wall_rho", 0.0)
+    fp = k.get("face_P", ((0.0, 0.0),) * 3)
+    fu = k.get("face_u", (((0.0,) * 3,) * 2,) * 3)
+    for ax in range(3):
+        for side in range(2):
+            p.face_P[ax][side] = fp[ax][side]
+            for i in range(3):
+                p.face_u[ax][side][i] = fu[ax][side][i]
     p.forchheimer = k.get("forchheimer", 0.0)
     p.solute = int(k.get("solute", 0))
     p.tau_D = k.get("tau_D", 1.0)

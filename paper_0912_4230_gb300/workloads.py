@@ -181,12 +181,14 @@ def _faces(P=None, u=None):
     return tuple(tuple(x) for x in fp), tuple(tuple(tuple(y) for y in x) for x in fu)
 
 
-def pressure_darcy(n=64, P_in=1.0 / 3.0 + 2e-4, P_out=1.0 / 3.0 - 2e-4, K=1.0, eps=0.5,
-                   tau=0.8, steps=4000) -> Problem:
+def pressure_darcy(n=64, dP=4e-4, K=1.0, eps=0.5, tau=0.8, steps=4000) -> Problem:
     """Flow through a uniform medium between two PRESSURE faces along x
-    (periodic y and z, one cell thick): the steady mass flux is uniform and
-    the density falls linearly between the face densities 3 eps P."""
+    (periodic y and z, one cell thick), face pressures 1/(3 eps) +- dP/2 (face
+    densities near 1): the steady mass flux is uniform and the density falls
+    linearly between the face densities 3 eps P."""
     N = n
+    P0 = 1.0 / (3.0 * float(np.float32(eps)))
+    P_in, P_out = P0 + 0.5 * dP, P0 - 0.5 * dP
     bc = ((PRESSURE, PRESSURE), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC))
     fp, fu = _faces(P={(0, 0): P_in, (0, 1): P_out})
     K6 = np.zeros((N, 6), np.float32)
@@ -211,11 +213,12 @@ def velocity_couette(nz=32, u_b=1e-3, K=16.0, eps=0.6, tau=0.8, steps=6000) -> P
                  _uniform(N, eps), K6.ravel(), steps=steps, storage="fp64")
 
 
-def inflow_darcy(n=64, u_in=2e-4, P_out=1.0 / 3.0, K=1.0, eps=0.5, tau=0.8,
-                 steps=4000) -> Problem:
+def inflow_darcy(n=64, u_in=2e-4, K=1.0, eps=0.5, tau=0.8, steps=4000) -> Problem:
     """Flow rate imposed at the x-low face (VELOCITY, normal inflow u_in),
-    pressure at the x-high face, uniform medium, periodic y and z."""
+    pressure 1/(3 eps) at the x-high face (face density 1), uniform medium,
+    periodic y and z."""
     N = n
+    P_out = 1.0 / (3.0 * float(np.float32(eps)))
     bc = ((VELOCITY, PRESSURE), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC))
     fp, fu = _faces(P={(0, 1): P_out}, u={(0, 0): (u_in, 0.0, 0.0)})
     K6 = np.zeros((N, 6), np.float32)
@@ -406,6 +409,8 @@ def random_medium(nx=8, ny=6, nz=5, seed=1, solid_frac=0.1, walls=True, solute=T
     rng = _rng(seed)
     N = nx * ny * nz
     eps = rng.uniform(0.3, 1.0, N)
+    if open_faces:   # pressure faces hold 3 eps P: keep the porosity near one value
+        eps = rng.uniform(0.85, 0.95, N)
     k = 10.0 ** rng.uniform(-3, 0, N)
     K6 = np.zeros((N, 6))
     K6[:, 0] = k * rng.uniform(0.5, 2, N)
@@ -429,8 +434,9 @@ def random_medium(nx=8, ny=6, nz=5, seed=1, solid_frac=0.1, walls=True, solute=T
         bc[2] = [PRESSURE, PRESSURE]
         sbc[0] = [INLET, OUTLET]
         sbc[2] = [INLET, OUTLET]
-        fp, fu = _faces(P={(0, 1): 0.34, (2, 0): 0.345, (2, 1): 0.33},
-                        u={(0, 0): (0.01, 0.004, -0.003)})
+        P0 = 1.0 / (3.0 * 0.9)
+        fp, fu = _faces(P={(0, 1): P0 * 0.998, (2, 0): P0 * 1.002, (2, 1): P0 * 0.999},
+                        u={(0, 0): (2e-4, 0.004, -0.003)})
         extra = dict(face_P=fp, face_u=fu)
     params = dict(tau=0.9, visc_law=visc_law if solute else 0, tau0=0.7, tau1=1.3,
                   nu_g=0.1, a=0.05, alpha=0.01, beta=0.5,

@@ -59,6 +59,15 @@ def _create(prob, **over):
     return lb.lb_create(dom, prob.eps, prob.K6, prob.solid, prm)
 
 
+def test_open_faces_refuse_free_surface_and_surface_tension(L):
+    for extra in (dict(A=1e-3), dict(free_surface=1)):
+        prob = W.random_medium(4, 4, 4, seed=0, open_faces=True, solute=False)
+        prob = prob.replace(K6=None)
+        with pytest.raises(lb.LbError) as e:
+            _create(prob, **extra)
+        assert e.value.code == lb.LB_EUNSUPPORTED
+
+
 @pytest.mark.parametrize("over,code", [
     (dict(forchheimer=-0.5), lb.LB_EINVAL),
     (dict(visc_law=0, tau=0.5), lb.LB_EINVAL),
