@@ -260,7 +260,8 @@ struct orc {
   double *out_rho, *out_u, *out_C, *out_nu;
   double *cell_in, *cell_out; /* per-cell solute flux of the current step */
   int64_t t;
-  double flux_in, flux_out;
+  int S;               /* solute species (0 without the solute lattice) */
+  double flux_in[ORC_MAX_SPECIES], flux_out[ORC_MAX_SPECIES];
 };
 
 static int64_t cell_index(const orc *o, int x, int y, int z)
@@ -407,10 +408,17 @@ orc *orc_create(const orc_params *p, const double *eps, const double *K6,
       if (K6[6 * n + 3] != 0.0 || K6[6 * n + 4] != 0.0 || K6[6 * n + 5] != 0.0) return NULL;
   }
 
+  if (p->species < 0 || p->species > ORC_MAX_SPECIES) return NULL;
+  if (p->species > 1 && !p->solute) return NULL;
+  for (int sp = 1; sp < p->species; sp++)
+    if (!(p->species_tau_D[sp] > 0.5)) return NULL;
+
   orc *o = (orc *)zalloc(sizeof(orc));
   o->p = *p;
   int64_t N = (int64_t)p->nx * p->ny * p->nz;
   o->N = N;
+  o->S = p->solute ? (p->species > 1 ? p->species : 1) : 0;
+  int S1 = o->S > 1 ? o->S : 1;
 #ifdef _OPENMP
   if (p->threads > 0) omp_set_num_threads(p->threads);
 #endif
@@ -419,9 +427,9 @@ orc *orc_create(const orc_params *p, const double *eps, const double *K6,
   o->fn = zalloc(nq);
   o->fs = zalloc(nq);
   if (p->solute) {
-    o->h = zalloc(nq);
-    o->hn = zalloc(nq);
-    o->hs = zalloc(nq);
+    o->h = zalloc(o->S * nq);
+    o->hn = zalloc(o->S * nq);
+    o->hs = zalloc(o->S * nq);
   }
   o->eps = zalloc(N * sizeof(double));
   o->geps = zalloc(3 * N * sizeof(double));
@@ -435,10 +443,10 @@ orc *orc_create(const orc_params *p, const double *eps, const double *K6,
   o->rhohat = zalloc(N * sizeof(double));
   o->out_rho = zalloc(N * sizeof(double));
   o->out_u = zalloc(3 * N * sizeof(double));
-  o->out_C = zalloc(N * sizeof(double));
+  o->out_C = zalloc(S1 * N * sizeof(double));
   o->out_nu = zalloc(N * sizeof(double));
-  o->cell_in = zalloc(N * sizeof(double));
-  o->cell_out = zalloc(N * sizeof(double));
+  o->cell_in = zalloc(S1 * N * sizeof(double));
+  o->cell_out = zalloc(S1 * N * sizeof(double));
   memcpy(o->solid, solid, N);
   for (int64_t n = 0; n < N; n++) {
     o->eps[n] = eps[n];
@@ -477,7 +485,12 @@ orc *orc_create(const orc_params *p, const double *eps, const double *K6,
   return o;
 }
 
-static double diffusivity(const orc *o) { return (o->p.tau_D - 0.5) / 3.0; }
+/* Species s >= 1 carry their own relaxation time and inlet concentration
+ * (reading R24); D = (tau_D - 1/2) / 3 (Section 2.2). */
+static double tau_D_of(const orc *o, int s) { return s ? o->p.species_tau_D[s] : o->p.tau_D; }
+static double C_in_of(const orc *o, int s) { return s ? o->p.species_C_in[s] : o->p.C_in; }
+static double diffusivity_of(const orc *o, int s) { return (tau_D_of(o, s) - 0.5) / 3.0; }
+static double diffusivity(const orc *o) { return diffusivity_of(o, 0); }
 
 /* Colour gradient F = sum_q rhohat(x + c_q) c_q (Eq. macros, second part).
  * Reading: the sum is unweighted as printed; a solid neighbour, or a step out
@@ -516,9 +529,8 @@ int orc_init(orc *o, const double *rho0, const double *u0, const double *C0,
   if (o->p.solute && !C0) return -1;
   if (o->p.free_surface && !type) return -1;
   int64_t N = o->N;
-  double D = o->p.solute ? diffusivity(o) : 0.0;
   o->t = 0;
-  o->flux_in = o->flux_out = 0.0;
+  for (int sp = 0; sp < ORC_MAX_SPECIES; sp++) o->flux_in[sp] = o->flux_out[sp] = 0.0;
   /* flowchart steps a and b: fields, cell types and cell masses */
   for (int64_t n = 0; n < N; n++) {
     o->type[n] = o->p.free_surface ? type[n] : ORC_LIQUID;
@@ -542,7 +554,9 @@ int orc_init(orc *o, const double *rho0, const double *u0, const double *C0,
   }
   /* flowchart step c: f = f^eq, h = h^eq */
   memset(o->f, 0, (size_t)N * Q * sizeof(double));
-  if (o->p.solute) memset(o->h, 0, (size_t)N * Q * sizeof(double));
+  if (o->p.solute) memset(o->h, 0, (size_t)o->S * N * Q * sizeof(double));
+  for (int sp = 1; sp < o->S; sp++)
+    for (int64_t n = 0; n < N; n++) o->out_C[sp * N + n] = 0.0;
   for (int64_t n = 0; n < N; n++) {
     o->out_rho[n] = o->out_C[n] = o->out_nu[n] = 0.0;
     o->out_u[3 * n] = o->out_u[3 * n + 1] = o->out_u[3 * n + 2] = 0.0;
@@ -554,15 +568,15 @@ int orc_init(orc *o, const double *rho0, const double *u0, const double *C0,
     orc_feq(rho0[n], u0 + 3 * n, o->eps[n], tau, o->p.A, F, fe);
     for (int q = 0; q < Q; q++)
       o->f[(int64_t)q * N + n] = fe[q] * (f_scale ? f_scale[(int64_t)q * N + n] : 1.0);
-    if (o->p.solute) {
-      double Vs[3], he[Q];
+    for (int sp = 0; sp < o->S; sp++) {
+      double Vs[3], he[Q], Cs = C0[sp * N + n], D = diffusivity_of(o, sp);
       for (int a = 0; a < 3; a++) Vs[a] = u0[3 * n + a] + D * o->geps[3 * n + a];
-      orc_heq(o->eps[n], Cc, Vs, he);
-      for (int q = 0; q < Q; q++) o->h[(int64_t)q * N + n] = he[q];
+      orc_heq(o->eps[n], Cs, Vs, he);
+      for (int q = 0; q < Q; q++) o->h[((int64_t)sp * Q + q) * N + n] = he[q];
+      o->out_C[sp * N + n] = Cs;
     }
     o->out_rho[n] = rho0[n];
     for (int a = 0; a < 3; a++) o->out_u[3 * n + a] = u0[3 * n + a];
-    o->out_C[n] = Cc;
     o->out_nu[n] = (tau - 0.5) / 3.0;
   }
   return 0;
@@ -665,34 +679,38 @@ static void stream_solute(orc *o, int64_t n)
   int x, y, z;
   int64_t N = o->N;
   cell_coords(o, n, &x, &y, &z);
-  double D = diffusivity(o);
   double r = 0, j[3] = {0, 0, 0};
   for (int q = 0; q < Q; q++) {
     double v = o->fs[(int64_t)q * N + n];
     r += v;
     for (int a = 0; a < 3; a++) j[a] += v * CV[q][a];
   }
-  double Vin[3];
-  for (int a = 0; a < 3; a++) Vin[a] = j[a] / r + D * o->geps[3 * n + a];
-  double fin = 0.0, fout = 0.0;
-  for (int q = 0; q < Q; q++) {
-    int64_t s = pull_source(o, o->p.sbc, x, y, z, q, NULL);
-    double v;
-    if (s == ORC_SRC_BOUNCE) {
-      v = o->h[(int64_t)OPP[q] * N + n];
-    } else if (s == ORC_SRC_INLET) {
-      v = WT[q] * o->eps[n] * o->p.C_in * (1.0 + 3.0 * cdot(q, Vin));
-      fin += v - o->h[(int64_t)OPP[q] * N + n];
-    } else if (s == ORC_SRC_OUTLET) {
-      v = o->h[(int64_t)q * N + n];
-      fout += o->h[(int64_t)OPP[q] * N + n] - v;
-    } else {
-      v = o->h[(int64_t)q * N + s];
+  for (int sp = 0; sp < o->S; sp++) {
+    const double *h = o->h + (int64_t)sp * Q * N;
+    double *hs = o->hs + (int64_t)sp * Q * N;
+    double D = diffusivity_of(o, sp), Cin = C_in_of(o, sp);
+    double Vin[3];
+    for (int a = 0; a < 3; a++) Vin[a] = j[a] / r + D * o->geps[3 * n + a];
+    double fin = 0.0, fout = 0.0;
+    for (int q = 0; q < Q; q++) {
+      int64_t s = pull_source(o, o->p.sbc, x, y, z, q, NULL);
+      double v;
+      if (s == ORC_SRC_BOUNCE) {
+        v = h[(int64_t)OPP[q] * N + n];
+      } else if (s == ORC_SRC_INLET) {
+        v = WT[q] * o->eps[n] * Cin * (1.0 + 3.0 * cdot(q, Vin));
+        fin += v - h[(int64_t)OPP[q] * N + n];
+      } else if (s == ORC_SRC_OUTLET) {
+        v = h[(int64_t)q * N + n];
+        fout += h[(int64_t)OPP[q] * N + n] - v;
+      } else {
+        v = h[(int64_t)q * N + s];
+      }
+      hs[(int64_t)q * N + n] = v;
     }
-    o->hs[(int64_t)q * N + n] = v;
+    o->cell_in[sp * N + n] = fin;
+    o->cell_out[sp * N + n] = fout;
   }
-  o->cell_in[n] = fin;
-  o->cell_out[n] = fout;
 }
 
 /* Flowchart step g, Eqs. eq:massmacro, eq:massevol, eq:deltamass. Reading:
@@ -753,14 +771,25 @@ static void collide(orc *o, int64_t n)
     double fq = o->fs[(int64_t)q * N + n];
     o->fn[(int64_t)q * N + n] = fq - (fq - fe[q]) / tau + T[q];
   }
-  if (o->p.solute) {
-    double D = diffusivity(o), Vs[3], he[Q];
-    for (int a = 0; a < 3; a++) Vs[a] = Vp[a] + D * o->geps[3 * n + a];
-    orc_heq(eps, Cc, Vs, he);
-    for (int q = 0; q < Q; q++) {
-      double hq = o->hs[(int64_t)q * N + n];
-      o->hn[(int64_t)q * N + n] = hq - (hq - he[q]) / o->p.tau_D;
+  /* every species relaxes towards its own equilibrium with the shared V'
+   * (reading R24: species 0's concentration sets the viscosity) */
+  for (int sp = 0; sp < o->S; sp++) {
+    const double *hs = o->hs + (int64_t)sp * Q * N;
+    double *hn = o->hn + (int64_t)sp * Q * N;
+    double Cs = Cc;
+    if (sp > 0) {
+      double s = 0;
+      for (int q = 0; q < Q; q++) s += hs[(int64_t)q * N + n];
+      Cs = s / eps;
     }
+    double D = diffusivity_of(o, sp), tD = tau_D_of(o, sp), Vs[3], he[Q];
+    for (int a = 0; a < 3; a++) Vs[a] = Vp[a] + D * o->geps[3 * n + a];
+    orc_heq(eps, Cs, Vs, he);
+    for (int q = 0; q < Q; q++) {
+      double hq = hs[(int64_t)q * N + n];
+      hn[(int64_t)q * N + n] = hq - (hq - he[q]) / tD;
+    }
+    o->out_C[sp * N + n] = Cs;
   }
   o->out_rho[n] = rho;
   for (int a = 0; a < 3; a++) o->out_u[3 * n + a] = Vp[a];
@@ -903,16 +932,18 @@ static void step_once(orc *o)
   if (o->p.solute) {
 #pragma omp parallel for schedule(static)
     for (n = 0; n < N; n++) {
-      o->cell_in[n] = o->cell_out[n] = 0.0;
+      for (int sp = 0; sp < o->S; sp++) o->cell_in[sp * N + n] = o->cell_out[sp * N + n] = 0.0;
       if (active(o, n)) stream_solute(o, n);
     }
-    double fin = 0.0, fout = 0.0;
-    for (n = 0; n < N; n++) {
-      fin += o->cell_in[n];
-      fout += o->cell_out[n];
+    for (int sp = 0; sp < o->S; sp++) {
+      double fin = 0.0, fout = 0.0;
+      for (n = 0; n < N; n++) {
+        fin += o->cell_in[sp * N + n];
+        fout += o->cell_out[sp * N + n];
+      }
+      o->flux_in[sp] += fin;
+      o->flux_out[sp] += fout;
     }
-    o->flux_in += fin;
-    o->flux_out += fout;
   }
   if (o->p.free_surface) {
 #pragma omp parallel for schedule(static)
@@ -1019,8 +1050,28 @@ int orc_reduce(const orc *o, double out[4])
   }
   out[0] = mass;
   out[1] = sol;
-  out[2] = o->flux_in;
-  out[3] = o->flux_out;
+  out[2] = o->flux_in[0];
+  out[3] = o->flux_out[0];
+  return 0;
+}
+
+int orc_species_state(const orc *o, int32_t s, double *C, double out[3], double *h)
+{
+  if (!o || s < 0 || s >= o->S) return -1;
+  int64_t N = o->N;
+  const double *hs = o->h + (int64_t)s * Q * N;
+  if (C) memcpy(C, o->out_C + (int64_t)s * N, N * sizeof(double));
+  if (h) memcpy(h, hs, (size_t)Q * N * sizeof(double));
+  if (out) {
+    double sol = 0.0;
+    for (int64_t n = 0; n < N; n++) {
+      if (o->solid[n]) continue;
+      for (int q = 0; q < Q; q++) sol += hs[(int64_t)q * N + n];
+    }
+    out[0] = sol;
+    out[1] = o->flux_in[s];
+    out[2] = o->flux_out[s];
+  }
   return 0;
 }
 

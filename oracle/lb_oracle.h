@@ -11,6 +11,8 @@
  *
  * Conventions: cell index n = x + nx*(y + ny*z); populations are stored
  * direction-major, pop[q*N + n]; all arrays are caller-owned and copied.
+ * With several solute species, per-species arrays follow one another
+ * (species-major): C0[s*N + n]; orc_init's C0 holds all species.
  */
 #ifndef LB_ORACLE_H
 #define LB_ORACLE_H
@@ -23,6 +25,7 @@ extern "C" {
 enum { ORC_PERIODIC = 0, ORC_WALL = 1, ORC_INLET = 2, ORC_OUTLET = 3,
        ORC_PRESSURE = 4, ORC_VELOCITY = 5 };
 enum { ORC_LIQUID = 0, ORC_INTERFACE = 1, ORC_EMPTY = 2 };
+enum { ORC_MAX_SPECIES = 8 };
 /* classes reported by orc_neighbors for populations that do not come from a cell */
 enum { ORC_SRC_NOT_UPDATED = -1, ORC_SRC_BOUNCE = -2, ORC_SRC_INLET = -3,
        ORC_SRC_OUTLET = -4, ORC_SRC_EMPTY = -5, ORC_SRC_PRESSURE = -6,
@@ -49,6 +52,9 @@ typedef struct {
                          Forchheimer drag); needs a diagonal or no K */
   double face_P[3][2];      /* pressure of each PRESSURE face */
   double face_u[3][2][3];   /* velocity of each VELOCITY face */
+  int32_t species;          /* solute lattices (species), 1..ORC_MAX_SPECIES; 0 = 1 */
+  double species_tau_D[8];  /* relaxation time of species s >= 1 (species 0: tau_D) */
+  double species_C_in[8];   /* inlet concentration of species s >= 1 (species 0: C_in) */
 } orc_params;
 
 typedef struct orc orc;
@@ -62,6 +68,10 @@ int orc_get_populations(const orc *o, double *f, double *h);
 int orc_step(orc *o, int64_t n);
 int orc_fields(const orc *o, double *rho, double *u, double *C, double *nu);
 int orc_reduce(const orc *o, double out[4]);
+/* Species s (0 <= s < species): its concentration field C (may be NULL), its
+ * totals out = {sum_q h_q, cumulative inlet flux, outlet flux} (may be NULL)
+ * and its populations h (19 N, may be NULL). */
+int orc_species_state(const orc *o, int32_t s, double *C, double out[3], double *h);
 int orc_neighbors(const orc *o, int32_t lattice, int32_t *src);
 int orc_free_surface_state(const orc *o, uint8_t *type, double *m);
 int64_t orc_time(const orc *o);

@@ -45,6 +45,7 @@ class OrcParams(ctypes.Structure):
         ("free_surface", c_int32), ("threads", c_int32),
         ("forchheimer", c_double),
         ("face_P", (c_double * 2) * 3), ("face_u", ((c_double * 3) * 2) * 3),
+        ("species", c_int32), ("species_tau_D", c_double * 8), ("species_C_in", c_double * 8),
     ]
 
 
@@ -76,6 +77,7 @@ def lib():
         L.orc_step.argtypes = [c_void_p, c_int64]
         L.orc_fields.argtypes = [c_void_p] + [c_void_p] * 4
         L.orc_reduce.argtypes = [c_void_p, c_void_p]
+        L.orc_species_state.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]
         L.orc_neighbors.argtypes = [c_void_p, c_int32, c_void_p]
         L.orc_free_surface_state.argtypes = [c_void_p, c_void_p, c_void_p]
         L.orc_time.restype = c_int64
@@ -128,6 +130,11 @@ def make_params(prob, threads: int = 0) -> OrcParams:
     p.free_surface = int(k.get("free_surface", 0))
     p.threads = threads
     p.forchheimer = k.get("forchheimer", 0.0)
+    p.species = int(k.get("species", 1 if k.get("solute") else 0))
+    for s_, v in enumerate(k.get("species_tau_D", ())):
+        p.species_tau_D[s_] = v
+    for s_, v in enumerate(k.get("species_C_in", ())):
+        p.species_C_in[s_] = v
     fp = k.get("face_P", ((0.0, 0.0),) * 3)
     fu = k.get("face_u", (((0.0,) * 3,) * 2,) * 3)
     for a in range(3):
@@ -226,6 +233,14 @@ class Oracle:
         out = np.zeros(4)
         lib().orc_reduce(self._h, _ptr(out))
         return out
+
+    def species_state(self, s: int):
+        """Species s: (C field, [solute total, inlet flux, outlet flux], h[19, N])."""
+        N = self.N
+        C, out, h = np.zeros(N), np.zeros(3), np.zeros(Q * N)
+        if lib().orc_species_state(self._h, int(s), _ptr(C), _ptr(out), _ptr(h)) != 0:
+            raise ValueError(f"no solute species {s}")
+        return C, out, h.reshape(Q, N)
 
     def populations(self):
         f = np.zeros(Q * self.N)

@@ -228,6 +228,34 @@ def inflow_darcy(n=64, u_in=2e-4, K=1.0, eps=0.5, tau=0.8, steps=4000) -> Proble
                  rho0=_uniform(N, 3.0 * eps * P_out), steps=steps, storage="fp64")
 
 
+def with_species(prob: Problem, tau_D=(), C_in=(), C0=()) -> Problem:
+    """The same problem with solute species 1, 2, ... added to species 0:
+    relaxation times tau_D[s-1], inlet concentrations C_in[s-1] and initial
+    fields C0[s-1] (each N values, default species 0's)."""
+    S = 1 + len(tau_D)
+    N = prob.N
+    fields = [np.asarray(prob.C0, np.float32).reshape(-1)[:N]]
+    for s in range(1, S):
+        c = C0[s - 1] if s - 1 < len(C0) and C0[s - 1] is not None else fields[0]
+        fields.append(np.asarray(c, np.float32).reshape(N))
+    params = dict(prob.params, species=S,
+                  species_tau_D=(0.0,) + tuple(float(t) for t in tau_D),
+                  species_C_in=(0.0,) + tuple(float(c) for c in
+                                              (list(C_in) + [0.0] * S)[:S - 1]))
+    return prob.replace(params=params, C0=np.concatenate(fields))
+
+
+def miscible_species(nx=128, ny=128, nz=128, seed=0, steps=5000, storage="fp32") -> Problem:
+    """The miscible medium with three solute species sharing the flow:
+    species 0 as there (tau_D 0.8, inlet C 1, it sets the viscosity), species
+    1 faster (tau_D 1.2, inlet C 0.5), species 2 slower (tau_D 0.6, inlet C 0,
+    initially 0.3 everywhere)."""
+    base = miscible(nx, ny, nz, seed=seed, steps=steps, storage=storage)
+    N = base.N
+    return with_species(base, tau_D=(1.2, 0.6), C_in=(0.5, 0.0),
+                        C0=(None, np.full(N, 0.3, np.float32))).replace(name="miscible_species")
+
+
 def _random_rotations(nblocks, seed):
     """Haar-random rotation matrices from unit quaternions of 4 normals."""
     rng = _rng(seed)
