@@ -48,6 +48,11 @@ def _other_workloads():
                            prec + "BF16 deviation storage"),
         "plain-fp64": (lambda r: W.plain_channel(), "fp64", 337,
                        "plain Brinkman channel 16x16x64, FP64, no solute"),
+        # algorithmic bytes: f and three solute lattices read and written once,
+        # eps, K^-1 and the mask read once
+        "species": (lambda r: W.miscible_species(seed=r), "fp32", 4 * 152 + 17,
+                    "miscible medium 128^3 with three solute species (tau_D 0.8 / 1.2 / 0.6), "
+                    "D3Q19 fluid + 3 solute lattices, FP32; step = fused pass + species pass"),
         "forchheimer": (lambda r: W.forchheimer(seed=r), "fp32", 321,
                         "coarse porous medium 128^3 with Forchheimer drag (diagonal K, "
                         "K_zz = 10 K_xx, G 1e-4), D3Q19 fluid + solute, FP32"),
@@ -373,6 +378,14 @@ def main():
     d2h = 6 * N * 4 + 2 * 8 + 48
 
     peak, peak_kind = measured_peaks()
+    species = int(prob.params.get("species", 1))
+    # launches of one step: the free surface's six passes and its tile
+    # compaction; the fused step and the species pass; else the fused step
+    # (plus the density pre-pass with surface tension)
+    if prob.cell_type is not None:
+        launches_per_step = 7
+    else:
+        launches_per_step = (2 if species > 1 else 1) + (1 if prob.params.get("A", 0.0) else 0)
     units = N
     if prob.cell_type is not None:
         units = int(((prob.cell_type != W.EMPTY) & (prob.solid == 0)).sum())  # updated cells
@@ -399,8 +412,10 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind,
-                     "kernel": ("six free-surface kernels of one step" if prob.cell_type is not None
-                                else "tma_step_kernel (row-pipelined)" if choice == 256 else
+                     "kernel": ("seven free-surface launches of one step" if prob.cell_type is not None
+                                else "step_kernel + species_kernel of one step"
+                                if species > 1 else
+                                "tma_step_kernel (row-pipelined)" if choice == 256 else
                                 f"pipe_step_kernel (row-staged), rows of {choice - 1000} threads"
                                 if choice > 1000 else
                                 f"step_kernel, rows of {choice or 'default'} threads"),
@@ -412,7 +427,7 @@ def main():
                 "d2h_bytes_per_step": d2h,
                 "step": f"lb_init from pinned host fields + {args.e2e_inner} lattice steps + "
                         f"lb_fields to pinned host + lb_reduce"},
-        "gpu_launches": K * (6 if prob.cell_type is not None else 1),
+        "gpu_launches": K * launches_per_step,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -78,6 +78,9 @@ enum { LB_BC_PERIODIC = 0, LB_BC_WALL = 1, LB_BC_INLET = 2, LB_BC_OUTLET = 3,
  * h_q/w_q - r_h), so density and solute content are carried in FP32. */
 enum { LB_STORE_FP32 = 0, LB_STORE_FP64 = 1, LB_STORE_FP16DEV = 2, LB_STORE_BF16DEV = 3 };
 
+/* Largest number of solute species (lb_params.species). */
+enum { LB_MAX_SPECIES = 8 };
+
 /* Free-surface cell types (Section 3). */
 enum { LB_CELL_LIQUID = 0, LB_CELL_INTERFACE = 1, LB_CELL_EMPTY = 2 };
 
@@ -133,6 +136,17 @@ typedef struct {
                            compute the same arithmetic. */
   double face_P[3][2];      /* pressure of each PRESSURE face [axis][side] */
   double face_u[3][2][3];   /* velocity of each VELOCITY face [axis][side][xyz] */
+  int32_t species;          /* solute species, 1..LB_MAX_SPECIES (0 = 1). The paper
+                               keeps the solute on its own lattice to allow
+                               several species (Section 2.2): each species is a
+                               D3Q19 lattice of Eqs. equild/boltzeqD with its own
+                               tau_D and inlet concentration, all sharing V';
+                               species 0's C sets the viscosity law. Needs
+                               solute = 1; with more than one species only the
+                               per-cell kernel runs (kernels 2 and 3 return
+                               LB_EUNSUPPORTED) and there is no free surface. */
+  double species_tau_D[LB_MAX_SPECIES]; /* tau_D of species s >= 1 (species 0: tau_D), > 1/2 */
+  double species_C_in[LB_MAX_SPECIES];  /* inlet concentration of species s >= 1 (species 0: C_in) */
 } lb_params;
 
 /* Create a lattice (flowchart of Section 4: the porosity field, the
@@ -163,7 +177,8 @@ int lb_set_stream(lb_ctx *ctx, void *cuda_stream);
 /* Initial fields (flowchart steps a-c, Section 4): f = f^eq (Eqs. equilc1,
  * equilc2) at density rho0 and velocity u0 (taken as V'), h = h^eq (Eq.
  * equild) at concentration C0; t = 0.
- *   rho0 N, u0 3N, C0 N (required iff solute), cell_type N (LB_CELL_*,
+ *   rho0 N, u0 3N, C0 N per solute species, species-major (required iff
+ *   solute; species s at C0 + s*N), cell_type N (LB_CELL_*,
  *   required iff free_surface), lambda0 N liquid fraction (NULL: 1 liquid,
  *   0.5 interface, 0 empty), f_scale 19*N factors multiplying the initial f
  *   (NULL = 1; seeded perturbations). Solid cells are ignored. */
@@ -239,6 +254,14 @@ int lb_debug_neighbors(lb_ctx *ctx, int32_t lattice, int32_t *src);
  * call returns LB_ETIMEOUT, as a step whose wait gave up would at the next
  * check. The context stays usable; the status is cleared by lb_init. */
 int lb_debug_wait_timeout(lb_ctx *ctx, int64_t limit_ns);
+
+/* Solute species s (0 <= s < species): its concentration field as exported
+ * by the last step of the latest lb_step call (C, N floats), its totals
+ * {sum_q h_q over non-solid cells, cumulative inlet flux, cumulative outlet
+ * flux} (totals, 3 doubles; the fluxes as in lb_reduce) and its populations h_q
+ * (h, 19 N doubles, as lb_get_populations). Any pointer may be NULL; host or
+ * device pointers. LB_EINVAL for s out of range or without solute. */
+int lb_species_state(lb_ctx *ctx, int32_t s, float *C, double *totals, double *h);
 
 /* Free-surface state: cell types (LB_CELL_*) and liquid mass m per cell
  * (in the collision precision, widened to double). */

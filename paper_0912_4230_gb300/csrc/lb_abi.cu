@@ -48,6 +48,9 @@ struct lb_ctx {
   bool solute = false, fs = false, has_solid = false, flux = false;
   unsigned f_wall = 0, f_press = 0, f_vel = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
   bool open_faces = false;  // pressure or velocity faces: per-cell kernel only
+  int S = 0;                // solute species (0 without the solute lattice)
+  void *vel = nullptr;      // S > 1: bare V and V' of the step (6 N Real)
+  void *spec = nullptr;     // S > 1: per-species 1/tau_D, C_in, D_s/D_0 (24 Real)
   void *face = nullptr;  // per-face values of pressure / velocity faces (24 Real)
   long long t = 0;
   long long n_live = 0;
@@ -166,6 +169,10 @@ void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
   a.f_press = c->f_press;
   a.f_vel = c->f_vel;
   a.face = static_cast<const Real *>(c->face);
+  a.vel = static_cast<Real *>(c->vel);
+  a.spec = static_cast<const Real *>(c->spec);
+  a.species = c->S;
+  a.slot_stride = c->nwarps * 2;
   a.s_wall = c->s_wall;
   a.s_inlet = c->s_inlet;
   a.s_outlet = c->s_outlet;
@@ -230,7 +237,7 @@ int check_status(lb_ctx *c) {
 // Launch shape of the row-staged kernel for rows of bx threads: the grid is
 // the resident blocks of all SMs, at most one block per row.
 bool pipe_shape(const lb_ctx *c, unsigned bx, lb_ctx::PipeShape *ps) {
-  if (!c->ops->pipe_config || c->open_faces) return false;
+  if (!c->ops->pipe_config || c->open_faces || c->S > 1) return false;
   size_t smem = 0;
   int bps = 0, sms = 0, dev = 0;
   const bool ok = c->ops->pipe_config(c->kmode, c->solute, bx, &smem, &bps) &&
@@ -277,6 +284,9 @@ FsArgs<Real> fs_args(lb_ctx *c, const StepArgs<Real> &a, long long t) {
 }
 
 unsigned fs_tile_count(const lb_ctx *c) { return c->ntx * c->nty * c->ntz; }
+
+// features of the per-cell step kernel this lattice needs
+int step_feat(const lb_ctx *c) { return (c->open_faces ? FEAT_OPEN : 0) | (c->S > 1 ? FEAT_VEL : 0); }
 
 // One warp waits, with the step kernels' bounded wait, on a shared-memory
 // barrier that nothing completes; on giving up it sets the timeout bit of the
@@ -345,6 +355,12 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (prm->visc_law != 0 && !prm->solute)
     return fail(nullptr, LB_EINVAL, "a concentration-dependent viscosity needs the solute lattice");
   if (prm->solute && !(prm->tau_D > 0.5)) return fail(nullptr, LB_EINVAL, "tau_D <= 1/2");
+  if (prm->species < 0 || prm->species > LB_MAX_SPECIES)
+    return fail(nullptr, LB_EINVAL, "species outside [0, LB_MAX_SPECIES]");
+  if (prm->species > 1 && !prm->solute)
+    return fail(nullptr, LB_EINVAL, "several species need the solute lattice");
+  for (int sp = 1; sp < prm->species; ++sp)
+    if (!(prm->species_tau_D[sp] > 0.5)) return fail(nullptr, LB_EINVAL, "species tau_D <= 1/2");
   if (prm->free_surface && (prm->solute || K6))
     return fail(nullptr, LB_EUNSUPPORTED, "free surface with solute or permeability");
   if ((face_mask(dom->bc, LB_BC_PRESSURE) | face_mask(dom->bc, LB_BC_VELOCITY)) &&
@@ -412,19 +428,42 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   const size_t pb = size_t(Q) * N * ops->elt_bytes;
   // device memory
   const bool shift = (prm->storage == LB_STORE_FP16DEV || prm->storage == LB_STORE_BF16DEV);
+  c->S = c->solute ? std::max(1, int(prm->species)) : 0;
+  const size_t S = size_t(std::max(c->S, 1));
   for (int b = 0; b < 2; ++b) {
     if (!(c->f[b] = dev_alloc(c, pb))) return bail(fail(c, LB_ENOMEM, "populations f"));
-    if (c->solute && !(c->h[b] = dev_alloc(c, pb))) return bail(fail(c, LB_ENOMEM, "populations h"));
+    if (c->solute && !(c->h[b] = dev_alloc(c, S * pb)))
+      return bail(fail(c, LB_ENOMEM, "populations h"));
     if (shift) {
       c->rf[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
       if (!c->rf[b]) return bail(fail(c, LB_ENOMEM, "references"));
-      if (c->solute && !(c->rh[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)))))
+      if (c->solute && !(c->rh[b] = static_cast<float *>(dev_alloc(c, S * N * sizeof(float)))))
         return bail(fail(c, LB_ENOMEM, "references"));
     }
   }
+  if (c->S > 1) {
+    double sv[24] = {};
+    const double D0 = (prm->tau_D - 0.5) / 3.0;
+    for (int sp = 0; sp < c->S; ++sp) {
+      const double tD = sp ? prm->species_tau_D[sp] : prm->tau_D;
+      sv[sp] = 1.0 / tD;
+      sv[8 + sp] = sp ? prm->species_C_in[sp] : prm->C_in;
+      sv[16 + sp] = ((tD - 0.5) / 3.0) / D0;
+    }
+    if (!(c->vel = dev_alloc(c, 6 * N * rb)) || !(c->spec = dev_alloc(c, 24 * rb)))
+      return bail(fail(c, LB_ENOMEM, "species"));
+    float sf[24];
+    for (int i = 0; i < 24; ++i) sf[i] = float(sv[i]);
+    cudaError_t e = cudaMemcpyAsync(c->spec, rb == 8 ? static_cast<const void *>(sv) : sf,
+                                    24 * rb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host arrays leave scope
+    if (e != cudaSuccess)
+      return bail(fail(c, LB_ECUDA, std::string("species values: ") + cudaGetErrorString(e)));
+  }
   c->eps = dev_alloc(c, N * rb);
   c->link = static_cast<uint32_t *>(dev_alloc(c, N * 4));
-  c->fields = static_cast<float *>(dev_alloc(c, 6 * N * sizeof(float)));
+  // rho, u (3), C, nu, then C of species 1 .. S-1
+  c->fields = static_cast<float *>(dev_alloc(c, (5 + S) * N * sizeof(float)));
   c->partials = static_cast<double *>(dev_alloc(c, size_t(c->nblk) * 4 * sizeof(double)));
   c->state = static_cast<DevState *>(dev_alloc(c, sizeof(DevState)));
   if (!c->eps || !c->link || !c->fields || !c->partials || !c->state)
@@ -526,7 +565,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   // row-pipelined kernel: eligible shapes only; grid = resident blocks of all SMs
   // (automatic selection keeps the per-cell kernel: on GB300 at 128^3 it is
   // 2x faster than this row-pipelined form, which stays available on request)
-  if (prm->kernel != 1 && !c->fs && !c->open_faces && ops->tma_config) {
+  if (prm->kernel != 1 && !c->fs && !c->open_faces && c->S <= 1 && ops->tma_config) {
     int bps = 0, sms = 0, dev = 0;
     if (ops->tma_config(c->kmode, c->solute, unsigned(dom->nx), &c->tma_smem, &c->tma_threads,
                         &bps) &&
@@ -554,7 +593,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     if (c->fs || !ops->pipe_config || !pipe_shape(c, bx, &c->pipe))
       return bail(fail(c, LB_EUNSUPPORTED, "row-staged kernel: this lattice or storage"));
   }
-  c->flux_slots = static_cast<double *>(dev_alloc(c, size_t(c->nwarps) * 2 * sizeof(double)));
+  c->flux_slots = static_cast<double *>(
+      dev_alloc(c, size_t(c->nwarps) * 2 * size_t(std::max(c->S, 1)) * sizeof(double)));
   if (!c->flux_slots) return bail(fail(c, LB_ENOMEM, "flux slots"));
   sa.eps = c->eps;
   sa.kinv = c->kinv;
@@ -593,18 +633,19 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
   if (c->solute && !C0) return fail(c, LB_EINVAL, "C0 is required with the solute lattice");
   if (c->fs && !cell_type) return fail(c, LB_EINVAL, "cell_type is required with a free surface");
   const size_t N = c->N;
-  const size_t bytes = N * 4 * 5 + (f_scale ? size_t(Q) * N * 4 : 0) + N * 4 + N + 256;
+  const size_t S = size_t(std::max(c->S, 1));  // C0: N values per species
+  const size_t bytes = N * 4 * (4 + S) + (f_scale ? size_t(Q) * N * 4 : 0) + N * 4 + N + 256;
   char *st = static_cast<char *>(stage(c, bytes));
   if (!st) return fail(c, LB_ENOMEM, "staging");
   float *d_rho = reinterpret_cast<float *>(st);
   float *d_u = d_rho + N;
   float *d_C = d_u + 3 * N;
-  float *d_lam = d_C + N;
+  float *d_lam = d_C + S * N;
   float *d_fs = d_lam + N;
   uint8_t *d_type = reinterpret_cast<uint8_t *>(d_fs + (f_scale ? size_t(Q) * N : 0));
   CK(c, cudaMemcpyAsync(d_rho, rho0, N * 4, cudaMemcpyDefault, c->stream));
   CK(c, cudaMemcpyAsync(d_u, u0, 3 * N * 4, cudaMemcpyDefault, c->stream));
-  if (C0) CK(c, cudaMemcpyAsync(d_C, C0, N * 4, cudaMemcpyDefault, c->stream));
+  if (C0) CK(c, cudaMemcpyAsync(d_C, C0, S * N * 4, cudaMemcpyDefault, c->stream));
   if (f_scale) CK(c, cudaMemcpyAsync(d_fs, f_scale, size_t(Q) * N * 4, cudaMemcpyDefault, c->stream));
   if (c->fs) {
     CK(c, cudaMemcpyAsync(d_type, cell_type, N, cudaMemcpyDefault, c->stream));
@@ -613,7 +654,9 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
   c->t = 0;
   c->cur = 0;
   CK(c, cudaMemsetAsync(c->state, 0, sizeof(DevState), c->stream));
-  CK(c, cudaMemsetAsync(c->flux_slots, 0, size_t(c->nwarps) * 2 * sizeof(double), c->stream));
+  CK(c, cudaMemsetAsync(c->flux_slots, 0,
+                        size_t(c->nwarps) * 2 * size_t(std::max(c->S, 1)) * sizeof(double),
+                        c->stream));
   if (c->fs) {
     CK(c, fs_init(c->N, c->link, d_type, d_rho, lambda0 ? d_lam : nullptr, c->type[0], c->type[1],
                   c->mass[0], c->lam, c->ops->fp64, c->stream));
@@ -643,6 +686,7 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
     in.f_scale = f_scale ? d_fs : nullptr;
     in.type = c->fs ? c->type[0] : nullptr;
     CK(c, c->ops->init(c->kmode, c->solute, args, &in, c->nblk, c->stream));
+    if (c->S > 1) CK(c, c->ops->species_init(args, d_u, d_C, c->nblk, c->stream));
     if (c->fs) {  // the first step's active tiles
       const FsArgs<Real> fa = fs_args(c, a, 0);
       CK(c, c->ops->fs_seed(&fa, fs_tile_count(c), (fs_tile_count(c) + BLOCK - 1) / BLOCK,
@@ -676,9 +720,11 @@ int lb_step(lb_ctx *c, int64_t n) {
       else if (c->pipe.bx)
         CK(c, c->ops->pipe_step(c->kmode, c->solute, args, c->pipe.grid, c->pipe.bx,
                                 c->pipe.smem, c->pipe.gxr, c->pipe.items, c->stream));
-      else
-        CK(c, c->ops->step(c->kmode, c->solute, c->open_faces, args, c->sgrid, c->sblock,
+      else {
+        CK(c, c->ops->step(c->kmode, c->solute, step_feat(c), args, c->sgrid, c->sblock,
                            c->stream));
+        if (c->S > 1) CK(c, c->ops->species_step(args, c->sgrid, c->sblock, c->stream));
+      }
       return int(LB_OK);
     });
     if (rc != LB_OK) return rc;
@@ -704,7 +750,8 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
   std::vector<int> alone, shared;
   for (int i = 0; i < n; ++i) {
     const dim3 g = ctxs[i]->sgrid;
-    (g.x * g.y * g.z >= wave || ctxs[i]->open_faces ? alone : shared).push_back(i);
+    (g.x * g.y * g.z >= wave || ctxs[i]->open_faces || ctxs[i]->S > 1 ? alone : shared)
+        .push_back(i);
   }
   const int ns = int(shared.size());
   std::vector<unsigned> begin(size_t(ns) + 1);
@@ -750,8 +797,9 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
     for (int i : alone) {
       StepArgs<Real> a;
       step_args(ctxs[i], a);
-      CK(c0, c0->ops->step(c0->kmode, c0->solute, ctxs[i]->open_faces, &a, ctxs[i]->sgrid,
+      CK(c0, c0->ops->step(c0->kmode, c0->solute, step_feat(ctxs[i]), &a, ctxs[i]->sgrid,
                            ctxs[i]->sblock, s));
+      if (ctxs[i]->S > 1) CK(c0, c0->ops->species_step(&a, ctxs[i]->sgrid, ctxs[i]->sblock, s));
     }
     for (int g0 = 0; g0 < ns; g0 += BATCH_MAX) {
       const int g1 = std::min(ns, g0 + BATCH_MAX);
@@ -850,7 +898,7 @@ int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {
           CK(c, c->ops->pipe_step(c->kmode, c->solute, args, cd.ps.grid, cd.ps.bx, cd.ps.smem,
                                   cd.ps.gxr, cd.ps.items, c->stream));
         else
-          CK(c, c->ops->step(c->kmode, c->solute, c->open_faces, args, grd, blk, c->stream));
+          CK(c, c->ops->step(c->kmode, c->solute, step_feat(c), args, grd, blk, c->stream));
         return int(LB_OK);
       });
     };
@@ -921,6 +969,41 @@ int lb_reduce(lb_ctx *c, double *mass, double *solute, double *flux_in, double *
   if (flux_out) *flux_out = tot[3];
   if (st.status & 1u) return fail(c, LB_ENONFINITE, "a step reduction met a NaN or an infinity");
   return LB_OK;
+}
+
+int lb_species_state(lb_ctx *c, int32_t sp, float *C, double *totals, double *h) {
+  if (!c) return LB_EINVAL;
+  if (sp < 0 || sp >= c->S) return fail(c, LB_EINVAL, "no such solute species");
+  const size_t N = c->N;
+  const size_t hoff = size_t(sp) * Q * N * c->ops->elt_bytes;
+  const char *hs = static_cast<const char *>(c->h[c->cur]) + hoff;
+  const float *rh = c->rh[c->cur] ? c->rh[c->cur] + size_t(sp) * N : nullptr;
+  if (C) {
+    const float *src = c->fields + (sp == 0 ? 4 * N : (5 + size_t(sp)) * N);
+    CK(c, cudaMemcpyAsync(C, src, N * sizeof(float), cudaMemcpyDefault, c->stream));
+  }
+  if (totals) {
+    double *out = static_cast<double *>(stage(c, 64));
+    if (!out) return fail(c, LB_ENOMEM, "staging");
+    CK(c, c->ops->totals(c->f[c->cur], hs, c->has_solid ? c->link : nullptr, c->N, c->partials,
+                         c->nblk, c->rf[c->cur], rh, c->stream));
+    CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
+    CK(c, finish_sum(c->flux_slots + size_t(sp) * c->nwarps * 2, c->nwarps, 2, out + 2,
+                     c->stream));
+    double tot[4];
+    CK(c, cudaMemcpyAsync(tot, out, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    totals[0] = tot[1];
+    totals[1] = tot[2];
+    totals[2] = tot[3];
+  }
+  if (h) {
+    double *st = static_cast<double *>(stage(c, size_t(Q) * N * sizeof(double)));
+    if (!st) return fail(c, LB_ENOMEM, "staging");
+    CK(c, c->ops->to_f64(hs, st, c->N, 1, rh, c->stream));
+    CK(c, cudaMemcpyAsync(h, st, size_t(Q) * N * sizeof(double), cudaMemcpyDefault, c->stream));
+  }
+  return check_status(c);
 }
 
 int lb_set_populations(lb_ctx *c, const double *f, const double *h) {

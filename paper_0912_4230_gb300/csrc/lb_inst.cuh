@@ -7,6 +7,7 @@
 #include "lb_tma.cuh"
 #include "lb_batch.cuh"
 #include "lb_pipe.cuh"
+#include "lb_species.cuh"
 #include "lb_ops.h"
 
 namespace lbgb {
@@ -38,19 +39,34 @@ struct Instance {
   using Real = typename S::Real;
   using A = StepArgs<Real>;
 
-  template <int KM, bool SOL, bool OPEN>
+  template <int KM, bool SOL, int FEAT>
   static cudaError_t step_t(const A &a, dim3 grid, dim3 block, cudaStream_t s) {
-    step_kernel<S, KM, SOL, OPEN><<<grid, block, 0, s>>>(a);
+    step_kernel<S, KM, SOL, FEAT><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
   }
-  static cudaError_t step(int kmode, bool solute, bool open, const void *args, dim3 grid,
+  static cudaError_t step(int kmode, bool solute, int feat, const void *args, dim3 grid,
                           dim3 block, cudaStream_t s) {
     const A &a = *static_cast<const A *>(args);
     return dispatch_mode(kmode, solute, [&](auto km, auto sol) {
       constexpr int K = decltype(km)::value;
       constexpr bool L = decltype(sol)::value;
-      return open ? step_t<K, L, true>(a, grid, block, s) : step_t<K, L, false>(a, grid, block, s);
+      switch (feat) {
+        case 0: return step_t<K, L, 0>(a, grid, block, s);
+        case FEAT_OPEN: return step_t<K, L, FEAT_OPEN>(a, grid, block, s);
+        case FEAT_VEL: return L ? step_t<K, L, FEAT_VEL>(a, grid, block, s) : cudaErrorInvalidValue;
+        default:
+          return L ? step_t<K, L, FEAT_OPEN | FEAT_VEL>(a, grid, block, s) : cudaErrorInvalidValue;
+      }
     });
+  }
+  static cudaError_t species_step(const void *args, dim3 grid, dim3 block, cudaStream_t s) {
+    species_kernel<S><<<grid, block, 0, s>>>(*static_cast<const A *>(args));
+    return cudaGetLastError();
+  }
+  static cudaError_t species_init(const void *args, const float *u0, const float *C0,
+                                  unsigned nblk, cudaStream_t s) {
+    species_init_kernel<S><<<nblk, BLOCK, 0, s>>>(*static_cast<const A *>(args), u0, C0);
+    return cudaGetLastError();
   }
   template <int KM, bool SOL>
   static cudaError_t init_t(const A &a, const InitArgs<Real> &in, unsigned nblk, cudaStream_t s) {
@@ -234,6 +250,8 @@ struct Instance {
       o.fs_seed = &fs_seed;
     }
     o.batch_step = &batch_step;
+    o.species_step = &species_step;
+    o.species_init = &species_init;
     o.tma_config = nullptr;
     o.tma_step = nullptr;
     o.pipe_config = nullptr;

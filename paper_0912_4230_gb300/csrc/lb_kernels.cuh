@@ -17,6 +17,12 @@
 
 namespace lbgb {
 
+// Compile-time features of the per-cell step kernel, each a separate
+// instantiation so that lattices without them keep the plain code:
+// pressure / velocity faces of the fluid lattice, and the export of each
+// cell's bare V and V' for the pass over further solute species.
+enum : int { FEAT_OPEN = 1, FEAT_VEL = 2 };
+
 template <int I, int N>
 struct Unroll {
   template <class F>
@@ -449,7 +455,7 @@ __device__ __forceinline__ void fluid_moments(FV fv, Real &drho, Real (&V)[3]) {
 // stores and exported fields. fv(q) and hv(q) give the arriving f_q - w_q and
 // h_q, kv(r) the rows of K^-1; drho, rho, V are the fluid moments, sC the
 // solute total of the arriving h.
-template <class S, int KMODE, bool SOLUTE, class FV, class HV, class KV>
+template <class S, int KMODE, bool SOLUTE, bool VEL = false, class FV, class HV, class KV>
 __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a, unsigned n,
                                              const CellGeo &g, FV fv, HV hv, KV kv,
                                              typename S::Real drho, typename S::Real rho,
@@ -519,12 +525,20 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
     if constexpr (S::kShift) a.rh_out[n] = float(sC);
   }
   if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
+  if constexpr (VEL) {
+    a.vel[n] = V[0];
+    a.vel[size_t(N) + n] = V[1];
+    a.vel[2 * size_t(N) + n] = V[2];
+    a.vel[3 * size_t(N) + n] = fc.Vp[0];
+    a.vel[4 * size_t(N) + n] = fc.Vp[1];
+    a.vel[5 * size_t(N) + n] = fc.Vp[2];
+  }
 }
 
 // The per-cell update of one step from global memory: stream f (and h),
 // moments, viscosity, colour gradient, V' and the Darcy force, fluid and
 // solute collision, store; accumulates the cell's flux and totals.
-template <class S, int KMODE, bool SOLUTE, bool OPEN = false>
+template <class S, int KMODE, bool SOLUTE, int FEAT = 0>
 __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a, unsigned x,
                                             unsigned y, unsigned z, unsigned n, uint32_t link,
                                             typename S::Real &fin_acc,
@@ -536,7 +550,7 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
   const CellGeo g = cell_geo_xyz(x, y, z, a.nx, a.ny, a.nz);
   const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
   Real d[Q];
-  // OPEN: the lattice has pressure or velocity faces. A separate
+  // FEAT_OPEN: the lattice has pressure or velocity faces. A separate
   // instantiation keeps the code of the lattices without them as it is (any
   // extra branch in this gather changes the register allocation of the
   // plain path at its 80-register cap and costs it ~15 %).
@@ -556,7 +570,7 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
         d[q] += wq<Real>(q) * __ldg(a.rf_in + (long long)n + (bb ? 0 : src_delta<q>(g)));
     });
   };
-  if constexpr (!OPEN) {
+  if constexpr (!(FEAT & FEAT_OPEN)) {
     // every source is a cell, or bounce-back
     if (link == 0 && !(g.onface & a.f_wall))
       gather_cells();
@@ -629,7 +643,7 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
     }
     Unroll<0, Q>::run([&](auto qc) { sC += hh[SOLUTE ? decltype(qc)::value : 0]; });
   }
-  collide_tail<S, KMODE, SOLUTE>(
+  collide_tail<S, KMODE, SOLUTE, (FEAT & FEAT_VEL) != 0>(
       a, n, g, [&](auto qc) { return d[decltype(qc)::value]; },
       [&](auto qc) { return hh[SOLUTE ? decltype(qc)::value : 0]; },
       [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
@@ -643,7 +657,7 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
 // thread): measured on GB300 at 128^3 this is 1.1x faster than the
 // unconstrained build (112 registers), since the kernel is bound by loads in
 // flight, and a little faster than 256-thread blocks at the same occupancy.
-template <class S, int KMODE, bool SOLUTE, bool OPEN>
+template <class S, int KMODE, bool SOLUTE, int FEAT>
 __global__ void __launch_bounds__(STEP_BLOCK, 6) step_kernel(const StepArgs<typename S::Real> a) {
   using Real = typename S::Real;
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -662,7 +676,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, 6) step_kernel(const StepArgs<type
   }
   Real fin_acc = Real(0), fout_acc = Real(0), drho = Real(0), sC = Real(0);
   bool open_face = false;
-  if (live) update_cell<S, KMODE, SOLUTE, OPEN>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
+  if (live) update_cell<S, KMODE, SOLUTE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
   warp_reductions(a, warp_gid, open_face, fin_acc, fout_acc, drho, sC);
 }
 

@@ -29,7 +29,8 @@ STORE = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_get_populations",
            "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
            "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
-           "lb_totals_noalloc", "lb_step_batch", "lb_autotune", "lb_debug_wait_timeout"]
+           "lb_totals_noalloc", "lb_step_batch", "lb_autotune", "lb_debug_wait_timeout",
+           "lb_species_state"]
 
 
 class LbError(RuntimeError):
@@ -50,7 +51,9 @@ class lb_params(ctypes.Structure):
                 ("forchheimer", c_double), ("solute", c_int32), ("tau_D", c_double),
                 ("C_in", c_double), ("free_surface", c_int32), ("storage", c_int32),
                 ("check_every", c_int32), ("kernel", c_int32),
-                ("face_P", (c_double * 2) * 3), ("face_u", ((c_double * 3) * 2) * 3)]
+                ("face_P", (c_double * 2) * 3), ("face_u", ((c_double * 3) * 2) * 3),
+                ("species", c_int32), ("species_tau_D", c_double * 8),
+                ("species_C_in", c_double * 8)]
 
 
 _lib = None
@@ -75,6 +78,7 @@ def load() -> ctypes.CDLL:
     L.lb_reduce.argtypes = [vp] * 5
     L.lb_debug_neighbors.argtypes = [vp, c_int32, vp]
     L.lb_debug_wait_timeout.argtypes = [vp, c_int64]
+    L.lb_species_state.argtypes = [vp, c_int32, vp, vp, vp]
     L.lb_free_surface_state.argtypes = [vp, vp, vp]
     L.lb_sync.argtypes = [vp]
     L.lb_time.argtypes = [vp]
@@ -172,6 +176,10 @@ def lb_debug_neighbors(ctx, lattice: int, src):
 
 def lb_debug_wait_timeout(ctx, limit_ns: int):
     _check(load().lb_debug_wait_timeout(ctx, int(limit_ns)), ctx)
+
+
+def lb_species_state(ctx, s: int, C=None, totals=None, h=None):
+    _check(load().lb_species_state(ctx, int(s), _ptr(C), _ptr(totals), _ptr(h)), ctx)
 
 
 def lb_free_surface_state(ctx, cell_type=None, mass=None):
@@ -272,6 +280,11 @@ def make_params(prob, storage=None, check_every=0, kernel="auto") -> lb_params:
             for i in range(3):
                 p.face_u[ax][side][i] = fu[ax][side][i]
     p.forchheimer = k.get("forchheimer", 0.0)
+    p.species = int(k.get("species", 1 if k.get("solute") else 0))
+    for s_, v in enumerate(k.get("species_tau_D", ())):
+        p.species_tau_D[s_] = v
+    for s_, v in enumerate(k.get("species_C_in", ())):
+        p.species_C_in[s_] = v
     p.solute = int(k.get("solute", 0))
     p.tau_D = k.get("tau_D", 1.0)
     p.C_in = k.get("C_in", 0.0)
@@ -328,6 +341,13 @@ class Lattice:
 
     def reduce(self):
         return lb_reduce(self.ctx)
+
+    def species_state(self, s: int):
+        """Species s: (C field, [solute total, inlet flux, outlet flux], h[19, N])."""
+        N = self.N
+        C, tot, h = np.zeros(N, np.float32), np.zeros(3), np.zeros(Q * N)
+        lb_species_state(self.ctx, s, C, tot, h)
+        return C, tot, h.reshape(Q, N)
 
     def populations(self):
         f = np.zeros(Q * self.N)
