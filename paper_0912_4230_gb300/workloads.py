@@ -256,6 +256,70 @@ def miscible_species(nx=128, ny=128, nz=128, seed=0, steps=5000, storage="fp32")
                         C0=(None, np.full(N, 0.3, np.float32))).replace(name="miscible_species")
 
 
+def wood_density(xi, rho0=310.0, a=0.62, b=0.2, c=-0.2):
+    """Eq. wooddensityfunc with the ring coordinate xi in [0, 1) of one year
+    ring: rho = rho0 [1 + 2 a xi^b exp(-c xi)] (kg/m^3)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    return rho0 * (1.0 + 2.0 * a * np.power(xi, b) * np.exp(-c * xi))
+
+
+def wood_tensor(rho, rho_max=1500.0, scale=1.0):
+    """Eq. Ktensor's principal permeabilities (radial, longitudinal,
+    tangential) for the density rho: (rho_max/rho)^2 eps^(11/3) (8.2, 51470,
+    0.82) times `scale` (the lattice unit), eps = 1 - rho/rho_max (Eq.
+    epsilonfunction)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    eps = 1.0 - rho / rho_max
+    f = (rho_max / rho) ** 2 * eps ** (11.0 / 3.0) * scale
+    return eps, np.stack([8.2 * f, 51470.0 * f, 0.82 * f], axis=-1)
+
+
+def wood(nx=90, ny=90, nz=1, wood_depth=60, delta=30.0, angle=45.0, rho0=310.0, a=0.62,
+         b=0.2, c=-0.2, rho_max=1500.0, K_scale=1e-3, P_ext=0.0441, nu_g=0.15,
+         a_h=2.05e-9, alpha=2e-3, beta=1e-3, tau_D=0.8, steps=2000) -> Problem:
+    """Penetration of an adhesive into wood (Section 5.5), read as miscible
+    displacement: the adhesive (solute concentration C = 1) fills a reservoir
+    above the wood (y >= wood_depth: eps = 1, negligible drag) and is pressed
+    by P_ext into the wood sample (y < wood_depth), initially filled with
+    solvent (C = 0). Year rings of width delta cells inclined by `angle` in
+    the x-y plane: density from Eq. wooddensityfunc along the ring
+    coordinate, porosity from Eq. epsilonfunction, permeability tensor of Eq.
+    Ktensor in the ring frame (radial across the rings, longitudinal along
+    z, tangential along the rings), rotated into the lattice (a full SPD K),
+    scaled by K_scale to lattice units. Faces: top PRESSURE 1/3 + P_ext with
+    solute INLET C = 1, bottom PRESSURE 1/(3 mean eps) with solute OUTLET, x and
+    z periodic. Viscosity Eq. nuall (hardening)."""
+    N = nx * ny * nz
+    x, y, z = _grid(nx, ny, nz)
+    th = np.deg2rad(angle)
+    r_dir = np.array([np.cos(th), np.sin(th), 0.0])      # radial: across the rings
+    t_dir = np.array([-np.sin(th), np.cos(th), 0.0])     # tangential: along the rings
+    l_dir = np.array([0.0, 0.0, 1.0])                    # longitudinal: the fibres
+    xi = np.mod((x * r_dir[0] + y * r_dir[1]) / delta, 1.0)
+    rho_w = wood_density(xi, rho0, a, b, c)
+    eps_w, kp = wood_tensor(rho_w, rho_max, K_scale)
+    R = np.stack([r_dir, l_dir, t_dir], axis=1)           # columns: principal axes
+    Kw = np.einsum("ij,nj,kj->nik", R, kp, R)
+    in_wood = y < wood_depth
+    eps = np.where(in_wood, eps_w, 1.0)
+    K = np.where(in_wood[:, None, None], Kw, 1e6 * np.eye(3)[None])
+    K6 = np.stack([K[:, 0, 0], K[:, 1, 1], K[:, 2, 2], K[:, 0, 1], K[:, 1, 2], K[:, 2, 0]], axis=1)
+    C0 = np.where(in_wood, 0.0, 1.0)
+    P_top = 1.0 / 3.0 + P_ext
+    eps_bottom = float(np.mean(eps[y == 0]))
+    P_bot = 1.0 / (3.0 * eps_bottom)
+    rho0_field = np.where(in_wood, 3.0 * eps * P_bot, 3.0 * P_top).astype(np.float32)
+    bc = ((PERIODIC, PERIODIC), (PRESSURE, PRESSURE), (PERIODIC, PERIODIC))
+    sbc = ((PERIODIC, PERIODIC), (OUTLET, INLET), (PERIODIC, PERIODIC))
+    fp, fu = _faces(P={(1, 0): P_bot, (1, 1): P_top})
+    params = dict(visc_law=2, nu_g=nu_g, a=a_h, alpha=alpha, beta=beta, solute=1,
+                  tau_D=tau_D, C_in=1.0, face_P=fp, face_u=fu)
+    return _base("wood", nx, ny, nz, bc, sbc, params, eps.astype(np.float32),
+                 K6.astype(np.float32).ravel(), rho0=rho0_field, C0=C0.astype(np.float32),
+                 steps=steps, storage="fp64",
+                 meta=dict(wood_depth=wood_depth, delta=delta, angle=angle, rho_max=rho_max))
+
+
 def _random_rotations(nblocks, seed):
     """Haar-random rotation matrices from unit quaternions of 4 normals."""
     rng = _rng(seed)
