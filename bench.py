@@ -53,6 +53,9 @@ def _other_workloads():
         "species": (lambda r: W.miscible_species(seed=r), "fp32", 4 * 152 + 17,
                     "miscible medium 128^3 with three solute species (tau_D 0.8 / 1.2 / 0.6), "
                     "D3Q19 fluid + 3 solute lattices, FP32; step = fused pass + species pass"),
+        "wood": (lambda r: W.wood(nx=256, ny=192, nz=64, wood_depth=128), "fp32", 333,
+                 "adhesive pressed into wood 256x192x64 (year rings of 30 cells at 45 deg, "
+                 "full SPD K, pressure faces, solute inlet/outlet, hardening law), FP32"),
         "forchheimer": (lambda r: W.forchheimer(seed=r), "fp32", 321,
                         "coarse porous medium 128^3 with Forchheimer drag (diagonal K, "
                         "K_zz = 10 K_xx, G 1e-4), D3Q19 fluid + solute, FP32"),
