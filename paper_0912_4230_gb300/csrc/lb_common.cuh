@@ -62,6 +62,9 @@ __host__ __device__ constexpr unsigned faces_ahead(int q) { return faces_crossed
 // Population storage formats. ld_f returns f_q - w_q, ld_h returns h_q, both
 // in the collision type Real; st_* take the same quantities.
 // ------------------------------------------------------------------------
+// FP32 / FP64 populations are stored with plain stores: measured on GB300 at
+// 128^3 they step 1.3 % faster than with the evict-first hint (the written
+// lines stay in L2 and drain behind the next loads).
 struct StoreF32 {
   using T = float;
   using Real = float;
@@ -70,9 +73,9 @@ struct StoreF32 {
   template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
-  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
+  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { *p = v; }
   template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
-  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { __stcs(p, v); }
+  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { *p = v; }
   __host__ __device__ static double to_f(T v, int q, double = 0.0) { return double(v) + wq<double>(q); }
   __host__ __device__ static T from_f(double f, int q, double = 0.0) { return T(f - wq<double>(q)); }
   __host__ __device__ static double to_h(T v, int, double = 0.0) { return double(v); }
@@ -87,9 +90,9 @@ struct StoreF64 {
   template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
-  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { __stcs(p, v); }
+  template <int q> __device__ __forceinline__ static void st_f(T *p, Real v) { *p = v; }
   template <int q> __device__ __forceinline__ static Real ld_h(const T *p) { return __ldg(p); }
-  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { __stcs(p, v); }
+  template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) { *p = v; }
   __host__ __device__ static double to_f(T v, int q, double = 0.0) { return v + wq<double>(q); }
   __host__ __device__ static T from_f(double f, int q, double = 0.0) { return f - wq<double>(q); }
   __host__ __device__ static double to_h(T v, int, double = 0.0) { return v; }
