@@ -371,7 +371,8 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
   const float *fl = a.fields;
   if (tn == CELL_NEW_INTERFACE) {
     // density and V' of each neighbour from its post-collision populations
-    // in the collision type (exact: the free surface has no Darcy drag)
+    // in the collision type (exact: the free surface has no Darcy drag); the
+    // 19 loads of a neighbour are unrolled so that they are in flight together
     const T *fo = static_cast<const T *>(a.f_out);
     Real rs = Real(0), u0 = Real(0), u1 = Real(0), u2 = Real(0);
     int cnt = 0;
@@ -381,20 +382,21 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
       if (y < 0) return;
       const uint8_t ty = s.type_new[y];
       if (ty != CELL_LIQUID && ty != CELL_INTERFACE) return;
-      double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
-      for (int k = 0; k < Q; ++k) {
-        const double v = S::to_f(fo[size_t(k) * N + y], k) - wq<double>(k);
+      Real r = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
+      Unroll<0, Q>::run([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const Real v = S::template ld_f<k>(fo + size_t(k) * N + y);
         r += v;
-        j0 += cx(k) * v;
-        j1 += cy(k) * v;
-        j2 += cz(k) * v;
-      }
-      const double ry = 1.0 + r;
-      const double ey = double(a.eps[y]);
-      rs += Real(ry);
-      u0 += Real(j0 / ry - 0.5 * ey * double(a.G[0]));
-      u1 += Real(j1 / ry - 0.5 * ey * double(a.G[1]));
-      u2 += Real(j2 / ry - 0.5 * ey * double(a.G[2]));
+        if (cx(k)) j0 += Real(cx(k)) * v;
+        if (cy(k)) j1 += Real(cy(k)) * v;
+        if (cz(k)) j2 += Real(cz(k)) * v;
+      });
+      const Real ry = Real(1) + r, iry = Real(1) / ry;
+      const Real ey = a.eps[y];
+      rs += ry;
+      u0 += j0 * iry - Real(0.5) * ey * a.G[0];
+      u1 += j1 * iry - Real(0.5) * ey * a.G[1];
+      u2 += j2 * iry - Real(0.5) * ey * a.G[2];
       ++cnt;
     });
     const Real ic = Real(1) / Real(cnt > 0 ? cnt : 1);
