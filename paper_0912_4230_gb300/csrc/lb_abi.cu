@@ -68,7 +68,7 @@ struct lb_ctx {
   // free surface
   uint8_t *type[2] = {nullptr, nullptr};
   void *mass[2] = {nullptr, nullptr};
-  void *lam = nullptr, *share = nullptr;
+  void *lam = nullptr, *share = nullptr, *mom = nullptr;
   uint8_t *flag_a = nullptr, *flag_b = nullptr;
   unsigned *any = nullptr;
   // free surface: active-tile lists (step parity), their lengths, tile stamps
@@ -270,6 +270,7 @@ FsArgs<Real> fs_args(lb_ctx *c, const StepArgs<Real> &a, long long t) {
   fa.flag_a = c->flag_a;
   fa.flag_b = c->flag_b;
   fa.share = static_cast<Real *>(c->share);
+  fa.mom = static_cast<Real *>(c->mom);
   fa.any = c->any;
   fa.tiles = c->tiles[t & 1];
   fa.n_tiles = c->n_tiles + (t & 1);
@@ -495,6 +496,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     }
     c->lam = dev_alloc(c, N * rb);
     c->share = dev_alloc(c, N * rb);
+    c->mom = dev_alloc(c, 4 * N * rb);
     c->flag_a = static_cast<uint8_t *>(dev_alloc(c, N));
     c->flag_b = static_cast<uint8_t *>(dev_alloc(c, N));
     c->any = static_cast<unsigned *>(dev_alloc(c, sizeof(unsigned)));
@@ -506,7 +508,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     c->tiles[1] = static_cast<uint32_t *>(dev_alloc(c, ntiles * sizeof(uint32_t)));
     c->n_tiles = static_cast<unsigned *>(dev_alloc(c, 2 * sizeof(unsigned)));
     c->stamp = static_cast<unsigned *>(dev_alloc(c, ntiles * sizeof(unsigned)));
-    if (!c->lam || !c->share || !c->flag_a || !c->flag_b || !c->any || !c->tiles[0] ||
+    if (!c->lam || !c->share || !c->mom || !c->flag_a || !c->flag_b || !c->any || !c->tiles[0] ||
         !c->tiles[1] || !c->n_tiles || !c->stamp)
       return bail(fail(c, LB_ENOMEM, "free surface"));
     // persistent grid of the tile passes: enough resident blocks to cover

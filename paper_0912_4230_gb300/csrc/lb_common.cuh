@@ -239,6 +239,8 @@ struct FsArgs {
   Real *rhohat_w;        // colour-gradient field written by the mass exchange
   uint8_t *flag_a, *flag_b;
   Real *share;           // excess mass handed to each interface neighbour
+  Real *mom;             // rho, V'_x, V'_y, V'_z (4 x N) of each live cell that pulls
+                         // from an empty cell, written by the step pass
   unsigned *any;         // nonzero when some cell fills or empties this step
   // Active tiles of FS_TX x FS_TY x FS_TZ cells: the tiles within one tile
   // (26-neighbourhood, wrapped) of a tile holding a liquid or interface cell.

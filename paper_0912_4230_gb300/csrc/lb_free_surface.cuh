@@ -282,6 +282,14 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
     S::template st_f<q>(fout + size_t(q) * N + n, fc.template post<q>(d[q]));
   });
   write_fields(a.fields, N, n, rho, fc.Vp, Real(0), nu);
+  // the moments a new interface cell averages: it was empty, so each of its
+  // live neighbours pulled from it in this pass
+  if (from_gas) {
+    s.mom[n] = rho;
+    s.mom[size_t(N) + n] = fc.Vp[0];
+    s.mom[2 * size_t(N) + n] = fc.Vp[1];
+    s.mom[3 * size_t(N) + n] = fc.Vp[2];
+  }
   // flowchart step j, candidates: lambda > 1 + 1e-3 fills, lambda < -1e-3 empties
   uint8_t flag = FS_NONE;
   if (t == CELL_INTERFACE) {
@@ -368,12 +376,11 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
   if (tn != CELL_NEW_INTERFACE && f == FS_NONE) return 0u;
   const uint32_t link = a.link ? a.link[n] : 0u;
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
-  const float *fl = a.fields;
   if (tn == CELL_NEW_INTERFACE) {
-    // density and V' of each neighbour from its post-collision populations
-    // in the collision type (exact: the free surface has no Darcy drag); the
-    // 19 loads of a neighbour are unrolled so that they are in flight together
-    const T *fo = static_cast<const T *>(a.f_out);
+    // density and V' of each neighbour as its collision in this step left
+    // them (its post-collision populations carry the same moments: the
+    // collision conserves mass, and without Darcy drag their momentum is
+    // rho (V' + eps G / 2)); the loads of all neighbours are in flight together
     Real rs = Real(0), u0 = Real(0), u1 = Real(0), u2 = Real(0);
     int cnt = 0;
     Unroll<1, Q>::run([&](auto qc) {
@@ -382,21 +389,10 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
       if (y < 0) return;
       const uint8_t ty = s.type_new[y];
       if (ty != CELL_LIQUID && ty != CELL_INTERFACE) return;
-      Real r = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
-      Unroll<0, Q>::run([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        const Real v = S::template ld_f<k>(fo + size_t(k) * N + y);
-        r += v;
-        if (cx(k)) j0 += Real(cx(k)) * v;
-        if (cy(k)) j1 += Real(cy(k)) * v;
-        if (cz(k)) j2 += Real(cz(k)) * v;
-      });
-      const Real ry = Real(1) + r, iry = Real(1) / ry;
-      const Real ey = a.eps[y];
-      rs += ry;
-      u0 += j0 * iry - Real(0.5) * ey * a.G[0];
-      u1 += j1 * iry - Real(0.5) * ey * a.G[1];
-      u2 += j2 * iry - Real(0.5) * ey * a.G[2];
+      rs += s.mom[y];
+      u0 += s.mom[size_t(N) + y];
+      u1 += s.mom[2 * size_t(N) + y];
+      u2 += s.mom[3 * size_t(N) + y];
       ++cnt;
     });
     const Real ic = Real(1) / Real(cnt > 0 ? cnt : 1);
