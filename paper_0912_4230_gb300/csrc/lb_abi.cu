@@ -473,17 +473,21 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if ((prm->A != 0.0 || c->fs) && !(c->rhohat = dev_alloc(c, N * rb)))
     return bail(fail(c, LB_ENOMEM, "rhohat"));
   {
-    // per-face values: 3 x pressure (the face density over eps), velocity
-    double fv[24] = {};
+    // per-face values: 3 x pressure (the face density over eps), velocity,
+    // and the part of 3 x pressure below the collision type's rounding (the
+    // face density rho_b = 3 eps P sits near 1, and the flow it drives follows
+    // rho_b - 1, which the rounded 3P alone would carry to only ~1e-7)
+    double fv[30] = {};
     for (int f = 0; f < 6; ++f) {
       fv[f] = 3.0 * prm->face_P[f / 2][f % 2];
       for (int i = 0; i < 3; ++i) fv[6 + 3 * f + i] = prm->face_u[f / 2][f % 2][i];
+      if (rb == 4) fv[24 + f] = fv[f] - double(float(fv[f]));
     }
-    if (!(c->face = dev_alloc(c, 24 * rb))) return bail(fail(c, LB_ENOMEM, "face values"));
-    float ff[24];
-    for (int i = 0; i < 24; ++i) ff[i] = float(fv[i]);
+    if (!(c->face = dev_alloc(c, 30 * rb))) return bail(fail(c, LB_ENOMEM, "face values"));
+    float ff[30];
+    for (int i = 0; i < 30; ++i) ff[i] = float(fv[i]);
     cudaError_t e = cudaMemcpyAsync(c->face, rb == 8 ? static_cast<const void *>(fv) : ff,
-                                    24 * rb, cudaMemcpyHostToDevice, c->stream);
+                                    30 * rb, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host arrays leave scope
     if (e != cudaSuccess)
       return bail(fail(c, LB_ECUDA, std::string("face values: ") + cudaGetErrorString(e)));

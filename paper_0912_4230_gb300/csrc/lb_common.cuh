@@ -70,6 +70,7 @@ struct StoreF32 {
   using Real = float;
   static constexpr int id = 0;
   static constexpr bool kShift = false;
+  static constexpr float kScale = 1.0f;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
@@ -87,6 +88,7 @@ struct StoreF64 {
   using Real = double;
   static constexpr int id = 1;
   static constexpr bool kShift = false;
+  static constexpr float kScale = 1.0f;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real cv_h(T v) { return v; }
   template <int q> __device__ __forceinline__ static Real ld_f(const T *p) { return __ldg(p); }
@@ -130,6 +132,14 @@ struct StoreF16 {
   template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) {
     __stcs(p, __float2half_rn(v * (float(inv_wq(q)) * kScale)));
   }
+  // the remainder g itself (unscaled), and a store of a value already in
+  // storage units
+  template <int q> __device__ __forceinline__ static Real ld_e(const T *p) {
+    return __half2float(__ldg(p)) * (1.0f / kScale);
+  }
+  template <int q> __device__ __forceinline__ static void st_raw(T *p, Real v) {
+    __stcs(p, __float2half_rn(v));
+  }
   // with ref: f = w (g + ref) + w, h = w (g + ref)
   __device__ static double to_f(T v, int q, double ref) { return (double(__half2float(v)) / kScale + ref) * wq<double>(q) + wq<double>(q); }
   __device__ static T from_f(double f, int q, double ref) { return __float2half_rn(float(((f - wq<double>(q)) * inv_wq(q) - ref) * kScale)); }
@@ -142,6 +152,7 @@ struct StoreBF16 {
   using Real = float;
   static constexpr int id = 3;
   static constexpr bool kShift = true;
+  static constexpr float kScale = 1.0f;
   template <int q> __device__ __forceinline__ static Real cv_f(T v) {
     return __bfloat162float(v) * wq<float>(q);
   }
@@ -159,6 +170,12 @@ struct StoreBF16 {
   }
   template <int q> __device__ __forceinline__ static void st_h(T *p, Real v) {
     __stcs(p, __float2bfloat16_rn(v * float(inv_wq(q))));
+  }
+  template <int q> __device__ __forceinline__ static Real ld_e(const T *p) {
+    return __bfloat162float(__ldg(p));
+  }
+  template <int q> __device__ __forceinline__ static void st_raw(T *p, Real v) {
+    __stcs(p, __float2bfloat16_rn(v));
   }
   __device__ static double to_f(T v, int q, double ref) { return (double(__bfloat162float(v)) + ref) * wq<double>(q) + wq<double>(q); }
   __device__ static T from_f(double f, int q, double ref) { return __float2bfloat16_rn(float((f - wq<double>(q)) * inv_wq(q) - ref)); }
@@ -200,7 +217,8 @@ struct StepArgs {
   const Real *geps;      // 3 x N: D grad(eps)/eps (solute only)
   const uint32_t *link;  // N: bit q = source x - c_q solid; bit 31 = cell solid (NULL: no solids)
   const Real *rhohat;    // N colour-gradient field (A != 0)
-  const Real *face;      // per face (2 axis + side): [0, 6) 3 x pressure, [6, 24) velocity xyz
+  const Real *face;      // per face (2 axis + side): [0, 6) 3 x pressure, [6, 24) velocity xyz,
+                         // [24, 30) 3 x pressure minus its rounding to Real
   Real G[3];
   Real tau, tau0, tau1, nu_g, a_h, alpha, beta;
   int visc_law;

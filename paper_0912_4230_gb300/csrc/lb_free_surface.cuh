@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
   fc.st = (a.A != Real(0)) && fc.Fn > st_threshold<Real>();
   fc.stc = fc.st ? a.A * eps * tau : Real(0);
   fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
+  fc.fold(Real(1), Real(0));
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     S::template st_f<q>(fout + size_t(q) * N + n, fc.template post<q>(d[q]));

@@ -284,37 +284,60 @@ __device__ __forceinline__ void colour_gradient(const Real *__restrict__ rh, uns
 // forcing terms (Eq. coeffforce1, with the weight and density factor w_q rho)
 // for one direction, in deviation form:
 //   f~_q - w_q = (f_q - w_q)(1 - 1/tau) + (f^eq_q - w_q)/tau + T_q.
+// fold() gathers the per-cell factors of the last two terms, so that per
+// direction they are w_q b_q with
+//   b_q = K + cu (B3 + B45 cu + P9 cF) + P3 cF [+ S2 (c_q.F)^2],
+// cu = c_q.V', cF = c_q.F_e (K0 in place of K for the rest direction), taken
+// as scale (b_q - shift): scale 1 and shift 0 give the deviation above;
+// 16-bit storage folds its scale and the cell's reference into them.
 template <class Real>
 struct FluidCollide {
   Real drho, rho, ie, uu, uF, itau, omt, pre, stc, Fn, iFn;
   Real Vp[3], Fe[3], F[3];
   bool st;
+  Real K, K0, B3, B45, P9, P3, S2;
 
+  __device__ __forceinline__ void fold(Real scale, Real shift) {
+    // 1/tau (f^eq - w) + T at cu = cF = 0, without the surface-tension part
+    const Real kb = itau * drho - Real(1.5) * itau * rho * ie * uu - Real(3) * pre * ie * uF;
+    const Real ks = st ? itau * stc * Fn : Real(0);
+    K = scale * (kb - ks - shift);
+    K0 = scale * (kb + ks - shift);
+    B3 = scale * Real(3) * itau * rho;
+    B45 = scale * Real(4.5) * itau * rho * ie;
+    P9 = scale * Real(9) * pre * ie;
+    P3 = scale * Real(3) * pre;
+    S2 = st ? scale * itau * stc * iFn : Real(0);
+  }
+  template <int q>
+  __device__ __forceinline__ Real br() const {
+    if (q == 0) return K0;
+    const Real cu = Real(cx(q)) * Vp[0] + Real(cy(q)) * Vp[1] + Real(cz(q)) * Vp[2];
+    const Real cF = Real(cx(q)) * Fe[0] + Real(cy(q)) * Fe[1] + Real(cz(q)) * Fe[2];
+    Real b = cu * (B3 + B45 * cu + P9 * cF) + (P3 * cF + K);
+    if (st) {
+      const Real cs = Real(cx(q)) * F[0] + Real(cy(q)) * F[1] + Real(cz(q)) * F[2];
+      b += S2 * cs * cs;
+    }
+    return b;
+  }
+  // f^eq_q - w_q (with the surface-tension part), for initialisation
   template <int q>
   __device__ __forceinline__ Real feq_dev() const {
     constexpr Real w = wq<Real>(q);
-    if (q == 0) {
-      return w * (drho - rho * Real(1.5) * ie * uu) + (st ? stc * w * Fn : Real(0));
-    } else {
-      const Real cu = Real(cx(q)) * Vp[0] + Real(cy(q)) * Vp[1] + Real(cz(q)) * Vp[2];
-      Real e = w * (drho + rho * (Real(3) * cu + Real(4.5) * ie * cu * cu - Real(1.5) * ie * uu));
-      if (st) {
-        const Real cF = Real(cx(q)) * F[0] + Real(cy(q)) * F[1] + Real(cz(q)) * F[2];
-        e += w * stc * (cF * cF * iFn - Fn);
-      }
-      return e;
-    }
-  }
-  template <int q>
-  __device__ __forceinline__ Real force() const {
-    constexpr Real w = wq<Real>(q);
+    if (q == 0) return w * (drho - rho * Real(1.5) * ie * uu) + (st ? stc * w * Fn : Real(0));
     const Real cu = Real(cx(q)) * Vp[0] + Real(cy(q)) * Vp[1] + Real(cz(q)) * Vp[2];
-    const Real cF = Real(cx(q)) * Fe[0] + Real(cy(q)) * Fe[1] + Real(cz(q)) * Fe[2];
-    return w * pre * (Real(3) * cF + Real(9) * ie * cu * cF - Real(3) * ie * uF);
+    Real e = w * (drho + rho * (Real(3) * cu + Real(4.5) * ie * cu * cu - Real(1.5) * ie * uu));
+    if (st) {
+      const Real cs = Real(cx(q)) * F[0] + Real(cy(q)) * F[1] + Real(cz(q)) * F[2];
+      e += w * stc * (cs * cs * iFn - Fn);
+    }
+    return e;
   }
+  // f~_q - w_q after fold(1, 0)
   template <int q>
   __device__ __forceinline__ Real post(Real d) const {
-    return d * omt + feq_dev<q>() * itau + force<q>();
+    return fma(wq<Real>(q), br<q>(), d * omt);
   }
 };
 
@@ -412,10 +435,12 @@ __device__ __noinline__ Pops<typename S::Real> gather_open_faces(
     if (cls == PULL_BOUNCE) {
       v = own[opp(q)];
     } else if (cls == PULL_PRESSURE) {
-      const Real rb = eps * __ldg(a.face + crossed_face<q>(g, a.f_press));
+      // rho_b - 1 from 3P = hi + lo with one rounding of eps hi - 1
+      const int fi = crossed_face<q>(g, a.f_press);
+      const Real rbm1 = fma(eps, __ldg(a.face + fi), Real(-1)) + eps * __ldg(a.face + 24 + fi);
+      const Real rb = Real(1) + rbm1;
       const Real cu = Real(cx(q)) * u0 + Real(cy(q)) * u1 + Real(cz(q)) * u2;
-      const Real e = wq<Real>(q) * ((rb - Real(1)) +
-                                    rb * (Real(4.5) * ie * cu * cu - Real(1.5) * ie * uu));
+      const Real e = wq<Real>(q) * (rbm1 + rb * (Real(4.5) * ie * cu * cu - Real(1.5) * ie * uu));
       v = Real(2) * e - own[opp(q)];
     } else if (cls == PULL_VELOCITY) {
       const Real *uf = a.face + 6 + 3 * crossed_face<q>(g, a.f_vel);
@@ -432,17 +457,27 @@ __device__ __noinline__ Pops<typename S::Real> gather_open_faces(
 }
 
 // Fluid moments of the arriving populations: drho += sum_q (f_q - w_q) and
-// V = j / rho with j = sum_q c_q (f_q - w_q), rho = 1 + drho.
-template <class Real, class FV>
+// V = j / rho with j = sum_q c_q (f_q - w_q), rho = 1 + drho. With E the
+// values are e_q = (f_q - w_q)/w_q (16-bit storage) and carry their weights
+// here.
+template <bool E = false, class Real, class FV>
 __device__ __forceinline__ void fluid_moments(FV fv, Real &drho, Real (&V)[3]) {
   Real j0 = Real(0), j1 = Real(0), j2 = Real(0);
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const Real v = fv(qc);
-    drho += v;
-    if (cx(q)) j0 += Real(cx(q)) * v;
-    if (cy(q)) j1 += Real(cy(q)) * v;
-    if (cz(q)) j2 += Real(cz(q)) * v;
+    if constexpr (E) {
+      constexpr Real w = wq<Real>(q);
+      drho = fma(w, v, drho);
+      if (cx(q)) j0 = fma(Real(cx(q)) * w, v, j0);
+      if (cy(q)) j1 = fma(Real(cy(q)) * w, v, j1);
+      if (cz(q)) j2 = fma(Real(cz(q)) * w, v, j2);
+    } else {
+      drho += v;
+      if (cx(q)) j0 += Real(cx(q)) * v;
+      if (cy(q)) j1 += Real(cy(q)) * v;
+      if (cz(q)) j2 += Real(cz(q)) * v;
+    }
   });
   const Real irho = rcp(Real(1) + drho);
   V[0] = j0 * irho;
@@ -453,8 +488,8 @@ __device__ __forceinline__ void fluid_moments(FV fv, Real &drho, Real (&V)[3]) {
 // The per-cell arithmetic after streaming: concentration and viscosity,
 // colour gradient, V' and the Darcy force, fluid and solute collision,
 // stores and exported fields. fv(q) and hv(q) give the arriving f_q - w_q and
-// h_q, kv(r) the rows of K^-1; drho, rho, V are the fluid moments, sC the
-// solute total of the arriving h.
+// h_q (16-bit storage: (f_q - w_q)/w_q and h_q/w_q), kv(r) the rows of K^-1;
+// drho, rho, V are the fluid moments, sC the solute total of the arriving h.
 template <class S, int KMODE, bool SOLUTE, bool VEL = false, class FV, class HV, class KV>
 __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a, unsigned n,
                                              const CellGeo &g, FV fv, HV hv, KV kv,
@@ -491,15 +526,47 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
     fc.stc = fc.st ? a.A * eps * tau : Real(0);
     fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
   }
-  Unroll<0, Q>::run([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    Real v = fc.template post<q>(fv(qc));
-    if constexpr (S::kShift) v -= wq<Real>(q) * drho;
-    S::template st_f<q>(fo + int(q * N), v);
-  });
+  if constexpr (S::kShift) {
+    // per unit weight, (f~_q - w_q)/w_q = omt e_q + b_q; stored as the
+    // remainder scale ((f~_q - w_q)/w_q - drho)
+    fc.fold(Real(S::kScale), drho);
+    const Real so = Real(S::kScale) * fc.omt;
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      S::template st_raw<q>(fo + int(q * N), fma(so, fv(qc), fc.template br<q>()));
+    });
+  } else {
+    fc.fold(Real(1), Real(0));
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      S::template st_f<q>(fo + int(q * N), fc.template post<q>(fv(qc)));
+    });
+  }
   if constexpr (S::kShift) a.rf_out[n] = float(drho);
 
-  if (SOLUTE) {
+  if constexpr (SOLUTE && S::kShift) {
+    // per unit weight: h~_q/w_q = (1 - 1/tau_D) h_q/w_q + h^eq_q/(w_q tau_D),
+    // h^eq_q/w_q = sC (1 + 3 c_q.v); stored as scale (h~_q/w_q - sC). The
+    // rest direction takes sC - sum_{q>0} h^eq_q, divided by its weight with
+    // a correctly rounded division, so the weights' rounding adds no solute.
+    T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
+    const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
+    const Real itd = a.inv_tau_D;
+    const Real sc = Real(S::kScale);
+    const Real sod = sc * (Real(1) - itd), h0 = sc * sC * (itd - Real(1)),
+               h3 = Real(3) * sc * itd * sC, s3 = Real(3) * sC;
+    Real hsum = Real(0);
+    Unroll<1, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+      hsum = fma(wq<Real>(q), fma(s3, cv, sC), hsum);
+      S::template st_raw<q>(ho + int(q * N), fma(sod, hv(qc), fma(h3, cv, h0)));
+    });
+    const Real he0 = (sC - hsum) / wq<Real>(0);
+    const Real h = hv(std::integral_constant<int, 0>{});
+    S::template st_raw<0>(ho, fma(sod, h, sc * (itd * he0 - sC)));
+    a.rh_out[n] = float(sC);
+  } else if constexpr (SOLUTE) {
     T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
     const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
     const Real itd = a.inv_tau_D;
@@ -514,15 +581,12 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
       const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
       hsum += heq;
       const Real h = hv(qc);
-      const Real shift = S::kShift ? wq<Real>(q) * sC : Real(0);
-      S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd - shift);
+      S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd);
     });
     {
       const Real h = hv(std::integral_constant<int, 0>{});
-      const Real shift = S::kShift ? wq<Real>(0) * sC : Real(0);
-      S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd - shift);
+      S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd);
     }
-    if constexpr (S::kShift) a.rh_out[n] = float(sC);
   }
   if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
   if constexpr (VEL) {
@@ -554,20 +618,26 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
   // instantiation keeps the code of the lattices without them as it is (any
   // extra branch in this gather changes the register allocation of the
   // plain path at its 80-register cap and costs it ~15 %).
+  // 16-bit storage: d[q] = (f_q - w_q)/w_q = g_q + the source cell's reference
   auto gather_cells = [&]() {
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
-      d[q] = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
-      if constexpr (S::kShift) d[q] += wq<Real>(q) * __ldg(a.rf_in + (long long)n + src_delta<q>(g));
+      if constexpr (S::kShift)
+        d[q] = S::template ld_e<q>(fb + (int(q * N) + src_delta<q>(g))) +
+               __ldg(a.rf_in + (long long)n + src_delta<q>(g));
+      else
+        d[q] = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
     });
   };
   auto gather_bounce = [&]() {
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       const bool bb = fluid_class<q>(g, link, a.f_wall) == PULL_BOUNCE;
-      d[q] = S::template ld_f<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g)));
       if constexpr (S::kShift)
-        d[q] += wq<Real>(q) * __ldg(a.rf_in + (long long)n + (bb ? 0 : src_delta<q>(g)));
+        d[q] = S::template ld_e<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g))) +
+               __ldg(a.rf_in + (long long)n + (bb ? 0 : src_delta<q>(g)));
+      else
+        d[q] = S::template ld_f<q>(fb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g)));
     });
   };
   if constexpr (!(FEAT & FEAT_OPEN)) {
@@ -581,7 +651,10 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
       gather_cells();
     } else if (g.onface & (a.f_press | a.f_vel)) {
       const Pops<Real> o = gather_open_faces<S>(a, g, n, link);
-      Unroll<0, Q>::run([&](auto qc) { d[decltype(qc)::value] = o.v[decltype(qc)::value]; });
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        d[q] = S::kShift ? o.v[q] * Real(inv_wq(q)) : o.v[q];
+      });
     } else {
       gather_bounce();
     }
@@ -602,41 +675,69 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
     if (h_simple) {
       Unroll<0, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
         if constexpr (S::kShift)
-          hh[SOLUTE ? q : 0] += wq<Real>(q) * __ldg(a.rh_in + (long long)n + src_delta<q>(g));
+          hh[SOLUTE ? q : 0] = S::template ld_e<q>(hb + (int(q * N) + src_delta<q>(g))) +
+                               __ldg(a.rh_in + (long long)n + src_delta<q>(g));
+        else
+          hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
       });
     }
   }
   Real V[3];
-  fluid_moments([&](auto qc) { return d[decltype(qc)::value]; }, drho, V);
+  fluid_moments<S::kShift>([&](auto qc) { return d[decltype(qc)::value]; }, drho, V);
   const Real rho = Real(1) + drho;
   const Real ie = rcp(eps);
 
-  if (SOLUTE) {
+  if constexpr (SOLUTE && S::kShift) {
+    if (!h_simple) {
+      // as below, per unit weight (h_q/w_q); the fluxes carry the weights
+      const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
+      const Real own = __ldg(a.rh_in + n);
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
+        Real v;
+        if (cls == PULL_CELL) {
+          v = S::template ld_e<q>(hb + (int(q * N) + src_delta<q>(g))) +
+              __ldg(a.rh_in + (long long)n + src_delta<q>(g));
+        } else if (cls == PULL_BOUNCE) {
+          v = S::template ld_e<opp(q)>(hb + int(opp(q) * N)) + own;
+        } else if (cls == PULL_INLET) {
+          const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
+          v = eps * a.C_in * (Real(1) + Real(3) * cv);
+          fin_acc += wq<Real>(q) * (v - (S::template ld_e<opp(q)>(hb + int(opp(q) * N)) + own));
+        } else {
+          v = S::template ld_e<q>(hb + int(q * N)) + own;
+          fout_acc += wq<Real>(q) * ((S::template ld_e<opp(q)>(hb + int(opp(q) * N)) + own) - v);
+        }
+        hh[SOLUTE ? q : 0] = v;
+      });
+    }
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      sC = fma(wq<Real>(q), hh[SOLUTE ? q : 0], sC);
+    });
+  } else if constexpr (SOLUTE) {
     if (!h_simple) {
       const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
       Unroll<0, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
         Real v;
-        // the cell's own reference term (FP16/BF16 storage), for own-cell reads
-        const Real own = S::kShift ? wq<Real>(q) * __ldg(a.rh_in + n) : Real(0);
         if (cls == PULL_CELL) {
           v = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
-          if constexpr (S::kShift) v += wq<Real>(q) * __ldg(a.rh_in + (long long)n + src_delta<q>(g));
         } else if (cls == PULL_BOUNCE) {
-          v = S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own;
+          v = S::template ld_h<opp(q)>(hb + int(opp(q) * N));
         } else if (cls == PULL_INLET) {
           // entering through an inlet face: h^eq at C_in with the cell's
           // bare streamed velocity plus D grad(eps)/eps
           const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
           v = wq<Real>(q) * eps * a.C_in * (Real(1) + Real(3) * cv);
-          fin_acc += v - (S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own);
+          fin_acc += v - S::template ld_h<opp(q)>(hb + int(opp(q) * N));
         } else {
           // outlet: the cell's own post-collision value (zero gradient)
-          v = S::template ld_h<q>(hb + int(q * N)) + own;
-          fout_acc += (S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own) - v;
+          v = S::template ld_h<q>(hb + int(q * N));
+          fout_acc += S::template ld_h<opp(q)>(hb + int(opp(q) * N)) - v;
         }
         hh[SOLUTE ? q : 0] = v;
       });

@@ -64,7 +64,10 @@ def test_species_against_the_oracle(storage):
         assert tot[1] == pytest.approx(rtot[1], rel=relf, abs=1e-9)
         assert tot[2] == pytest.approx(rtot[2], rel=relf, abs=1e-9)
         if storage != "fp16":
-            tolp = 1e-13 if storage == "fp64" else 2e-7
+            # FP32: each step rounds every population to 2^-24 of its size;
+            # 25 steps accumulate at most ~25 x 2^-24 = 1.5e-6 of max |h|
+            scale = max(1.0, float(np.abs(rh[:, live]).max()))
+            tolp = 1e-13 if storage == "fp64" else 1.5e-6 * scale
             assert np.abs(h[:, live] - rh[:, live]).max() < tolp
 
 
