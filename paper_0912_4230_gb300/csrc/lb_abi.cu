@@ -46,6 +46,9 @@ struct lb_ctx {
   } pipe;
   int kmode = KM_NONE;
   bool solute = false, fs = false, has_solid = false, flux = false;
+  // 16-bit storage with solute: f buffers hold (f, h) pairs of species 0, rf
+  // the __half2 reference pairs, h and rh species 1 .. only
+  bool paired = false;
   unsigned f_wall = 0, f_press = 0, f_vel = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
   bool open_faces = false;  // pressure or velocity faces: per-cell kernel only
   int S = 0;                // solute species (0 without the solute lattice)
@@ -184,6 +187,7 @@ void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
   a.rf_out = c->rf[1 - c->cur];
   a.rh_in = c->rh[c->cur];
   a.rh_out = c->rh[1 - c->cur];
+  a.paired = c->paired ? 1 : 0;
   a.eps = static_cast<const Real *>(c->eps);
   a.kinv = static_cast<const Real *>(c->kinv);
   a.geps = static_cast<const Real *>(c->geps);
@@ -282,6 +286,18 @@ FsArgs<Real> fs_args(lb_ctx *c, const StepArgs<Real> &a, long long t) {
   fa.nty = c->nty;
   fa.ntz = c->ntz;
   return fa;
+}
+
+// The current populations of the fluid lattice and of solute species sp as
+// stored (the paired layout keeps f and species 0 in one buffer).
+PopView f_view(const lb_ctx *c) {
+  return PopView{c->f[c->cur], c->paired ? 2 : 1, 0, c->rf[c->cur], c->paired ? 1 : 0};
+}
+PopView h_view(const lb_ctx *c, int sp) {
+  if (c->paired && sp == 0) return PopView{c->f[c->cur], 2, 1, c->rf[c->cur], 1};
+  const size_t hoff = size_t(sp - (c->paired ? 1 : 0)) * Q * c->N * c->ops->elt_bytes;
+  const float *rh = c->rh[c->cur] ? c->rh[c->cur] + size_t(sp) * c->N : nullptr;
+  return PopView{static_cast<const char *>(c->h[c->cur]) + hoff, 1, 0, rh, 0};
 }
 
 unsigned fs_tile_count(const lb_ctx *c) { return c->ntx * c->nty * c->ntz; }
@@ -431,14 +447,18 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   const bool shift = (prm->storage == LB_STORE_FP16DEV || prm->storage == LB_STORE_BF16DEV);
   c->S = c->solute ? std::max(1, int(prm->species)) : 0;
   const size_t S = size_t(std::max(c->S, 1));
+  c->paired = shift && c->solute;
+  // species held in the h buffers (the paired layout keeps species 0 with f)
+  const size_t Sh = c->solute ? S - (c->paired ? 1 : 0) : 0;
   for (int b = 0; b < 2; ++b) {
-    if (!(c->f[b] = dev_alloc(c, pb))) return bail(fail(c, LB_ENOMEM, "populations f"));
-    if (c->solute && !(c->h[b] = dev_alloc(c, S * pb)))
-      return bail(fail(c, LB_ENOMEM, "populations h"));
+    if (!(c->f[b] = dev_alloc(c, c->paired ? 2 * pb : pb)))
+      return bail(fail(c, LB_ENOMEM, "populations f"));
+    if (Sh && !(c->h[b] = dev_alloc(c, Sh * pb))) return bail(fail(c, LB_ENOMEM, "populations h"));
     if (shift) {
+      // a float per cell, or the __half2 reference pair of the paired layout
       c->rf[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
       if (!c->rf[b]) return bail(fail(c, LB_ENOMEM, "references"));
-      if (c->solute && !(c->rh[b] = static_cast<float *>(dev_alloc(c, S * N * sizeof(float)))))
+      if (Sh && !(c->rh[b] = static_cast<float *>(dev_alloc(c, S * N * sizeof(float)))))
         return bail(fail(c, LB_ENOMEM, "references"));
     }
   }
@@ -960,9 +980,8 @@ int lb_reduce(lb_ctx *c, double *mass, double *solute, double *flux_in, double *
   if (c->fs)
     CK(c, fs_totals(c->N, c->link, c->mass[c->cur], c->partials, c->ops->fp64, c->stream));
   else
-    CK(c, c->ops->totals(c->f[c->cur], c->solute ? c->h[c->cur] : nullptr,
-                         c->has_solid ? c->link : nullptr, c->N, c->partials, c->nblk,
-                         c->rf[c->cur], c->rh[c->cur], c->stream));
+    CK(c, c->ops->totals(f_view(c), c->solute ? h_view(c, 0) : PopView{}, 
+                         c->has_solid ? c->link : nullptr, c->N, c->partials, c->nblk, c->stream));
   CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
   CK(c, finish_sum(c->flux_slots, c->nwarps, 2, out + 2, c->stream));
   CK(c, cudaMemcpyAsync(tot, out, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
@@ -981,9 +1000,7 @@ int lb_species_state(lb_ctx *c, int32_t sp, float *C, double *totals, double *h)
   if (!c) return LB_EINVAL;
   if (sp < 0 || sp >= c->S) return fail(c, LB_EINVAL, "no such solute species");
   const size_t N = c->N;
-  const size_t hoff = size_t(sp) * Q * N * c->ops->elt_bytes;
-  const char *hs = static_cast<const char *>(c->h[c->cur]) + hoff;
-  const float *rh = c->rh[c->cur] ? c->rh[c->cur] + size_t(sp) * N : nullptr;
+  const PopView hv = h_view(c, sp);
   if (C) {
     const float *src = c->fields + (sp == 0 ? 4 * N : (5 + size_t(sp)) * N);
     CK(c, cudaMemcpyAsync(C, src, N * sizeof(float), cudaMemcpyDefault, c->stream));
@@ -991,8 +1008,8 @@ int lb_species_state(lb_ctx *c, int32_t sp, float *C, double *totals, double *h)
   if (totals) {
     double *out = static_cast<double *>(stage(c, 64));
     if (!out) return fail(c, LB_ENOMEM, "staging");
-    CK(c, c->ops->totals(c->f[c->cur], hs, c->has_solid ? c->link : nullptr, c->N, c->partials,
-                         c->nblk, c->rf[c->cur], rh, c->stream));
+    CK(c, c->ops->totals(f_view(c), hv, c->has_solid ? c->link : nullptr, c->N, c->partials,
+                         c->nblk, c->stream));
     CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
     CK(c, finish_sum(c->flux_slots + size_t(sp) * c->nwarps * 2, c->nwarps, 2, out + 2,
                      c->stream));
@@ -1006,7 +1023,7 @@ int lb_species_state(lb_ctx *c, int32_t sp, float *C, double *totals, double *h)
   if (h) {
     double *st = static_cast<double *>(stage(c, size_t(Q) * N * sizeof(double)));
     if (!st) return fail(c, LB_ENOMEM, "staging");
-    CK(c, c->ops->to_f64(hs, st, c->N, 1, rh, c->stream));
+    CK(c, c->ops->to_f64(hv, st, c->N, 1, c->stream));
     CK(c, cudaMemcpyAsync(h, st, size_t(Q) * N * sizeof(double), cudaMemcpyDefault, c->stream));
   }
   return check_status(c);
@@ -1019,11 +1036,11 @@ int lb_set_populations(lb_ctx *c, const double *f, const double *h) {
   if (!st) return fail(c, LB_ENOMEM, "staging");
   if (f) {
     CK(c, cudaMemcpyAsync(st, f, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
-    CK(c, c->ops->from_f64(st, c->f[c->cur], c->N, 0, c->rf[c->cur], c->stream));
+    CK(c, c->ops->from_f64(st, f_view(c), c->N, 0, c->stream));
   }
   if (h && c->solute) {
     CK(c, cudaMemcpyAsync(st, h, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
-    CK(c, c->ops->from_f64(st, c->h[c->cur], c->N, 1, c->rh[c->cur], c->stream));
+    CK(c, c->ops->from_f64(st, h_view(c, 0), c->N, 1, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
   return LB_OK;
@@ -1035,12 +1052,12 @@ int lb_get_populations(lb_ctx *c, double *f, double *h) {
   double *st = static_cast<double *>(stage(c, size_t(Q) * N * sizeof(double)));
   if (!st) return fail(c, LB_ENOMEM, "staging");
   if (f) {
-    CK(c, c->ops->to_f64(c->f[c->cur], st, c->N, 0, c->rf[c->cur], c->stream));
+    CK(c, c->ops->to_f64(f_view(c), st, c->N, 0, c->stream));
     CK(c, cudaMemcpyAsync(f, st, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
   }
   if (h && c->solute) {
-    CK(c, c->ops->to_f64(c->h[c->cur], st, c->N, 1, c->rh[c->cur], c->stream));
+    CK(c, c->ops->to_f64(h_view(c, 0), st, c->N, 1, c->stream));
     CK(c, cudaMemcpyAsync(h, st, size_t(Q) * N * 8, cudaMemcpyDefault, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
   }

@@ -140,6 +140,16 @@ struct StoreF16 {
   template <int q> __device__ __forceinline__ static void st_raw(T *p, Real v) {
     __stcs(p, __float2half_rn(v));
   }
+  // the (f, h) pair of the paired layout as unscaled remainders, and a store
+  // of a pair already in storage units
+  using T2 = __half2;
+  __device__ __forceinline__ static float2 ld2(const T2 *p) {
+    const float2 v = __half22float2(__ldg(p));
+    return make_float2(v.x * (1.0f / kScale), v.y * (1.0f / kScale));
+  }
+  __device__ __forceinline__ static void st2(T2 *p, float lo, float hi) {
+    __stcs(p, __floats2half2_rn(lo, hi));
+  }
   // with ref: f = w (g + ref) + w, h = w (g + ref)
   __device__ static double to_f(T v, int q, double ref) { return (double(__half2float(v)) / kScale + ref) * wq<double>(q) + wq<double>(q); }
   __device__ static T from_f(double f, int q, double ref) { return __float2half_rn(float(((f - wq<double>(q)) * inv_wq(q) - ref) * kScale)); }
@@ -177,11 +187,26 @@ struct StoreBF16 {
   template <int q> __device__ __forceinline__ static void st_raw(T *p, Real v) {
     __stcs(p, __float2bfloat16_rn(v));
   }
+  using T2 = __nv_bfloat162;
+  __device__ __forceinline__ static float2 ld2(const T2 *p) {
+    return __bfloat1622float2(__ldg(p));
+  }
+  __device__ __forceinline__ static void st2(T2 *p, float lo, float hi) {
+    __stcs(p, __floats2bfloat162_rn(lo, hi));
+  }
   __device__ static double to_f(T v, int q, double ref) { return (double(__bfloat162float(v)) + ref) * wq<double>(q) + wq<double>(q); }
   __device__ static T from_f(double f, int q, double ref) { return __float2bfloat16_rn(float((f - wq<double>(q)) * inv_wq(q) - ref)); }
   __device__ static double to_h(T v, int q, double ref) { return (double(__bfloat162float(v)) + ref) * wq<double>(q); }
   __device__ static T from_h(double h, int q, double ref) { return __float2bfloat16_rn(float(h * inv_wq(q) - ref)); }
 };
+
+// The FP16 reference pair (f, h) of a cell in the paired layout; the
+// references are FP16 for both 16-bit formats (the remainders are formed
+// against the rounded values, so their precision only sets how small the
+// remainders are).
+__device__ __forceinline__ float2 ld_ref2(const float *p) {
+  return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+}
 
 // ------------------------------------------------------------------------
 // Kernel arguments (passed by value).
@@ -212,6 +237,11 @@ struct StepArgs {
   void *h_out;
   const float *rf_in, *rh_in;  // FP16/BF16: per-cell references of the input populations
   float *rf_out, *rh_out;      // ... and of the output populations
+  // paired (FP16/BF16 with solute): f_in/f_out hold (f_q, h_q) of species 0
+  // as one 32-bit pair per direction and cell, rf_in/rf_out the FP16 pair of
+  // references (f, h) per cell (__half2), h_in/h_out species 1 .. only
+  // (species s at (s - 1) Q N) with their FP32 references at rh + s N
+  int paired;
   const Real *eps;       // N
   const Real *kinv;      // KM_DIAG: 3 x N (xx, yy, zz); KM_SPD: 6 x N (xx, yy, zz, xy, yz, zx)
   const Real *geps;      // 3 x N: D grad(eps)/eps (solute only)

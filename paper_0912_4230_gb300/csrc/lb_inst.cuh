@@ -84,28 +84,28 @@ struct Instance {
     rhohat_kernel<S><<<nblk, BLOCK, 0, s>>>(*static_cast<const A *>(args), static_cast<Real *>(rh));
     return cudaGetLastError();
   }
-  static cudaError_t to_f64(const void *src, double *dst, unsigned N, int lattice, const float *ref,
-                            cudaStream_t s) {
+  // the references of FP32 / FP64 storage are ignored
+  static PopView own_refs(PopView v) {
+    if (!S::kShift) v.ref = nullptr;
+    return v;
+  }
+  static cudaError_t to_f64(PopView src, double *dst, unsigned N, int lattice, cudaStream_t s) {
     const size_t tot = size_t(Q) * N;
-    to_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(
-        static_cast<const typename S::T *>(src), dst, N, lattice, S::kShift ? ref : nullptr);
+    to_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(own_refs(src), dst, N,
+                                                                             lattice);
     return cudaGetLastError();
   }
-  static cudaError_t from_f64(const double *src, void *dst, unsigned N, int lattice, float *ref,
+  static cudaError_t from_f64(const double *src, PopView dst, unsigned N, int lattice,
                               cudaStream_t s) {
     const size_t tot = size_t(Q) * N;
-    if (S::kShift) ref_from_f64_kernel<<<(N + BLOCK - 1) / BLOCK, BLOCK, 0, s>>>(src, N, lattice, ref);
-    from_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(
-        src, static_cast<typename S::T *>(dst), N, lattice, S::kShift ? ref : nullptr);
+    dst = own_refs(dst);
+    if (S::kShift) ref_from_f64_kernel<<<(N + BLOCK - 1) / BLOCK, BLOCK, 0, s>>>(src, N, lattice, dst);
+    from_f64_kernel<S><<<unsigned((tot + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(src, dst, N, lattice);
     return cudaGetLastError();
   }
-  static cudaError_t totals(const void *f, const void *h, const uint32_t *link, unsigned N,
-                            double *partials, unsigned nblk, const float *rf, const float *rh,
-                            cudaStream_t s) {
-    totals_kernel<S><<<nblk, BLOCK, 0, s>>>(static_cast<const typename S::T *>(f),
-                                             static_cast<const typename S::T *>(h), link, N,
-                                             partials, S::kShift ? rf : nullptr,
-                                             S::kShift ? rh : nullptr);
+  static cudaError_t totals(PopView f, PopView h, const uint32_t *link, unsigned N,
+                            double *partials, unsigned nblk, cudaStream_t s) {
+    totals_kernel<S><<<nblk, BLOCK, 0, s>>>(own_refs(f), own_refs(h), link, N, partials);
     return cudaGetLastError();
   }
   static cudaError_t fs_step(const void *args, unsigned grid, unsigned tile_blocks,

@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "lb_common.cuh"
+#include "lb_ops.h"
 
 namespace lbgb {
 
@@ -128,19 +129,27 @@ __device__ __forceinline__ int solute_class(const CellGeo &g, uint32_t link, uns
 }
 
 // Stream the fluid populations into d[] (f_q - w_q of the arriving populations).
+// paired: 16-bit storage in the paired layout (rf then holds __half2 pairs).
 template <class S>
 __device__ __forceinline__ void gather_f(const typename S::T *__restrict__ fin, unsigned N,
                                          unsigned n, const CellGeo &g, uint32_t link,
                                          unsigned f_wall, typename S::Real (&d)[Q],
-                                         const float *rf = nullptr) {
+                                         const float *rf = nullptr, bool paired = false) {
+  using Real = typename S::Real;
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int cls = fluid_class<q>(g, link, f_wall);
     const long long src = (cls == PULL_BOUNCE) ? (long long)n : (long long)n + src_delta<q>(g);
-    const typename S::T *p = (cls == PULL_BOUNCE) ? fin + size_t(opp(q)) * N + n
-                                                  : fin + size_t(q) * N + src;
-    d[q] = S::template ld_f<q>(p);
-    if constexpr (S::kShift) d[q] += wq<typename S::Real>(q) * __ldg(rf + src);
+    const size_t idx = (cls == PULL_BOUNCE) ? size_t(opp(q)) * N + n : size_t(q) * N + src;
+    if constexpr (S::kShift) {
+      if (paired)
+        d[q] = wq<Real>(q) * (S::ld2(reinterpret_cast<const typename S::T2 *>(fin) + idx).x +
+                              ld_ref2(rf + src).x);
+      else
+        d[q] = S::template ld_f<q>(fin + idx) + wq<Real>(q) * __ldg(rf + src);
+    } else {
+      d[q] = S::template ld_f<q>(fin + idx);
+    }
   });
 }
 
@@ -414,10 +423,22 @@ __device__ __noinline__ Pops<typename S::Real> gather_open_faces(
   const T *__restrict__ fb = static_cast<const T *>(a.f_in) + n;
   Real own[Q];
   Real r = Real(0), j0 = Real(0), j1 = Real(0), j2 = Real(0);
+  // 16-bit storage: f_q - w_q = w_q (remainder + reference), from the pairs
+  // of the paired layout or the plain rows
+  auto ld_src = [&](auto qc, int off, int roff) -> Real {
+    constexpr int q = decltype(qc)::value;
+    if constexpr (S::kShift) {
+      if (a.paired)
+        return wq<Real>(q) * (S::ld2(static_cast<const typename S::T2 *>(a.f_in) + n + off).x +
+                              ld_ref2(a.rf_in + (long long)n + roff).x);
+      return S::template ld_f<q>(fb + off) + wq<Real>(q) * __ldg(a.rf_in + (long long)n + roff);
+    } else {
+      return S::template ld_f<q>(fb + off);
+    }
+  };
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
-    Real v = S::template ld_f<q>(fb + int(q * N));
-    if constexpr (S::kShift) v += wq<Real>(q) * __ldg(a.rf_in + n);
+    const Real v = ld_src(qc, int(q * N), 0);
     own[q] = v;
     r += v;
     if (cx(q)) j0 += Real(cx(q)) * v;
@@ -448,8 +469,7 @@ __device__ __noinline__ Pops<typename S::Real> gather_open_faces(
                        Real(cz(q)) * __ldg(uf + 2);
       v = own[opp(q)] + Real(6) * wq<Real>(q) * rho * cub;
     } else {
-      v = S::template ld_f<q>(fb + (int(q * N) + src_delta<q>(g)));
-      if constexpr (S::kShift) v += wq<Real>(q) * __ldg(a.rf_in + (long long)n + src_delta<q>(g));
+      v = ld_src(qc, int(q * N) + src_delta<q>(g), src_delta<q>(g));
     }
     d.v[q] = v;
   });
@@ -526,7 +546,39 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
     fc.stc = fc.st ? a.A * eps * tau : Real(0);
     fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
   }
-  if constexpr (S::kShift) {
+  if constexpr (S::kShift && SOLUTE) {
+    // paired layout: both lattices per unit weight in one loop, one 32-bit
+    // pair store per direction. The references are drho and sC rounded to
+    // FP16; the remainders are formed against the rounded values.
+    // f: (f~_q - w_q)/w_q = omt e_q + b_q, stored scale ((f~_q - w_q)/w_q - Rf).
+    // h: h~_q/w_q = (1 - 1/tau_D) h_q/w_q + h^eq_q/(w_q tau_D) with
+    // h^eq_q/w_q = sC (1 + 3 c_q.v), stored scale (h~_q/w_q - Rh); the rest
+    // direction takes sC - sum_{q>0} h^eq_q, divided by its weight with a
+    // correctly rounded division, so the weights' rounding adds no solute.
+    const __half2 r2 = __floats2half2_rn(drho, sC);
+    const float2 R = __half22float2(r2);
+    using T2 = typename S::T2;
+    T2 *__restrict__ po = static_cast<T2 *>(a.f_out) + n;
+    const Real sc = Real(S::kScale);
+    fc.fold(sc, R.x);
+    const Real so = sc * fc.omt;
+    const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
+    const Real itd = a.inv_tau_D;
+    const Real sod = sc * (Real(1) - itd), h0 = sc * (itd * sC - R.y),
+               h3 = Real(3) * sc * itd * sC, s3 = Real(3) * sC;
+    Real hsum = Real(0);
+    Unroll<1, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+      hsum = fma(wq<Real>(q), fma(s3, cv, sC), hsum);
+      S::st2(po + int(q * N), fma(so, fv(qc), fc.template br<q>()),
+             fma(sod, hv(qc), fma(h3, cv, h0)));
+    });
+    const Real he0 = (sC - hsum) / wq<Real>(0);
+    const auto q0 = std::integral_constant<int, 0>{};
+    S::st2(po, fma(so, fv(q0), fc.template br<0>()), fma(sod, hv(q0), sc * (itd * he0 - R.y)));
+    reinterpret_cast<__half2 *>(a.rf_out)[n] = r2;
+  } else if constexpr (S::kShift) {
     // per unit weight, (f~_q - w_q)/w_q = omt e_q + b_q; stored as the
     // remainder scale ((f~_q - w_q)/w_q - drho)
     fc.fold(Real(S::kScale), drho);
@@ -542,31 +594,9 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
       S::template st_f<q>(fo + int(q * N), fc.template post<q>(fv(qc)));
     });
   }
-  if constexpr (S::kShift) a.rf_out[n] = float(drho);
+  if constexpr (S::kShift && !SOLUTE) a.rf_out[n] = float(drho);
 
-  if constexpr (SOLUTE && S::kShift) {
-    // per unit weight: h~_q/w_q = (1 - 1/tau_D) h_q/w_q + h^eq_q/(w_q tau_D),
-    // h^eq_q/w_q = sC (1 + 3 c_q.v); stored as scale (h~_q/w_q - sC). The
-    // rest direction takes sC - sum_{q>0} h^eq_q, divided by its weight with
-    // a correctly rounded division, so the weights' rounding adds no solute.
-    T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
-    const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
-    const Real itd = a.inv_tau_D;
-    const Real sc = Real(S::kScale);
-    const Real sod = sc * (Real(1) - itd), h0 = sc * sC * (itd - Real(1)),
-               h3 = Real(3) * sc * itd * sC, s3 = Real(3) * sC;
-    Real hsum = Real(0);
-    Unroll<1, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
-      hsum = fma(wq<Real>(q), fma(s3, cv, sC), hsum);
-      S::template st_raw<q>(ho + int(q * N), fma(sod, hv(qc), fma(h3, cv, h0)));
-    });
-    const Real he0 = (sC - hsum) / wq<Real>(0);
-    const Real h = hv(std::integral_constant<int, 0>{});
-    S::template st_raw<0>(ho, fma(sod, h, sc * (itd * he0 - sC)));
-    a.rh_out[n] = float(sC);
-  } else if constexpr (SOLUTE) {
+  if constexpr (SOLUTE && !S::kShift) {
     T *__restrict__ ho = static_cast<T *>(a.h_out) + n;
     const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
     const Real itd = a.inv_tau_D;
@@ -599,11 +629,98 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
   }
 }
 
+// update_cell for 16-bit storage with solute (the paired layout): one 32-bit
+// load brings f_q and h_q of a source cell, one more its reference pair, and
+// both lattices are gathered per unit weight, d[q] = (f_q - w_q)/w_q and
+// hh[q] = h_q/w_q (remainder + the source's reference).
+template <class S, int KMODE, int FEAT>
+__device__ __forceinline__ void update_cell_paired(const StepArgs<float> &a, unsigned x, unsigned y,
+                                                   unsigned z, unsigned n, uint32_t link,
+                                                   float &fin_acc, float &fout_acc, float &drho,
+                                                   float &sC, bool &open_face) {
+  using Real = float;
+  using T2 = typename S::T2;
+  const unsigned N = a.N;
+  const CellGeo g = cell_geo_xyz(x, y, z, a.nx, a.ny, a.nz);
+  const T2 *__restrict__ pb = static_cast<const T2 *>(a.f_in) + n;
+  const float *__restrict__ rb = a.rf_in + n;  // a __half2 per cell
+  Real d[Q], hh[Q];
+  const unsigned s_open = a.s_inlet | a.s_outlet;
+  open_face = (g.onface & s_open) != 0;
+  bool f_simple = link == 0 && !(g.onface & a.f_wall);
+  if constexpr ((FEAT & FEAT_OPEN) != 0) f_simple = f_simple && !(g.onface & (a.f_press | a.f_vel));
+  const bool both = f_simple && link == 0 && !(g.onface & (a.s_wall | s_open));
+  if (both) {
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const float2 p = S::ld2(pb + (int(q * N) + src_delta<q>(g)));
+      const float2 r = ld_ref2(rb + src_delta<q>(g));
+      d[q] = p.x + r.x;
+      hh[q] = p.y + r.y;
+    });
+  } else if (((FEAT & FEAT_OPEN) != 0) && (g.onface & (a.f_press | a.f_vel))) {
+    const Pops<Real> o = gather_open_faces<S>(a, g, n, link);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      d[q] = o.v[q] * Real(inv_wq(q));
+    });
+  } else {
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const bool bb = fluid_class<q>(g, link, a.f_wall) == PULL_BOUNCE;
+      d[q] = S::ld2(pb + (bb ? int(opp(q) * N) : int(q * N) + src_delta<q>(g))).x +
+             ld_ref2(rb + (bb ? 0 : src_delta<q>(g))).x;
+    });
+  }
+  const Real eps = __ldg(a.eps + n);
+  const Real gx = __ldg(a.geps + n), gy = __ldg(a.geps + N + n),
+             gz = __ldg(a.geps + 2 * size_t(N) + n);
+  Real V[3];
+  fluid_moments<true>([&](auto qc) { return d[decltype(qc)::value]; }, drho, V);
+  const Real rho = Real(1) + drho;
+  const Real ie = rcp(eps);
+  if (!both) {
+    // the solute classes, per unit weight; the fluxes carry the weights
+    const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
+    const Real own = ld_ref2(rb).y;
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
+      Real v;
+      if (cls == PULL_CELL) {
+        v = S::ld2(pb + (int(q * N) + src_delta<q>(g))).y + ld_ref2(rb + src_delta<q>(g)).y;
+      } else if (cls == PULL_BOUNCE) {
+        v = S::ld2(pb + int(opp(q) * N)).y + own;
+      } else if (cls == PULL_INLET) {
+        // entering through an inlet face: h^eq at C_in with the cell's bare
+        // streamed velocity plus D grad(eps)/eps
+        const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
+        v = eps * a.C_in * (Real(1) + Real(3) * cv);
+        fin_acc += wq<Real>(q) * (v - (S::ld2(pb + int(opp(q) * N)).y + own));
+      } else {
+        // outlet: the cell's own post-collision value (zero gradient)
+        v = S::ld2(pb + int(q * N)).y + own;
+        fout_acc += wq<Real>(q) * ((S::ld2(pb + int(opp(q) * N)).y + own) - v);
+      }
+      hh[q] = v;
+    });
+  }
+  Unroll<0, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    sC = fma(wq<Real>(q), hh[q], sC);
+  });
+  collide_tail<S, KMODE, true, (FEAT & FEAT_VEL) != 0>(
+      a, n, g, [&](auto qc) { return d[decltype(qc)::value]; },
+      [&](auto qc) { return hh[decltype(qc)::value]; },
+      [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
+      gz);
+}
+
 // The per-cell update of one step from global memory: stream f (and h),
 // moments, viscosity, colour gradient, V' and the Darcy force, fluid and
 // solute collision, store; accumulates the cell's flux and totals.
 template <class S, int KMODE, bool SOLUTE, int FEAT = 0>
-__device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a, unsigned x,
+__device__ __forceinline__ void update_cell_sep(const StepArgs<typename S::Real> &a, unsigned x,
                                             unsigned y, unsigned z, unsigned n, uint32_t link,
                                             typename S::Real &fin_acc,
                                             typename S::Real &fout_acc, typename S::Real &drho,
@@ -675,11 +792,7 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
     if (h_simple) {
       Unroll<0, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        if constexpr (S::kShift)
-          hh[SOLUTE ? q : 0] = S::template ld_e<q>(hb + (int(q * N) + src_delta<q>(g))) +
-                               __ldg(a.rh_in + (long long)n + src_delta<q>(g));
-        else
-          hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+        hh[SOLUTE ? q : 0] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
       });
     }
   }
@@ -688,36 +801,7 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
   const Real rho = Real(1) + drho;
   const Real ie = rcp(eps);
 
-  if constexpr (SOLUTE && S::kShift) {
-    if (!h_simple) {
-      // as below, per unit weight (h_q/w_q); the fluxes carry the weights
-      const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
-      const Real own = __ldg(a.rh_in + n);
-      Unroll<0, Q>::run([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
-        Real v;
-        if (cls == PULL_CELL) {
-          v = S::template ld_e<q>(hb + (int(q * N) + src_delta<q>(g))) +
-              __ldg(a.rh_in + (long long)n + src_delta<q>(g));
-        } else if (cls == PULL_BOUNCE) {
-          v = S::template ld_e<opp(q)>(hb + int(opp(q) * N)) + own;
-        } else if (cls == PULL_INLET) {
-          const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
-          v = eps * a.C_in * (Real(1) + Real(3) * cv);
-          fin_acc += wq<Real>(q) * (v - (S::template ld_e<opp(q)>(hb + int(opp(q) * N)) + own));
-        } else {
-          v = S::template ld_e<q>(hb + int(q * N)) + own;
-          fout_acc += wq<Real>(q) * ((S::template ld_e<opp(q)>(hb + int(opp(q) * N)) + own) - v);
-        }
-        hh[SOLUTE ? q : 0] = v;
-      });
-    }
-    Unroll<0, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      sC = fma(wq<Real>(q), hh[SOLUTE ? q : 0], sC);
-    });
-  } else if constexpr (SOLUTE) {
+  if constexpr (SOLUTE) {
     if (!h_simple) {
       const Real vi0 = V[0] + gx, vi1 = V[1] + gy, vi2 = V[2] + gz;
       Unroll<0, Q>::run([&](auto qc) {
@@ -749,6 +833,19 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
       [&](auto qc) { return hh[SOLUTE ? decltype(qc)::value : 0]; },
       [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
       gz);
+}
+
+template <class S, int KMODE, bool SOLUTE, int FEAT = 0>
+__device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a, unsigned x,
+                                            unsigned y, unsigned z, unsigned n, uint32_t link,
+                                            typename S::Real &fin_acc,
+                                            typename S::Real &fout_acc, typename S::Real &drho,
+                                            typename S::Real &sC, bool &open_face) {
+  if constexpr (S::kShift && SOLUTE)
+    update_cell_paired<S, KMODE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
+  else
+    update_cell_sep<S, KMODE, SOLUTE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC,
+                                            open_face);
 }
 
 // One time step for every non-solid cell (see update_cell).
@@ -796,7 +893,8 @@ __global__ void __launch_bounds__(BLOCK) rhohat_kernel(const StepArgs<typename S
   }
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
   Real d[Q];
-  gather_f<S>(static_cast<const typename S::T *>(a.f_in), a.N, n, g, link, a.f_wall, d, a.rf_in);
+  gather_f<S>(static_cast<const typename S::T *>(a.f_in), a.N, n, g, link, a.f_wall, d, a.rf_in,
+              a.paired != 0);
   Real s = Real(0);
   Unroll<0, Q>::run([&](auto qc) { s += d[decltype(qc)::value]; });
   rhohat[n] = Real(1) + s;
@@ -823,6 +921,25 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
   T *fout2 = static_cast<T *>(const_cast<void *>(a.f_in));  // both buffers get the same state
   const bool solid = a.link && (__ldg(a.link + n) >> 31);
   const bool empty = in.type && in.type[n] == CELL_EMPTY;
+  if constexpr (S::kShift && SOLUTE) {
+    // paired layout: (f, h) remainders per direction, FP16 reference pairs
+    using T2 = typename S::T2;
+    T2 *p1 = static_cast<T2 *>(a.f_out) + n;
+    T2 *p0 = static_cast<T2 *>(const_cast<void *>(a.f_in)) + n;
+    if (solid || empty) {
+      // absolute populations 0: references (-1, 0), remainders 0
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        S::st2(p1 + size_t(q) * N, 0.0f, 0.0f);
+        S::st2(p0 + size_t(q) * N, 0.0f, 0.0f);
+      });
+      const __half2 r2 = __floats2half2_rn(-1.0f, 0.0f);
+      reinterpret_cast<__half2 *>(a.rf_out)[n] = r2;
+      reinterpret_cast<__half2 *>(const_cast<float *>(a.rf_in))[n] = r2;
+      if (a.fields) zero_fields(a.fields, N, n);
+      return;
+    }
+  }
   if (solid || empty) {
     // absolute populations 0 (FP16/BF16: reference -1, remainders 0)
     const Real shift = S::kShift ? Real(-1) : Real(0);
@@ -881,6 +998,35 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
     devs[q] = dev;
     dsum += dev;
   });
+  if constexpr (S::kShift && SOLUTE) {
+    const Real vs0 = u[0] + a.geps[n], vs1 = u[1] + a.geps[N + n], vs2 = u[2] + a.geps[2 * size_t(N) + n];
+    Real hs[Q];
+    Real hsum = Real(0);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+      hs[q] = wq<Real>(q) * eps * C * (Real(1) + Real(3) * cv);
+      hsum += hs[q];
+    });
+    // remainders per unit weight against the FP16-rounded references
+    const __half2 r2 = __floats2half2_rn(dsum, hsum);
+    const float2 R = __half22float2(r2);
+    using T2 = typename S::T2;
+    T2 *p1 = static_cast<T2 *>(a.f_out) + n;
+    T2 *p0 = static_cast<T2 *>(const_cast<void *>(a.f_in)) + n;
+    const Real sc = Real(S::kScale);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const Real gf = sc * (devs[q] * Real(inv_wq(q)) - R.x);
+      const Real gh = sc * (hs[q] * Real(inv_wq(q)) - R.y);
+      S::st2(p1 + size_t(q) * N, gf, gh);
+      S::st2(p0 + size_t(q) * N, gf, gh);
+    });
+    reinterpret_cast<__half2 *>(a.rf_out)[n] = r2;
+    reinterpret_cast<__half2 *>(const_cast<float *>(a.rf_in))[n] = r2;
+    if (a.fields) write_fields(a.fields, N, n, rho, u, C, (tau - Real(0.5)) / Real(3));
+    return;
+  }
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const Real v = devs[q] - (S::kShift ? wq<Real>(q) * dsum : Real(0));
@@ -918,51 +1064,67 @@ __global__ void __launch_bounds__(BLOCK) init_kernel(const StepArgs<typename S::
 // ------------------------------------------------------------------------
 // Populations <-> absolute FP64, totals and the neighbour export.
 // ------------------------------------------------------------------------
-// ref: the per-cell references of FP16/BF16 storage (NULL otherwise)
+// The reference of cell n in a view (0 without references).
+__device__ __forceinline__ double pop_ref(const PopView &v, unsigned n) {
+  if (!v.ref) return 0.0;
+  if (v.ref_pair) {
+    const __half2 r = static_cast<const __half2 *>(v.ref)[n];
+    return double(v.off ? __high2float(r) : __low2float(r));
+  }
+  return double(static_cast<const float *>(v.ref)[n]);
+}
 template <class S>
-__global__ void to_f64_kernel(const typename S::T *src, double *dst, unsigned N, int lattice,
-                              const float *ref) {
+__device__ __forceinline__ typename S::T pop_at(const PopView &v, size_t i) {
+  return static_cast<const typename S::T *>(v.p)[size_t(v.stride) * i + v.off];
+}
+
+template <class S>
+__global__ void to_f64_kernel(const PopView v, double *dst, unsigned N, int lattice) {
   const size_t i = size_t(blockIdx.x) * BLOCK + threadIdx.x;
   if (i >= size_t(Q) * N) return;
   const int q = int(i / N);
-  const double r = ref ? double(ref[i % N]) : 0.0;
-  dst[i] = lattice == 0 ? S::to_f(src[i], q, r) : S::to_h(src[i], q, r);
+  const double r = pop_ref(v, unsigned(i % N));
+  dst[i] = lattice == 0 ? S::to_f(pop_at<S>(v, i), q, r) : S::to_h(pop_at<S>(v, i), q, r);
 }
 
-// per cell: the reference of given FP64 populations (sum of f_q - w_q, or of h_q)
-static __global__ void ref_from_f64_kernel(const double *src, unsigned N, int lattice, float *ref) {
+// per cell: the reference of given FP64 populations (sum of f_q - w_q, or of
+// h_q), stored rounded to the view's reference type
+static __global__ void ref_from_f64_kernel(const double *src, unsigned N, int lattice,
+                                           const PopView v) {
   const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
   if (n >= N) return;
   double s = 0.0;
   for (int q = 0; q < Q; ++q) s += src[size_t(q) * N + n] - (lattice == 0 ? wq<double>(q) : 0.0);
-  ref[n] = float(s);
+  if (v.ref_pair)
+    static_cast<__half *>(const_cast<void *>(v.ref))[2 * size_t(n) + v.off] = __float2half_rn(float(s));
+  else
+    static_cast<float *>(const_cast<void *>(v.ref))[n] = float(s);
 }
 
 template <class S>
-__global__ void from_f64_kernel(const double *src, typename S::T *dst, unsigned N, int lattice,
-                                const float *ref) {
+__global__ void from_f64_kernel(const double *src, const PopView v, unsigned N, int lattice) {
   const size_t i = size_t(blockIdx.x) * BLOCK + threadIdx.x;
   if (i >= size_t(Q) * N) return;
   const int q = int(i / N);
-  const double r = ref ? double(ref[i % N]) : 0.0;
-  dst[i] = lattice == 0 ? S::from_f(src[i], q, r) : S::from_h(src[i], q, r);
+  const double r = pop_ref(v, unsigned(i % N));
+  static_cast<typename S::T *>(const_cast<void *>(v.p))[size_t(v.stride) * i + v.off] =
+      lattice == 0 ? S::from_f(src[i], q, r) : S::from_h(src[i], q, r);
 }
 
 // Per-block FP64 sums of the fluid mass and the solute over non-solid cells.
 template <class S>
-__global__ void __launch_bounds__(BLOCK) totals_kernel(const typename S::T *f, const typename S::T *h,
+__global__ void __launch_bounds__(BLOCK) totals_kernel(const PopView f, const PopView h,
                                                        const uint32_t *link, unsigned N,
-                                                       double *partials, const float *rf,
-                                                       const float *rh) {
+                                                       double *partials) {
   __shared__ double sh[BLOCK][2];
   const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
   double m = 0.0, s = 0.0;
   if (n < N && !(link && (link[n] >> 31))) {
-    const double r = rf ? double(rf[n]) : 0.0;
-    for (int q = 0; q < Q; ++q) m += S::to_f(f[size_t(q) * N + n], q, r);
-    if (h) {
-      const double r2 = rh ? double(rh[n]) : 0.0;
-      for (int q = 0; q < Q; ++q) s += S::to_h(h[size_t(q) * N + n], q, r2);
+    const double r = pop_ref(f, n);
+    for (int q = 0; q < Q; ++q) m += S::to_f(pop_at<S>(f, size_t(q) * N + n), q, r);
+    if (h.p) {
+      const double r2 = pop_ref(h, n);
+      for (int q = 0; q < Q; ++q) s += S::to_h(pop_at<S>(h, size_t(q) * N + n), q, r2);
     }
   }
   sh[threadIdx.x][0] = m;

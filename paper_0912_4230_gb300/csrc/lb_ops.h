@@ -8,6 +8,18 @@
 
 namespace lbgb {
 
+// A stored lattice for the conversion and totals kernels: element (q, n) at
+// p[stride (q N + n) + off] in units of the stored type (stride 2 for the
+// (f, h) pairs of 16-bit storage with solute: off 0 f, off 1 h); ref holds
+// the FP16/BF16 references, a float per cell, or with ref_pair the half off
+// of a __half2 per cell (NULL for FP32/FP64).
+struct PopView {
+  const void *p;
+  int stride, off;
+  const void *ref;
+  int ref_pair;
+};
+
 struct StorageOps {
   int storage;       // LB_STORE_*
   size_t elt_bytes;  // bytes per stored population
@@ -25,14 +37,14 @@ struct StorageOps {
   cudaError_t (*init)(int kmode, bool solute, const void *args, const void *init_args,
                       unsigned nblk, cudaStream_t s);
   cudaError_t (*rhohat)(const void *args, void *rhohat, unsigned nblk, cudaStream_t s);
-  // ref / rf / rh: per-cell references of FP16/BF16 storage (ignored otherwise)
-  cudaError_t (*to_f64)(const void *src, double *dst, unsigned N, int lattice, const float *ref,
-                        cudaStream_t s);
-  cudaError_t (*from_f64)(const double *src, void *dst, unsigned N, int lattice, float *ref,
+  // absolute FP64 populations of a lattice (0 f, 1 h) from / into storage;
+  // from_f64 also sets the references (FP16/BF16). totals: per-block FP64
+  // sums of the fluid mass and (h.p not NULL) the solute
+  cudaError_t (*to_f64)(PopView src, double *dst, unsigned N, int lattice, cudaStream_t s);
+  cudaError_t (*from_f64)(const double *src, PopView dst, unsigned N, int lattice,
                           cudaStream_t s);
-  cudaError_t (*totals)(const void *f, const void *h, const uint32_t *link, unsigned N,
-                        double *partials, unsigned nblk, const float *rf, const float *rh,
-                        cudaStream_t s);
+  cudaError_t (*totals)(PopView f, PopView h, const uint32_t *link, unsigned N, double *partials,
+                        unsigned nblk, cudaStream_t s);
   // one free-surface step, FsArgs<Real>*: six passes over the active tiles
   // (grid blocks each) and the compaction of the next step's tiles
   // (tile_blocks = ceil(tiles / BLOCK)); fs_seed stamps and lists the first

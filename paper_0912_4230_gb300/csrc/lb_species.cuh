@@ -25,7 +25,8 @@ __device__ __forceinline__ void species_cell(const StepArgs<typename S::Real> &a
   using T = typename S::T;
   const unsigned N = a.N;
   const CellGeo g = cell_geo_xyz(x, y, z, a.nx, a.ny, a.nz);
-  const size_t off = size_t(sp) * Q * N;
+  // the paired layout keeps species 0 with f, so the h buffers start at species 1
+  const size_t off = size_t(sp - a.paired) * Q * N;
   const T *__restrict__ hb = static_cast<const T *>(a.h_in) + off + n;
   T *__restrict__ ho = static_cast<T *>(a.h_out) + off + n;
   const float *rh_in = S::kShift ? a.rh_in + size_t(sp) * N : nullptr;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(BLOCK) species_init_kernel(const StepArgs<type
   const bool solid = a.link && (__ldg(a.link + n) >> 31);
   const Real eps = a.eps[n];
   for (int sp = 1; sp < a.species; ++sp) {
-    const size_t off = size_t(sp) * Q * N;
+    const size_t off = size_t(sp - a.paired) * Q * N;
     T *h0 = const_cast<T *>(static_cast<const T *>(a.h_in)) + off + n;
     T *h1 = static_cast<T *>(a.h_out) + off + n;
     const Real C = solid ? Real(0) : Real(C0[size_t(sp) * N + n]);
