@@ -7,6 +7,8 @@ turns the C tolerance into 0.3e-5). FP64 storage: the populations agree to
 agree to float32 rounding (2^-24 relative, 1.2e-7 with margin). Index work
 (pull sources, boundary classes) is bit-exact.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -344,9 +346,9 @@ def test_fp32_long_run_parity():
 
 
 def test_fp16_long_run_error():
-    """FP16 storage with per-cell FP32 references, 2000 steps of the rotated
-    SPD medium (24^3 crop): velocity within 1e-3 of the oracle, mass drift
-    within 1e-6."""
+    """FP16 storage with per-cell FP16 reference pairs, 2000 steps of the
+    rotated SPD medium (24^3 crop): velocity within 1e-3 of the oracle, mass
+    drift within 1e-6."""
     big = W.precision(64, 64, 64, storage="fp16")
     p = W.crop(big, 16, 0, 8, 24, 24, 24)
     g = lb.Lattice(p, storage="fp16")
@@ -375,3 +377,41 @@ def test_autotune_leaves_state_and_picks_a_shape():
     o = O.Oracle(p)
     o.step(43)
     compare(g, o, p, "fp32")
+
+
+def test_reduced_precision_storage_full_protocol():
+    """The precision workload's error protocol, 10 000 steps: FP16 / BF16
+    storage against the FP32-storage GPU run over the full 256^3 domain and
+    against the FP64 oracle on a 32^3 crop. FP16 keeps max|du|/max|u| within
+    1e-3 and the mass drift within 1e-6 in both; BF16 (8-bit mantissa) is
+    held to 5e-3."""
+    steps = 10000
+    full = {}
+    for st in ("fp32", "fp16", "bf16"):
+        g = lb.Lattice(W.precision(storage=st), storage=st, check_every=100)
+        m0 = g.reduce()[0]
+        g.step(steps)
+        _, u, C, _ = g.fields()
+        full[st] = (u, C, abs(g.reduce()[0] / m0 - 1))
+        g.close()
+    u32, C32, _ = full["fp32"]
+    big = W.precision(64, 64, 64, storage="fp32")
+    crop = W.crop(big, 16, 0, 8, 32, 32, 32)
+    o = O.Oracle(crop, threads=os.cpu_count())
+    o.step(steps)
+    _, ru, rC, _ = o.fields()
+    for st, bound in (("fp16", 1e-3), ("bf16", 5e-3)):
+        u, C, drift = full[st]
+        du_full = np.abs(u - u32).max() / np.abs(u32).max()
+        g = lb.Lattice(crop.replace(storage=st), storage=st)
+        m0 = g.reduce()[0]
+        g.step(steps)
+        _, uc, Cc, _ = g.fields()
+        du_crop = np.abs(uc - ru).max() / np.abs(ru).max()
+        drift_crop = abs(g.reduce()[0] / m0 - 1)
+        g.close()
+        print(f"{st}: full vs FP32 du {du_full:.2e} dC {np.abs(C - C32).max():.2e} drift "
+              f"{drift:.1e}; crop vs oracle du {du_crop:.2e} dC {np.abs(Cc - rC).max():.2e} "
+              f"drift {drift_crop:.1e}")
+        assert du_full <= bound and du_crop <= bound
+        assert drift <= 1e-6 and drift_crop <= 1e-6
