@@ -293,6 +293,8 @@ def main():
     ap.add_argument("--workload", default="miscible")
     ap.add_argument("--kernel", default="auto", choices=["auto", "cell", "rows", "staged"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--graphs", default="on", choices=["on", "off"],
+                    help="replay step pairs from a CUDA graph (on) or launch every step")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--steps-scale", type=float, default=0.02)
     ap.add_argument("--chunk", type=int, default=100)
@@ -331,8 +333,10 @@ def main():
     choice = 0
     if not args.no_autotune and args.kernel == "auto":
         choice = lb.lb_autotune(lat.ctx, 5)   # launch shape picked by timing, state unchanged
-    for _ in range(args.warmup):
-        lat.step(1)
+    if args.graphs == "off":
+        lat.set_graphs(False)
+    # one call, so that a CUDA graph of the step pair is captured before timing
+    lat.step(args.warmup)
     torch.cuda.synchronize()
 
     K = args.steps
@@ -410,7 +414,7 @@ def main():
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)",
                   "bf16": "f32 (bf16 storage)"}[storage], "data": "synthetic",
         "config": {"workload": workload, "cells": N, "lattice": [prob.nx, prob.ny, prob.nz],
-                   "parallelism": f"replicas{ws}",
+                   "parallelism": f"replicas{ws}", "cuda_graphs": args.graphs,
                    "l2": f"inputs larger than L2: {algo * N / 1e6:.0f} MB moved per step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

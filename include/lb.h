@@ -200,6 +200,22 @@ int lb_get_populations(lb_ctx *ctx, double *f, double *h);
  * Enqueued asynchronously; launch errors return LB_ECUDA. */
 int lb_step(lb_ctx *ctx, int64_t n);
 
+/* CUDA graphs for lb_step and lb_step_batch (no counterpart in the paper;
+ * default on). While a lattice's launches repeat exactly from one step pair
+ * to the next (no free surface, no time-dependent viscosity law, check_every
+ * 0 or 1), the calls capture two steps, one of each buffer parity, into a
+ * graph once and replay it for all but the last step of the call, which is
+ * launched directly and exports the fields; the steps compute exactly what
+ * direct launches compute. A batch graph is kept by the batch's first
+ * context for its members in that order and parity. enable = 0 drops the
+ * context's graphs and launches every step directly. Synchronises the
+ * context's stream. */
+int lb_set_graphs(lb_ctx *ctx, int32_t enable);
+
+/* Test hook: bit 0 set when the context holds a captured lb_step graph, bit 1
+ * when it holds a batch graph (as the first context of a batch). */
+int lb_debug_graphs(const lb_ctx *ctx);
+
 /* Pick the step kernel and its launch shape by timing (no counterpart in the
  * paper): the per-cell kernel with rows of 32, 64 or 128 threads per block,
  * the row-staged kernel with rows of 32, 64 or 128 threads (FP32/FP64

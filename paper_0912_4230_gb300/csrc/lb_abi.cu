@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/lb.h): context management,
 // validation, device memory, and the per-step launch sequence.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -54,7 +55,17 @@ struct lb_ctx {
   int S = 0;                // solute species (0 without the solute lattice)
   void *vel = nullptr;      // S > 1: bare V and V' of the step (6 N Real)
   void *spec = nullptr;     // S > 1: per-species 1/tau_D, C_in, D_s/D_0 (24 Real)
-  void *face = nullptr;  // per-face values of pressure / velocity faces (24 Real)
+  void *face = nullptr;  // per-face values of pressure / velocity faces (30 Real)
+  // CUDA graphs: two steps (both buffer parities) captured once on a private
+  // stream and replayed while the launch configuration holds (lb_step), and
+  // the same for a batch led by this context, keyed by its members' serial
+  // numbers and parities and the work list (lb_step_batch)
+  bool graphs = true;
+  uint64_t serial = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g_step = nullptr;
+  cudaGraphExec_t g_batch = nullptr;
+  std::vector<uint64_t> g_batch_key;
   long long t = 0;
   long long n_live = 0;
   int cur = 0;
@@ -135,7 +146,17 @@ void dev_free(lb_ctx *c, void *p) {
     cudaFree(p);
 }
 
+void drop_graphs(lb_ctx *c) {
+  if (c->g_step) cudaGraphExecDestroy(c->g_step);
+  if (c->g_batch) cudaGraphExecDestroy(c->g_batch);
+  c->g_step = c->g_batch = nullptr;
+  c->g_batch_key.clear();
+}
+
 void free_all(lb_ctx *c) {
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
   for (void *p : c->allocs) {
     if (c->release_fn)
       c->release_fn(p, c->alloc_user);
@@ -303,6 +324,85 @@ PopView h_view(const lb_ctx *c, int sp) {
 unsigned fs_tile_count(const lb_ctx *c) { return c->ntx * c->nty * c->ntz; }
 
 // features of the per-cell step kernel this lattice needs
+int step_feat(const lb_ctx *c);
+
+// One step of a lattice (the one that brings it to t + 1 from buffer parity
+// cur) enqueued on stream s; with last the step exports the fields. Launches
+// only, so it can be captured into a graph.
+int enqueue_step(lb_ctx *c, cudaStream_t s, bool last) {
+  return with_args(c, [&](void *args, auto &a) {
+    using Real = std::remove_reference_t<decltype(a.G[0])>;
+    a.t = c->t + 1;
+    a.reduce = (c->prm.check_every > 0 && a.t % c->prm.check_every == 0) ? 1 : 0;
+    a.fields = last ? c->fields : nullptr;
+    if (c->fs) {
+      a.fields = c->fields;
+      const FsArgs<Real> fa = fs_args(c, a, a.t);
+      CK(c, c->ops->fs_step(&fa, c->fs_grid, (fs_tile_count(c) + BLOCK - 1) / BLOCK, s));
+      return int(LB_OK);
+    }
+    if (c->prm.A != 0.0) CK(c, c->ops->rhohat(args, c->rhohat, c->nblk, s));
+    if (c->use_tma)
+      CK(c, c->ops->tma_step(c->kmode, c->solute, args, c->tma_grid, c->tma_threads, c->tma_smem, s));
+    else if (c->pipe.bx)
+      CK(c, c->ops->pipe_step(c->kmode, c->solute, args, c->pipe.grid, c->pipe.bx, c->pipe.smem,
+                              c->pipe.gxr, c->pipe.items, s));
+    else {
+      CK(c, c->ops->step(c->kmode, c->solute, step_feat(c), args, c->sgrid, c->sblock, s));
+      if (c->S > 1) CK(c, c->ops->species_step(args, c->sgrid, c->sblock, s));
+    }
+    return int(LB_OK);
+  });
+}
+
+// A lattice's steps can be replayed from a graph when every step of a pair
+// launches the same work with the same arguments: no free surface (its tile
+// lists change), no time-dependent viscosity (t is an argument), and checks
+// on every step or none.
+bool graph_safe(const lb_ctx *c) {
+  return c->graphs && !c->fs && c->prm.visc_law != 2 && c->prm.check_every <= 1;
+}
+
+// Capture two steps, issued by step(stream) with the lattices' t and parity
+// advanced in between (enqueue restores nothing: the caller's step function
+// reads c->t / c->cur), on the leader's private stream, and instantiate.
+template <class StepFn, class AdvanceFn>
+int capture_two(lb_ctx *lead, cudaGraphExec_t *out, StepFn &&step, AdvanceFn &&advance) {
+  if (!lead->cap_stream &&
+      cudaStreamCreateWithFlags(&lead->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  if (cudaStreamBeginCapture(lead->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  int rc = step(lead->cap_stream);
+  advance(+1);
+  if (rc == LB_OK) rc = step(lead->cap_stream);
+  advance(-1);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(lead->cap_stream, &g);
+  if (rc == LB_OK && e == cudaSuccess && g &&
+      cudaGraphInstantiate(out, g, 0) == cudaSuccess) {
+    cudaGraphDestroy(g);
+    return LB_OK;
+  }
+  if (g) cudaGraphDestroy(g);
+  *out = nullptr;
+  cudaGetLastError();
+  return LB_ECUDA;
+}
+
+template <class StepFn>
+int capture_pair(lb_ctx *c, cudaGraphExec_t *out, StepFn &&step) {
+  return capture_two(c, out, step, [&](int d) {
+    c->t += d;
+    c->cur = 1 - c->cur;
+  });
+}
+
+// features of the per-cell step kernel this lattice needs
 int step_feat(const lb_ctx *c) { return (c->open_faces ? FEAT_OPEN : 0) | (c->S > 1 ? FEAT_VEL : 0); }
 
 // One warp waits, with the step kernels' bounded wait, on a shared-memory
@@ -399,6 +499,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
 
   lb_ctx *c = new (std::nothrow) lb_ctx;
   if (!c) return fail(nullptr, LB_ENOMEM, "host allocation");
+  static std::atomic<uint64_t> next_serial{1};
+  c->serial = next_serial++;
   c->dom = *dom;
   c->prm = *prm;
   c->ops = ops;
@@ -725,37 +827,42 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
 int lb_step(lb_ctx *c, int64_t n) {
   if (!c) return LB_EINVAL;
   if (n < 0) return fail(c, LB_EINVAL, "n < 0");
-  for (int64_t i = 0; i < n; ++i) {
-    c->t += 1;
-    const bool last = (i == n - 1);
-    const int rc = with_args(c, [&](void *args, auto &a) {
-      using Real = std::remove_reference_t<decltype(a.G[0])>;
-      a.t = c->t;
-      a.reduce = (c->prm.check_every > 0 && c->t % c->prm.check_every == 0) ? 1 : 0;
-      a.fields = last ? c->fields : nullptr;
-      if (c->fs) {
-        a.fields = c->fields;
-        const FsArgs<Real> fa = fs_args(c, a, c->t);
-        CK(c, c->ops->fs_step(&fa, c->fs_grid, (fs_tile_count(c) + BLOCK - 1) / BLOCK, c->stream));
-        return int(LB_OK);
+  int64_t i = 0;
+  while (i < n) {
+    // all but the last step (which exports the fields) in whole pairs from
+    // the graph, starting from buffer parity 0
+    const int64_t pairs = (n - i - 1) / 2;
+    if (pairs > 0 && c->cur == 0 && graph_safe(c)) {
+      if (!c->g_step && capture_pair(c, &c->g_step, [&](cudaStream_t s) {
+            return enqueue_step(c, s, false);
+          }) != LB_OK)
+        c->graphs = false;  // not capturable here: plain launches from now on
+      if (c->g_step) {
+        for (int64_t p = 0; p < pairs; ++p) CK(c, cudaGraphLaunch(c->g_step, c->stream));
+        c->t += 2 * pairs;
+        i += 2 * pairs;
+        continue;
       }
-      if (c->prm.A != 0.0) CK(c, c->ops->rhohat(args, c->rhohat, c->nblk, c->stream));
-      if (c->use_tma)
-        CK(c, c->ops->tma_step(c->kmode, c->solute, args, c->tma_grid, c->tma_threads, c->tma_smem,
-                               c->stream));
-      else if (c->pipe.bx)
-        CK(c, c->ops->pipe_step(c->kmode, c->solute, args, c->pipe.grid, c->pipe.bx,
-                                c->pipe.smem, c->pipe.gxr, c->pipe.items, c->stream));
-      else {
-        CK(c, c->ops->step(c->kmode, c->solute, step_feat(c), args, c->sgrid, c->sblock,
-                           c->stream));
-        if (c->S > 1) CK(c, c->ops->species_step(args, c->sgrid, c->sblock, c->stream));
-      }
-      return int(LB_OK);
-    });
+    }
+    const int rc = enqueue_step(c, c->stream, i == n - 1);
     if (rc != LB_OK) return rc;
+    c->t += 1;
     c->cur = 1 - c->cur;
+    ++i;
   }
+  return LB_OK;
+}
+
+int lb_debug_graphs(const lb_ctx *c) {
+  if (!c) return LB_EINVAL;
+  return (c->g_step ? 1 : 0) | (c->g_batch ? 2 : 0);
+}
+
+int lb_set_graphs(lb_ctx *c, int32_t enable) {
+  if (!c) return LB_EINVAL;
+  CK(c, cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  c->graphs = enable != 0;
   return LB_OK;
 }
 
@@ -812,8 +919,7 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
   // one table per launch of at most BATCH_MAX lattices, filled on the host
   // for every step (the launch copies it into its parameter space)
   std::unique_ptr<BatchTable<Real>> tab(new BatchTable<Real>());
-  for (int64_t k = 0; k < steps; ++k) {
-    const bool last = (k == steps - 1);
+  auto one_step = [&](cudaStream_t st, bool last) -> int {
     auto step_args = [&](lb_ctx *c, StepArgs<Real> &a) {
       fill_args(c, a);
       a.t = c->t + 1;
@@ -824,8 +930,8 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
       StepArgs<Real> a;
       step_args(ctxs[i], a);
       CK(c0, c0->ops->step(c0->kmode, c0->solute, step_feat(ctxs[i]), &a, ctxs[i]->sgrid,
-                           ctxs[i]->sblock, s));
-      if (ctxs[i]->S > 1) CK(c0, c0->ops->species_step(&a, ctxs[i]->sgrid, ctxs[i]->sblock, s));
+                           ctxs[i]->sblock, st));
+      if (ctxs[i]->S > 1) CK(c0, c0->ops->species_step(&a, ctxs[i]->sgrid, ctxs[i]->sblock, st));
     }
     for (int g0 = 0; g0 < ns; g0 += BATCH_MAX) {
       const int g1 = std::min(ns, g0 + BATCH_MAX);
@@ -840,12 +946,46 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
       }
       const unsigned blocks = begin[g1] - begin[g0];
       CK(c0, c0->ops->batch_step(c0->kmode, c0->solute, tab.get(), d_work, unsigned(g0),
-                                 begin[g0], begin[g1], std::min(blocks, wave), s));
+                                 begin[g0], begin[g1], std::min(blocks, wave), st));
     }
+    return int(LB_OK);
+  };
+  auto advance = [&](int d) {
     for (int i = 0; i < n; ++i) {
-      ctxs[i]->t += 1;
+      ctxs[i]->t += d;
       ctxs[i]->cur = 1 - ctxs[i]->cur;
     }
+  };
+  // the graph of a step pair is valid for this set of lattices in this order,
+  // these parities and this work list
+  bool safe = true;
+  std::vector<uint64_t> key;
+  key.push_back(uint64_t(reinterpret_cast<uintptr_t>(d_work)));
+  for (int i = 0; i < n; ++i) {
+    safe = safe && graph_safe(ctxs[i]);
+    key.push_back(ctxs[i]->serial * 2 + uint64_t(ctxs[i]->cur));
+  }
+  int64_t k = 0;
+  const int64_t pairs = steps > 0 ? (steps - 1) / 2 : 0;
+  if (safe && pairs > 0) {
+    if (!c0->g_batch || c0->g_batch_key != key) {
+      if (c0->g_batch) cudaGraphExecDestroy(c0->g_batch);
+      c0->g_batch = nullptr;
+      c0->g_batch_key.clear();
+      if (capture_two(c0, &c0->g_batch, [&](cudaStream_t st) { return one_step(st, false); },
+                      advance) == LB_OK)
+        c0->g_batch_key = key;
+    }
+    if (c0->g_batch) {
+      for (int64_t p = 0; p < pairs; ++p) CK(c0, cudaGraphLaunch(c0->g_batch, s));
+      for (int i = 0; i < n; ++i) ctxs[i]->t += 2 * pairs;
+      k = 2 * pairs;
+    }
+  }
+  for (; k < steps; ++k) {
+    const int rc = one_step(s, k == steps - 1);
+    if (rc != LB_OK) return rc;
+    advance(+1);
   }
   return LB_OK;
 }
@@ -951,6 +1091,7 @@ int lb_autotune(lb_ctx *c, int32_t reps, int32_t *choice) {
   cudaEventDestroy(e1);
   if (rc != LB_OK || best_i < 0) return rc;
   const Cand &w = cands[best_i];
+  drop_graphs(c);  // the captured launches used the previous shape
   c->use_tma = w.kind == ROWS;
   c->pipe = w.kind == STAGED ? w.ps : lb_ctx::PipeShape{};
   if (w.kind == CELL) {

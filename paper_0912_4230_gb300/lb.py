@@ -30,7 +30,7 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_ge
            "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
            "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
            "lb_totals_noalloc", "lb_step_batch", "lb_autotune", "lb_debug_wait_timeout",
-           "lb_species_state"]
+           "lb_species_state", "lb_set_graphs", "lb_debug_graphs"]
 
 
 class LbError(RuntimeError):
@@ -78,6 +78,8 @@ def load() -> ctypes.CDLL:
     L.lb_reduce.argtypes = [vp] * 5
     L.lb_debug_neighbors.argtypes = [vp, c_int32, vp]
     L.lb_debug_wait_timeout.argtypes = [vp, c_int64]
+    L.lb_set_graphs.argtypes = [vp, c_int32]
+    L.lb_debug_graphs.argtypes = [vp]
     L.lb_species_state.argtypes = [vp, c_int32, vp, vp, vp]
     L.lb_free_surface_state.argtypes = [vp, vp, vp]
     L.lb_sync.argtypes = [vp]
@@ -176,6 +178,17 @@ def lb_debug_neighbors(ctx, lattice: int, src):
 
 def lb_debug_wait_timeout(ctx, limit_ns: int):
     _check(load().lb_debug_wait_timeout(ctx, int(limit_ns)), ctx)
+
+
+def lb_set_graphs(ctx, enable: bool):
+    _check(load().lb_set_graphs(ctx, 1 if enable else 0), ctx)
+
+
+def lb_debug_graphs(ctx) -> int:
+    rc = load().lb_debug_graphs(ctx)
+    if rc < 0:
+        _check(rc, ctx)
+    return rc
 
 
 def lb_species_state(ctx, s: int, C=None, totals=None, h=None):
@@ -327,6 +340,9 @@ class Lattice:
 
     def step(self, n=1):
         lb_step(self.ctx, n)
+
+    def set_graphs(self, enable: bool):
+        lb_set_graphs(self.ctx, enable)
 
     @property
     def t(self):
