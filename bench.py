@@ -245,7 +245,12 @@ def run_serving(args):
     from paper_0912_4230_gb300 import lb
     n_req, scale = args.requests, args.steps_scale
     stream = W.requests(n=n_req, rate=50.0, seed=5)
-    lb.use_torch_allocator()   # cached device memory: no cudaMalloc/cudaFree per request
+    # every lattice is sub-allocated from one packed arena of the admission
+    # budget inside a torch tensor: no cudaMalloc/cudaFree per request
+    budget = 120 * 10 ** 9
+    region = torch.empty(budget, dtype=torch.uint8, device="cuda")
+    arena = lb.Arena(budget, region.data_ptr())
+    arena.use()
     step_s, admit_s = torch.cuda.Stream(), torch.cuda.Stream()
     res = {}
     cap = args.max_resident or None
@@ -255,7 +260,7 @@ def run_serving(args):
         reqs = serve.make_requests(stream, storage=storage, steps_scale=scale)
         be = serve.LibraryBackend(storage, keep_fields=False, batched=batched,
                                   admit_stream=admit_s, step_stream=step_s)
-        srv = serve.Server(be, budget_bytes=120 * 10 ** 9, chunk=args.chunk, max_resident=maxres,
+        srv = serve.Server(be, budget_bytes=budget, chunk=args.chunk, max_resident=maxres,
                            fill_cells=(args.fill_cells or None) if batched else None,
                            admit_in_thread=True)
         torch.cuda.synchronize()
@@ -263,7 +268,11 @@ def run_serving(args):
             st = srv.run(reqs)
             torch.cuda.synchronize()
         st["clocks"] = clk.summary()
+        st["arena_peak_bytes"] = arena.stats()["peak"]
         res[name] = st
+    lb.Arena.use_none()
+    arena.close()
+    del region
     b = res["batched_fp32"]
     line = {
         "metric": "served-solve throughput (MLUPS) and p50/p99 latency", "value": b["mlups"],
@@ -271,7 +280,7 @@ def run_serving(args):
         "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{n_req} requests, Poisson 50/s, sides 32..160, z-aspect 1..2, "
-                               f"steps U(2000, 20000) x {scale}, 120 GB admission budget, "
+                               f"steps U(2000, 20000) x {scale}, 120 GB admission budget (one packed arena), "
                                f"chunk {args.chunk} steps, at most "
                                f"{args.max_resident or 'budget-many'} resident, oldest stepped "
                                f"together up to {args.fill_cells or 'all'} cells"},

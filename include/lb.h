@@ -306,8 +306,10 @@ int lb_set_allocator(void *(*alloc)(size_t bytes, void *user),
  * that cannot allocate device memory where they need the totals, e.g. code
  * whose device memory is all reserved up front by a framework's pool, or a
  * loop that must not pay the device-wide synchronisation of cudaMalloc and
- * cudaFree). Computes the same FP64 mass and solute totals as lb_reduce, but
- * of caller-owned device arrays and with no device allocation at all:
+ * cudaFree). Computes the FP64 mass and solute totals of lb_reduce (every
+ * stored value widened to FP64 here; lb_reduce sums a cell's 19 values in
+ * FP32 first, which differs by at most 18 * 2^-24 * sum_q |f_q - w_q| per
+ * cell), but of caller-owned device arrays and with no device allocation:
  *   f        19*n_cells floats in device memory, the FP32 storage form
  *            f_q - w_q, direction-major (f[q*n_cells + n]);
  *   h        19*n_cells floats h_q in device memory, or NULL (solute 0);
@@ -324,6 +326,33 @@ int lb_set_allocator(void *(*alloc)(size_t bytes, void *user),
  * report its messages). */
 int lb_totals_noalloc(const float *f, const float *h, const uint8_t *solid, int64_t n_cells,
                       double *out, void *stream);
+
+/* Packed lattice arena (no counterpart in the paper): one region of device
+ * memory from which the lattices of a serving loop are sub-allocated, so
+ * that admission by an HBM budget is admission into one fixed region.
+ * First-fit over an address-ordered free list, blocks aligned to 256 bytes,
+ * neighbouring free blocks merged on release; thread-safe.
+ *   lb_arena_create  base: a region of `bytes` device memory owned by the
+ *                    caller (for example one framework tensor), or NULL: the
+ *                    arena allocates it with cudaMalloc and frees it in
+ *                    lb_arena_destroy. *out is NULL on failure.
+ *   lb_arena_use     route the device allocations of contexts created
+ *                    afterwards into the arena (as lb_set_allocator does);
+ *                    NULL restores cudaMalloc. An arena must outlive the
+ *                    contexts allocated from it.
+ *   lb_arena_alloc / lb_arena_free  one block (NULL when nothing fits).
+ *   lb_arena_stats   bytes in use, the largest free block, the peak use and
+ *                    the number of live blocks (any pointer may be NULL).
+ * The bookkeeping never touches the region, so a host region serves for
+ * tests of the allocator. */
+typedef struct lb_arena lb_arena;
+int lb_arena_create(void *base, size_t bytes, lb_arena **out);
+void lb_arena_destroy(lb_arena *arena);
+int lb_arena_use(lb_arena *arena);
+void *lb_arena_alloc(lb_arena *arena, size_t bytes);
+void lb_arena_free(lb_arena *arena, void *ptr);
+int lb_arena_stats(const lb_arena *arena, size_t *used, size_t *largest_free, size_t *peak,
+                   size_t *blocks);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbgb.so")
 
 SOURCES = ["lb_abi.cu", "lb_setup.cu", "lb_inst_f32.cu", "lb_inst_f64.cu", "lb_inst_f16.cu",
-           "lb_inst_bf16.cu", "lb_free_surface.cu", "lb_static.cu"]
+           "lb_inst_bf16.cu", "lb_free_surface.cu", "lb_static.cu", "lb_arena.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -1121,9 +1121,9 @@ int lb_reduce(lb_ctx *c, double *mass, double *solute, double *flux_in, double *
   if (c->fs)
     CK(c, fs_totals(c->N, c->link, c->mass[c->cur], c->partials, c->ops->fp64, c->stream));
   else
-    CK(c, c->ops->totals(f_view(c), c->solute ? h_view(c, 0) : PopView{}, 
+    CK(c, c->ops->totals(f_view(c), c->solute ? h_view(c, 0) : PopView{},
                          c->has_solid ? c->link : nullptr, c->N, c->partials, c->nblk, c->stream));
-  CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
+  CK(c, finish_sum(c->partials, c->fs ? c->nblk : totals_blocks(c->nblk), 2, out, c->stream));
   CK(c, finish_sum(c->flux_slots, c->nwarps, 2, out + 2, c->stream));
   CK(c, cudaMemcpyAsync(tot, out, sizeof tot, cudaMemcpyDeviceToHost, c->stream));
   DevState st;
@@ -1151,7 +1151,7 @@ int lb_species_state(lb_ctx *c, int32_t sp, float *C, double *totals, double *h)
     if (!out) return fail(c, LB_ENOMEM, "staging");
     CK(c, c->ops->totals(f_view(c), hv, c->has_solid ? c->link : nullptr, c->N, c->partials,
                          c->nblk, c->stream));
-    CK(c, finish_sum(c->partials, c->nblk, 2, out, c->stream));
+    CK(c, finish_sum(c->partials, totals_blocks(c->nblk), 2, out, c->stream));
     CK(c, finish_sum(c->flux_slots + size_t(sp) * c->nwarps * 2, c->nwarps, 2, out + 2,
                      c->stream));
     double tot[4];

@@ -105,7 +105,8 @@ struct Instance {
   }
   static cudaError_t totals(PopView f, PopView h, const uint32_t *link, unsigned N,
                             double *partials, unsigned nblk, cudaStream_t s) {
-    totals_kernel<S><<<nblk, BLOCK, 0, s>>>(own_refs(f), own_refs(h), link, N, partials);
+    totals_kernel<S><<<totals_blocks(nblk), BLOCK, 0, s>>>(own_refs(f), own_refs(h), link, N,
+                                                          partials);
     return cudaGetLastError();
   }
   static cudaError_t fs_step(const void *args, unsigned grid, unsigned tile_blocks,

@@ -1111,50 +1111,72 @@ __global__ void from_f64_kernel(const double *src, const PopView v, unsigned N, 
       lattice == 0 ? S::from_f(src[i], q, r) : S::from_h(src[i], q, r);
 }
 
-// Per-block FP64 sums of the fluid mass and the solute over non-solid cells.
+// Per-block FP64 sums of the fluid mass and the solute over non-solid cells,
+// each block taking cells blockIdx.x*BLOCK + tid + k*gridDim.x*BLOCK. A
+// cell's 19 stored values are summed in the collision type as deviations
+// (FP32 / FP64 storage: f_q - w_q, h_q; 16-bit: the remainders times w_q),
+// then mass = 1 + reference + sum, solute = reference + sum in FP64; the
+// cell sums, the block's shuffle tree and the finish are FP64.
 template <class S>
 __global__ void __launch_bounds__(BLOCK) totals_kernel(const PopView f, const PopView h,
                                                        const uint32_t *link, unsigned N,
                                                        double *partials) {
-  __shared__ double sh[BLOCK][2];
-  const unsigned n = blockIdx.x * BLOCK + threadIdx.x;
+  using Real = typename S::Real;
+  __shared__ double sh[BLOCK / 32][2];
   double m = 0.0, s = 0.0;
-  if (n < N && !(link && (link[n] >> 31))) {
-    const double r = pop_ref(f, n);
-    for (int q = 0; q < Q; ++q) m += S::to_f(pop_at<S>(f, size_t(q) * N + n), q, r);
+  for (unsigned n = blockIdx.x * BLOCK + threadIdx.x; n < N; n += gridDim.x * BLOCK) {
+    if (link && (link[n] >> 31)) continue;
+    Real a = Real(0);
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      a += S::template cv_f<q>(pop_at<S>(f, size_t(q) * N + n));
+    });
+    m += 1.0 + pop_ref(f, n) + double(a);
     if (h.p) {
-      const double r2 = pop_ref(h, n);
-      for (int q = 0; q < Q; ++q) s += S::to_h(pop_at<S>(h, size_t(q) * N + n), q, r2);
+      Real b = Real(0);
+      Unroll<0, Q>::run([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        b += S::template cv_h<q>(pop_at<S>(h, size_t(q) * N + n));
+      });
+      s += pop_ref(h, n) + double(b);
     }
   }
-  sh[threadIdx.x][0] = m;
-  sh[threadIdx.x][1] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_down_sync(0xffffffffu, m, o);
+    s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  const unsigned w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31u) == 0) {
+    sh[w][0] = m;
+    sh[w][1] = s;
+  }
   __syncthreads();
-  for (int k = BLOCK / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) {
-      sh[threadIdx.x][0] += sh[threadIdx.x + k][0];
-      sh[threadIdx.x][1] += sh[threadIdx.x + k][1];
-    }
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    partials[2 * size_t(blockIdx.x)] = sh[0][0];
-    partials[2 * size_t(blockIdx.x) + 1] = sh[0][1];
+    double tm = 0.0, ts = 0.0;
+    for (unsigned k = 0; k < BLOCK / 32; ++k) {
+      tm += sh[k][0];
+      ts += sh[k][1];
+    }
+    partials[2 * size_t(blockIdx.x)] = tm;
+    partials[2 * size_t(blockIdx.x) + 1] = ts;
   }
 }
 
-// Fixed-order sum of nblk x K partials by one block.
+// Fixed-order sum of nblk x K partials by one block of FINISH_THREADS
+// threads (thread t sums partials t, t + FINISH_THREADS, ..., then a fixed
+// tree), so the result does not depend on timing.
+constexpr int FINISH_THREADS = 1024;
 template <int K>
-__global__ void __launch_bounds__(BLOCK) finish_sum_kernel(const double *partials, unsigned nblk,
-                                                           double *out) {
-  __shared__ double sh[BLOCK][K];
+__global__ void __launch_bounds__(FINISH_THREADS) finish_sum_kernel(const double *partials,
+                                                                    unsigned nblk, double *out) {
+  __shared__ double sh[FINISH_THREADS][K];
   double acc[K];
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  for (unsigned b = threadIdx.x; b < nblk; b += BLOCK)
+  for (unsigned b = threadIdx.x; b < nblk; b += FINISH_THREADS)
     for (int k = 0; k < K; ++k) acc[k] += partials[size_t(b) * K + k];
   for (int k = 0; k < K; ++k) sh[threadIdx.x][k] = acc[k];
   __syncthreads();
-  for (int s = BLOCK / 2; s > 0; s >>= 1) {
+  for (int s = FINISH_THREADS / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s)
       for (int k = 0; k < K; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
     __syncthreads();

@@ -20,6 +20,11 @@ struct PopView {
   int ref_pair;
 };
 
+// The totals kernel runs at most this many blocks (grid-stride over the
+// cells), so the fixed-order finish sums few partials.
+constexpr unsigned TOTALS_BLOCKS = 1024;
+inline unsigned totals_blocks(unsigned nblk) { return nblk < TOTALS_BLOCKS ? nblk : TOTALS_BLOCKS; }
+
 struct StorageOps {
   int storage;       // LB_STORE_*
   size_t elt_bytes;  // bytes per stored population
@@ -38,8 +43,9 @@ struct StorageOps {
                       unsigned nblk, cudaStream_t s);
   cudaError_t (*rhohat)(const void *args, void *rhohat, unsigned nblk, cudaStream_t s);
   // absolute FP64 populations of a lattice (0 f, 1 h) from / into storage;
-  // from_f64 also sets the references (FP16/BF16). totals: per-block FP64
-  // sums of the fluid mass and (h.p not NULL) the solute
+  // from_f64 also sets the references (FP16/BF16). totals: FP64 sums of the
+  // fluid mass and (h.p not NULL) the solute over totals_blocks(nblk) blocks,
+  // one partial pair per block
   cudaError_t (*to_f64)(PopView src, double *dst, unsigned N, int lattice, cudaStream_t s);
   cudaError_t (*from_f64)(const double *src, PopView dst, unsigned N, int lattice,
                           cudaStream_t s);

@@ -149,9 +149,9 @@ cudaError_t setup_fields(const SetupArgs &a, bool fp64, cudaStream_t s) {
 
 cudaError_t finish_sum(const double *partials, unsigned nblk, int k, double *out, cudaStream_t s) {
   if (k == 2)
-    finish_sum_kernel<2><<<1, BLOCK, 0, s>>>(partials, nblk, out);
+    finish_sum_kernel<2><<<1, FINISH_THREADS, 0, s>>>(partials, nblk, out);
   else
-    finish_sum_kernel<4><<<1, BLOCK, 0, s>>>(partials, nblk, out);
+    finish_sum_kernel<4><<<1, FINISH_THREADS, 0, s>>>(partials, nblk, out);
   return cudaGetLastError();
 }
 

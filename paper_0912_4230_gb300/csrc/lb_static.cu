@@ -63,8 +63,8 @@ int scratch_address(double **out) {
 }
 
 // Per-block FP64 sums of the fluid mass (sum of f over non-solid cells, from
-// the f_q - w_q storage) and the solute (sum of h); same arithmetic as the
-// per-block kernel behind lb_reduce, with a byte mask for solid cells.
+// the f_q - w_q storage, every value widened to FP64 before it is added) and
+// the solute (sum of h), with a byte mask for solid cells.
 __global__ void __launch_bounds__(BLOCK) noalloc_totals_kernel(const float *f, const float *h,
                                                                const uint8_t *solid, unsigned N,
                                                                double *partials) {
@@ -111,7 +111,7 @@ extern "C" int lb_totals_noalloc(const float *f, const float *h, const uint8_t *
   noalloc_totals_kernel<<<nblk, BLOCK, 0, s>>>(f, h, solid, N, scratch);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
-    finish_sum_kernel<2><<<1, BLOCK, 0, s>>>(scratch, nblk, scratch + 2 * kMaxBlocks);
+    finish_sum_kernel<2><<<1, FINISH_THREADS, 0, s>>>(scratch, nblk, scratch + 2 * kMaxBlocks);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)

@@ -30,7 +30,8 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_ge
            "lb_step", "lb_fields", "lb_reduce", "lb_debug_neighbors", "lb_free_surface_state",
            "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
            "lb_totals_noalloc", "lb_step_batch", "lb_autotune", "lb_debug_wait_timeout",
-           "lb_species_state", "lb_set_graphs", "lb_debug_graphs"]
+           "lb_species_state", "lb_set_graphs", "lb_debug_graphs", "lb_arena_create",
+           "lb_arena_destroy", "lb_arena_use", "lb_arena_alloc", "lb_arena_free", "lb_arena_stats"]
 
 
 class LbError(RuntimeError):
@@ -96,6 +97,15 @@ def load() -> ctypes.CDLL:
     L.lb_totals_noalloc.argtypes = [vp, vp, vp, c_int64, vp, vp]
     L.lb_step_batch.argtypes = [vp, c_int32, c_int64]
     L.lb_autotune.argtypes = [vp, c_int32, vp]
+    L.lb_arena_create.argtypes = [vp, c_size_t, POINTER(vp)]
+    L.lb_arena_destroy.argtypes = [vp]
+    L.lb_arena_destroy.restype = None
+    L.lb_arena_use.argtypes = [vp]
+    L.lb_arena_alloc.argtypes = [vp, c_size_t]
+    L.lb_arena_alloc.restype = vp
+    L.lb_arena_free.argtypes = [vp, vp]
+    L.lb_arena_free.restype = None
+    L.lb_arena_stats.argtypes = [vp] * 5
     _lib = L
     return L
 
@@ -256,6 +266,44 @@ def use_torch_allocator():
     import torch
     lb_set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n),
                      lambda p: torch.cuda.caching_allocator_delete(p))
+
+
+class Arena:
+    """Packed lattice arena (lb_arena_*): one region of device memory
+    (``base``, ``nbytes``; base None: the library allocates it) from which
+    the lattices created while it is in use are sub-allocated."""
+
+    def __init__(self, nbytes: int, base=None):
+        out = c_void_p()
+        rc = load().lb_arena_create(None if base is None else c_void_p(int(base)),
+                                    c_size_t(int(nbytes)), ctypes.byref(out))
+        if rc != LB_OK:
+            raise LbError(rc, "lb_arena_create failed")
+        self.ptr = out
+        self.nbytes = int(nbytes)
+
+    def use(self):
+        _check(load().lb_arena_use(self.ptr))
+
+    @staticmethod
+    def use_none():
+        _check(load().lb_arena_use(None))
+
+    def alloc(self, nbytes: int):
+        return load().lb_arena_alloc(self.ptr, c_size_t(int(nbytes)))
+
+    def free(self, ptr):
+        load().lb_arena_free(self.ptr, c_void_p(ptr))
+
+    def stats(self) -> dict:
+        v = [c_size_t() for _ in range(4)]
+        _check(load().lb_arena_stats(self.ptr, *[ctypes.byref(x) for x in v]))
+        return dict(used=v[0].value, largest_free=v[1].value, peak=v[2].value, blocks=v[3].value)
+
+    def close(self):
+        if self.ptr:
+            load().lb_arena_destroy(self.ptr)
+            self.ptr = None
 
 
 # ---------------------------------------------------------------- convenience

@@ -88,7 +88,17 @@ class LibraryBackend:
                             bool(prob.params.get("solute")), kr)
 
     def admit(self, prob):
-        """Create and initialise a lattice (may run on a background thread)."""
+        """Create and initialise a lattice (may run on a background thread).
+        Raises MemoryError when its device memory does not fit (for example
+        in a packed arena that is full or fragmented)."""
+        try:
+            return self._admit(prob)
+        except self.lb.LbError as e:
+            if e.code == self.lb.LB_ENOMEM:
+                raise MemoryError(str(e)) from None
+            raise
+
+    def _admit(self, prob):
         if self.admit_stream is None:
             return self.lb.Lattice(prob, storage=self.storage, kernel="cell", stream=self.stream)
         import torch
@@ -159,6 +169,8 @@ class Server:
         active: List[Request] = []
         finished: List[Request] = []
         self._used = 0
+        self._released = 0       # requests finished so far (wakes a waiting admission)
+        self._admit_error = None
         t0 = self.clock()
         lups = 0
         lock = threading.Condition()
@@ -177,7 +189,22 @@ class Server:
                                 len(active) + len(ready) >= self.max_resident)):
                             lock.wait(0.01)
                         self._used += r.bytes
-                    r.handle = self.backend.admit(r.problem)
+                    while True:
+                        try:
+                            r.handle = self.backend.admit(r.problem)
+                            break
+                        except MemoryError as e:
+                            # device memory is short of the estimate (a full or
+                            # fragmented arena): wait for a request to finish
+                            with lock:
+                                if not active and not ready:
+                                    self._used -= r.bytes
+                                    self._admit_error = e
+                                    lock.notify_all()
+                                    return
+                                seen = self._released
+                                while self._released == seen:
+                                    lock.wait(0.01)
                     r.admitted = self.clock() - t0
                     with lock:
                         pending.pop(0)
@@ -189,6 +216,8 @@ class Server:
             now = self.clock() - t0
             if admitter is not None:
                 with lock:
+                    if self._admit_error is not None:
+                        raise self._admit_error
                     for r in ready:
                         if hasattr(self.backend, "activate"):
                             self.backend.activate(r.handle)
@@ -206,8 +235,14 @@ class Server:
                 while (pending and pending[0].arrival <= now
                        and self._used + pending[0].bytes <= self.budget
                        and (self.max_resident is None or len(active) < self.max_resident)):
+                    try:
+                        handle = self.backend.admit(pending[0].problem)
+                    except MemoryError:
+                        if not active:
+                            raise      # nothing resident will free memory
+                        break          # retry after the next chunk
                     r = pending.pop(0)
-                    r.handle = self.backend.admit(r.problem)
+                    r.handle = handle
                     if hasattr(self.backend, "activate"):
                         self.backend.activate(r.handle)
                     r.admitted = self.clock() - t0
@@ -238,6 +273,7 @@ class Server:
                     r.done = self.clock() - t0
                     with lock:
                         self._used -= r.bytes
+                        self._released += 1
                         lock.notify_all()
                     finished.append(r)
                 else:

@@ -90,3 +90,30 @@ def test_serving_results_same_alone_and_in_the_mix():
         for k in ("rho", "u", "C", "nu"):
             assert np.array_equal(a[k], b[k]), (r.id, k)
         assert np.array_equal(a["totals"], b["totals"])
+
+
+def test_serving_in_a_packed_arena():
+    """All lattices of the mix sub-allocated from one arena inside a torch
+    tensor: the results equal those of lattices from cudaMalloc, the arena is
+    empty afterwards, and its peak stays inside the budget."""
+    torch = pytest.importorskip("torch")
+    stream = W.requests(n=6, rate=200.0, seed=11, sides=(32, 48), steps_range=(60, 140))
+    plain = serve.make_requests(stream)
+    serve.Server(serve.LibraryBackend("fp32"), budget_bytes=2 * 10 ** 9, chunk=32).run(plain)
+    budget = 2 * 10 ** 9
+    region = torch.empty(budget, dtype=torch.uint8, device="cuda")
+    arena = lb.Arena(budget, region.data_ptr())
+    arena.use()
+    try:
+        reqs = serve.make_requests(stream)
+        st = serve.Server(serve.LibraryBackend("fp32"), budget_bytes=budget, chunk=32).run(reqs)
+    finally:
+        lb.Arena.use_none()
+    assert st["requests"] == 6
+    stats = arena.stats()
+    assert stats["used"] == 0 and stats["blocks"] == 0 and 0 < stats["peak"] <= budget
+    for a, b in zip(plain, reqs):
+        for k in ("rho", "u", "C", "nu"):
+            assert np.array_equal(a.result[k], b.result[k]), (a.id, k)
+        assert np.array_equal(a.result["totals"], b.result["totals"])
+    arena.close()

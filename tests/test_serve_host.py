@@ -158,3 +158,68 @@ def test_admission_thread_overlaps_and_respects_budget():
     assert st["requests"] == 4
     assert be.max_resident <= 2 and be.resident == 0
     assert all(r.done >= r.admitted >= r.arrival for r in reqs)
+
+
+class ArenaBackend(FakeBackend):
+    """Device memory from a fixed arena (the library's first-fit arena on a
+    host region): admit raises MemoryError when the lattice does not fit, even
+    if the estimate said it would."""
+
+    def __init__(self, clock, arena, scale=1.5):
+        super().__init__(clock)
+        self.arena, self.scale = arena, scale
+        self.blocks = {}
+
+    def admit(self, prob):
+        p = self.arena.alloc(int(self.bytes(prob) * self.scale))   # estimate too low
+        if p is None:
+            raise MemoryError("arena full")
+        h, N = super().admit(prob)
+        self.blocks[h] = p
+        return (h, N)
+
+    def finish(self, handle):
+        self.arena.free(self.blocks.pop(handle[0]))
+        return super().finish(handle)
+
+
+@pytest.mark.parametrize("threaded", [False, True])
+def test_admission_waits_when_the_arena_is_short(threaded):
+    """The estimate admits three requests under the budget but the arena
+    holds two: the third is admitted after one finishes, every request
+    completes, and the arena is empty at the end."""
+    import time
+    from paper_0912_4230_gb300 import lb
+    buf = np.zeros((1 << 20) + 256, np.uint8)
+    base = (buf.ctypes.data + 255) // 256 * 256
+    side = 10                                  # 1000 cells: estimate 100 000 bytes
+    arena = lb.Arena(2 * 150_000 + 4096, base)
+    if threaded:
+        clock, sleep = time.perf_counter, time.sleep
+        be = ArenaBackend(None, arena)
+        be.step = lambda handles, n: None
+    else:
+        clk = FakeClock()
+        clock, sleep = clk, clk.sleep
+        be = ArenaBackend(clk, arena)
+    reqs = _reqs([(0.0, side, 300), (0.0, side, 300), (0.0, side, 300)])
+    srv = serve.Server(be, budget_bytes=10 ** 7, chunk=100, clock=clock, sleep=sleep,
+                       admit_in_thread=threaded)
+    st = srv.run(reqs)
+    assert st["requests"] == 3
+    assert reqs[2].admitted >= min(reqs[0].done, reqs[1].done)
+    assert arena.stats()["used"] == 0
+    arena.close()
+
+
+def test_admission_fails_when_nothing_can_free_memory():
+    from paper_0912_4230_gb300 import lb
+    buf = np.zeros((1 << 16) + 256, np.uint8)
+    base = (buf.ctypes.data + 255) // 256 * 256
+    arena = lb.Arena(1 << 16, base)
+    clk = FakeClock()
+    be = ArenaBackend(clk, arena)
+    srv = serve.Server(be, budget_bytes=10 ** 7, chunk=100, clock=clk, sleep=clk.sleep)
+    with pytest.raises(MemoryError):
+        srv.run(_reqs([(0.0, 10, 100)]))       # 150 000 bytes > the 64 KiB arena
+    arena.close()
