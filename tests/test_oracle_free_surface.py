@@ -88,3 +88,77 @@ def test_laplace_law():
     pred = A @ np.array([slope, icpt])
     r2 = 1 - ((dps - pred) ** 2).sum() / ((dps - dps.mean()) ** 2).sum()
     assert r2 > 0.99
+
+
+def _neighbours(p):
+    """D3Q19 neighbours of every cell (N x 18 indices, -1 across a wall face
+    or onto a solid cell), from the box and its face kinds alone."""
+    vel = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    vel += [(a, b, 0) for a in (1, -1) for b in (1, -1)]
+    vel += [(a, 0, b) for a in (1, -1) for b in (1, -1)]
+    vel += [(0, a, b) for a in (1, -1) for b in (1, -1)]
+    n = np.arange(p.N)
+    x, y, z = n % p.nx, (n // p.nx) % p.ny, n // (p.nx * p.ny)
+    out = np.full((p.N, 18), -1, np.int64)
+    dims = (p.nx, p.ny, p.nz)
+    for k, c in enumerate(vel):
+        ok = np.ones(p.N, bool)
+        coords = []
+        for axis, (v, d) in enumerate(zip((x, y, z), dims)):
+            w = v + c[axis]
+            if p.bc[axis][0] == W.PERIODIC:
+                w = w % d
+            else:
+                ok &= (w >= 0) & (w < d)
+                w = np.clip(w, 0, d - 1)
+            coords.append(w)
+        m = coords[0] + p.nx * (coords[1] + p.ny * coords[2])
+        ok &= p.solid[m] == 0
+        out[:, k] = np.where(ok, m, -1)
+    return out
+
+
+def _check_layers(p, o, nb, prev):
+    """The interface layer separates liquid from gas (no liquid cell next to
+    an empty one) and empty cells hold no mass; a cell liquid before and
+    after the step keeps m - rho (its mass exchange equals its density
+    change: its links reach no empty cell, and bounce-back links cancel)."""
+    t, m = o.free_surface_state()
+    rho = o.fields()[0]
+    live = p.solid == 0
+    liquid = live & (t == W.LIQUID)
+    nbt = np.where(nb >= 0, t[np.maximum(nb, 0)], W.LIQUID)
+    assert not np.any(liquid[:, None] & (nbt == W.EMPTY)), "liquid cell next to an empty cell"
+    assert np.all(m[live & (t == W.EMPTY)] == 0.0)
+    d = m - rho
+    if prev is not None:
+        t0, d0 = prev
+        both = liquid & (t0 == W.LIQUID)
+        assert np.abs(d[both] - d0[both]).max(initial=0.0) < 1e-12
+    return (t, d), int(np.sum(live & (t == W.INTERFACE)))
+
+
+def test_conversions_keep_the_interface_layer_closed():
+    """Reading R18 (conversion of filled and emptied cells): while the drop
+    falls, fills and empties, every step leaves an interface layer between
+    liquid and gas, no mass in the gas, and m - rho unchanged in cells that
+    stay liquid. A filled cell whose empty neighbours were not made
+    interface, or an emptied cell whose liquid neighbours stayed liquid,
+    breaks the first property; excess mass left in an emptied cell the
+    second; an exchange term dropped between liquid and interface cells the
+    third."""
+    p = W.drop(nx=24, ny=24, nz=28, R=5.0, gap=6.0, steps=400, seed=3)
+    o = O.Oracle(p)
+    nb = _neighbours(p)
+    o.step(1)   # the exported density of lb_init is rho0, not that of the perturbed populations
+    prev, n0 = _check_layers(p, o, nb, None)
+    n_if = [n0]
+    changed = 0
+    for _ in range(200):
+        o.step(1)
+        t_prev = prev[0]
+        prev, k = _check_layers(p, o, nb, prev)
+        n_if.append(k)
+        changed += int(np.sum(prev[0] != t_prev))
+    assert changed > 50            # cells did fill and empty along the way
+    assert min(n_if) > 0
