@@ -162,3 +162,23 @@ def test_conversions_keep_the_interface_layer_closed():
         changed += int(np.sum(prev[0] != t_prev))
     assert changed > 50            # cells did fill and empty along the way
     assert min(n_if) > 0
+
+
+def test_contact_angle_sweep_is_reproduced_and_ordered():
+    """The stored sweep of the wetting reading (R16, written by
+    tests/golden/contact_angle.py from the oracle): the angle falls as the
+    wall looks more like liquid, a wall with wall_rho = 1 wets at about 90
+    degrees, and the drop workload's 0.6 case relaxed from a half disc is
+    reproduced."""
+    import importlib.util
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    sweep = json.load(open(os.path.join(here, "contact_angle.json")))
+    for angles in sweep["angles_deg"].values():
+        assert all(a >= b for a, b in zip(angles, angles[1:]))
+    k = sweep["wall_rho"].index(1.0)
+    assert all(abs(v[k] - 90.0) < 10.0 for v in sweep["angles_deg"].values())
+    spec = importlib.util.spec_from_file_location("contact_angle", os.path.join(here, "contact_angle.py"))
+    ca = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(ca)
+    i = sweep["wall_rho"].index(0.6)
+    assert ca.run(0.6, -7.0) == pytest.approx(sweep["angles_deg"]["from_90deg"][i], abs=0.05)
