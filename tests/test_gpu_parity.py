@@ -415,3 +415,23 @@ def test_reduced_precision_storage_full_protocol():
               f"drift {drift_crop:.1e}")
         assert du_full <= bound and du_crop <= bound
         assert drift <= 1e-6 and drift_crop <= 1e-6
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 2e-7), ("fp32", 1e-5)])
+@pytest.mark.parametrize("tau", [0.8, 0.5 + np.sqrt(3.0 / 16.0)])
+def test_poiseuille_exact_discrete_solution_on_the_gpu(storage, tol, tau):
+    """The GPU path on plane Poiseuille flow against the exact steady BGK
+    solution with halfway bounce-back walls (the oracle's pin),
+    u(y) = G/(2 nu) [y (L - y) + (16 (tau - 1/2)^2 - 3)/12]; FP64 storage to
+    the float32 rounding of the exported field, FP32 to the 1e-5 bound."""
+    nz, G = 16, 1e-6
+    p = W.brinkman(nz=nz, K=1.0, eps=1.0, tau=tau, G=G, nxy=4).replace(K6=None, storage=storage)
+    g = lb.Lattice(p, storage=storage)
+    nu = (tau - 0.5) / 3.0
+    g.step(int(np.ceil(40.0 * nz * nz / (np.pi ** 2 * nu))))
+    _, u, _, _ = g.fields()
+    u = u.reshape(nz, 4, 4, 3)
+    y = np.arange(nz) + 0.5
+    exact = G / (2 * nu) * (y * (nz - y) + (16 * (tau - 0.5) ** 2 - 3) / 12)
+    assert np.abs(u[..., 0] - exact[:, None, None]).max() <= tol * np.abs(exact).max()
+    g.close()

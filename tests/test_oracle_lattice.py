@@ -164,6 +164,28 @@ def _brinkman_error(nz, K, steps, tau=0.8, solute_C=None):
     return np.linalg.norm(u[:, 0] - exact) / np.linalg.norm(exact)
 
 
+@pytest.mark.parametrize("tau", [0.55, 0.8, 0.5 + np.sqrt(3.0 / 16.0), 1.2, 2.0])
+def test_poiseuille_exact_discrete_solution(tau):
+    """Plane Poiseuille flow (eps = 1, no medium, body force G between two
+    halfway bounce-back walls a distance L apart): the steady BGK solution
+    on the lattice is the parabola plus a uniform slip fixed by tau alone,
+    u(y) = G/(2 nu) [y (L - y) + (16 (tau - 1/2)^2 - 3)/12]
+    (He, Zou, Luo and Dembo, J. Stat. Phys. 87 (1997): the halfway wall sits
+    exactly at the link midpoint only for (tau - 1/2)^2 = 3/16). Reached to
+    rounding for every tau; a misplaced wall, a dropped half force or a
+    wrong viscosity would leave an error of order one in the slip term."""
+    nz, G = 16, 1e-6
+    p = W.brinkman(nz=nz, K=1.0, eps=1.0, tau=tau, G=G).replace(K6=None)
+    o = O.Oracle(p)
+    nu = (tau - 0.5) / 3.0
+    o.step(int(np.ceil(40.0 * nz * nz / (np.pi ** 2 * nu))))   # 40 e-folds of the slowest mode
+    _, u, _, _ = o.fields()
+    y = np.arange(nz) + 0.5
+    exact = G / (2 * nu) * (y * (nz - y) + (16 * (tau - 0.5) ** 2 - 3) / 12)
+    assert np.abs(u[:, 0] - exact).max() <= 1e-9 * np.abs(exact).max()
+    assert np.abs(u[:, 1:]).max() <= 1e-9 * np.abs(exact).max()
+
+
 def test_brinkman_closed_form_and_convergence():
     """Eq. eq:darcy with the boundary layer resolved (1/r = 5.2 cells at
     L = 64): relative L2 error below 1e-2, second order under refinement at
