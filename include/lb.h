@@ -202,8 +202,9 @@ int lb_step(lb_ctx *ctx, int64_t n);
 
 /* CUDA graphs for lb_step and lb_step_batch (no counterpart in the paper;
  * default on). While a lattice's launches repeat exactly from one step pair
- * to the next (no free surface, no time-dependent viscosity law, check_every
- * 0 or 1), the calls capture two steps, one of each buffer parity, into a
+ * to the next (no time-dependent viscosity law, check_every 0 or 1; the free
+ * surface keeps its tile lists and stamps on the device, so it qualifies),
+ * the calls capture two steps, one of each buffer parity, into a
  * graph once and replay it for all but the last step of the call, which is
  * launched directly and exports the fields; the steps compute exactly what
  * direct launches compute. A batch graph is kept by the batch's first

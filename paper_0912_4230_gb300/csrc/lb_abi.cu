@@ -89,6 +89,7 @@ struct lb_ctx {
   uint32_t *tiles[2] = {nullptr, nullptr};
   unsigned *n_tiles = nullptr;
   unsigned *stamp = nullptr;
+  unsigned *stamp_ctr = nullptr;  // steps taken since lb_init (device)
   unsigned ntx = 0, nty = 0, ntz = 0, fs_grid = 0;
   // table of lb_step_batch calls led by this context
   void *batch_tab = nullptr;
@@ -302,7 +303,7 @@ FsArgs<Real> fs_args(lb_ctx *c, const StepArgs<Real> &a, long long t) {
   fa.next_tiles = c->tiles[(t + 1) & 1];
   fa.next_n_tiles = c->n_tiles + ((t + 1) & 1);
   fa.stamp = c->stamp;
-  fa.stamp_next = unsigned(t + 1);
+  fa.stamp_ctr = c->stamp_ctr;
   fa.ntx = c->ntx;
   fa.nty = c->nty;
   fa.ntz = c->ntz;
@@ -356,11 +357,11 @@ int enqueue_step(lb_ctx *c, cudaStream_t s, bool last) {
 }
 
 // A lattice's steps can be replayed from a graph when every step of a pair
-// launches the same work with the same arguments: no free surface (its tile
-// lists change), no time-dependent viscosity (t is an argument), and checks
-// on every step or none.
+// launches the same work with the same arguments: no time-dependent viscosity
+// (t is an argument) and checks on every step or none. (The free surface's
+// tile lists and stamps live on the device, its passes' grids are fixed.)
 bool graph_safe(const lb_ctx *c) {
-  return c->graphs && !c->fs && c->prm.visc_law != 2 && c->prm.check_every <= 1;
+  return c->graphs && c->prm.visc_law != 2 && c->prm.check_every <= 1;
 }
 
 // Capture two steps, issued by step(stream) with the lattices' t and parity
@@ -634,8 +635,9 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     c->tiles[1] = static_cast<uint32_t *>(dev_alloc(c, ntiles * sizeof(uint32_t)));
     c->n_tiles = static_cast<unsigned *>(dev_alloc(c, 2 * sizeof(unsigned)));
     c->stamp = static_cast<unsigned *>(dev_alloc(c, ntiles * sizeof(unsigned)));
+    c->stamp_ctr = static_cast<unsigned *>(dev_alloc(c, sizeof(unsigned)));
     if (!c->lam || !c->share || !c->mom || !c->flag_a || !c->flag_b || !c->any || !c->tiles[0] ||
-        !c->tiles[1] || !c->n_tiles || !c->stamp)
+        !c->tiles[1] || !c->n_tiles || !c->stamp || !c->stamp_ctr)
       return bail(fail(c, LB_ENOMEM, "free surface"));
     // persistent grid of the tile passes: enough resident blocks to cover
     // the list of a typical step in one round
@@ -797,6 +799,7 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
     CK(c, cudaMemsetAsync(c->flag_a, 0, N, c->stream));
     CK(c, cudaMemsetAsync(c->flag_b, 0, N, c->stream));
     CK(c, cudaMemsetAsync(c->stamp, 0, size_t(fs_tile_count(c)) * sizeof(unsigned), c->stream));
+    CK(c, cudaMemsetAsync(c->stamp_ctr, 0, sizeof(unsigned), c->stream));
     CK(c, cudaMemsetAsync(c->n_tiles, 0, 2 * sizeof(unsigned), c->stream));
   } else if (c->prm.A != 0.0) {
     CK(c, rhohat_init(c->N, c->link, d_rho, nullptr, c->prm.wall_rho, c->rhohat, c->ops->fp64,

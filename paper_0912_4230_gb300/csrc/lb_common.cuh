@@ -299,7 +299,8 @@ struct FsArgs {
   uint32_t *next_tiles;
   unsigned *next_n_tiles;
   unsigned *stamp;       // per tile: the step whose list holds it
-  unsigned stamp_next;   // the next step's stamp
+  unsigned *stamp_ctr;   // steps taken; the next step's stamp is *stamp_ctr + 1 (the
+                         // first pass of a step advances it, so a step is launch-invariant)
   unsigned ntx, nty, ntz;
 };
 constexpr unsigned FS_TX = 32, FS_TY = 4, FS_TZ = 2;  // one BLOCK of cells

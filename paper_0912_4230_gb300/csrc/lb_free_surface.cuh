@@ -60,7 +60,7 @@ __device__ __forceinline__ void fs_stamp_tiles(const FsArgs<Real> &s, unsigned b
     const unsigned mx = (bx + s.ntx + k % 3 - 1) % s.ntx;
     const unsigned my = (by + s.nty + (k / 3) % 3 - 1) % s.nty;
     const unsigned mz = (bz + s.ntz + k / 9 - 1) % s.ntz;
-    s.stamp[mx + s.ntx * (my + s.nty * mz)] = s.stamp_next;
+    s.stamp[mx + s.ntx * (my + s.nty * mz)] = *s.stamp_ctr + 1u;
   }
   __syncthreads();  // block_mask is reset for the next tile only after every read
 }
@@ -92,7 +92,7 @@ template <class Real>
 __global__ void __launch_bounds__(BLOCK) fs_compact_kernel(const FsArgs<Real> s) {
   const unsigned t = blockIdx.x * BLOCK + threadIdx.x;
   if (t >= s.ntx * s.nty * s.ntz) return;
-  if (s.stamp[t] == s.stamp_next) s.next_tiles[atomicAdd(s.next_n_tiles, 1u)] = t;
+  if (s.stamp[t] == *s.stamp_ctr + 1u) s.next_tiles[atomicAdd(s.next_n_tiles, 1u)] = t;
 }
 
 // After initialisation: one block per tile stamps the tiles the first step
@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S:
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *s.any = 0u;
     *s.next_n_tiles = 0u;
+    *s.stamp_ctr += 1u;  // read only by the later passes of this step
   }
   fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
   const uint32_t link = a.link ? __ldg(a.link + n) : 0u;
