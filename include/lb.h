@@ -181,7 +181,10 @@ int lb_set_stream(lb_ctx *ctx, void *cuda_stream);
  *   solute; species s at C0 + s*N), cell_type N (LB_CELL_*,
  *   required iff free_surface), lambda0 N liquid fraction (NULL: 1 liquid,
  *   0.5 interface, 0 empty), f_scale 19*N factors multiplying the initial f
- *   (NULL = 1; seeded perturbations). Solid cells are ignored. */
+ *   (NULL = 1; seeded perturbations). Solid cells are ignored. rho0, u0, C0
+ *   and f_scale in memory the GPU can address (device, managed, pinned host)
+ *   are read in place by the initialisation on the context's stream (keep
+ *   them until lb_sync); others are copied before lb_init returns. */
 int lb_init(lb_ctx *ctx, const float *rho0, const float *u0, const float *C0,
             const uint8_t *cell_type, const float *lambda0, const float *f_scale);
 

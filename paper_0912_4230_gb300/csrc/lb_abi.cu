@@ -773,10 +773,37 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
   float *d_lam = d_C + S * N;
   float *d_fs = d_lam + N;
   uint8_t *d_type = reinterpret_cast<uint8_t *>(d_fs + (f_scale ? size_t(Q) * N : 0));
-  CK(c, cudaMemcpyAsync(d_rho, rho0, N * 4, cudaMemcpyDefault, c->stream));
-  CK(c, cudaMemcpyAsync(d_u, u0, 3 * N * 4, cudaMemcpyDefault, c->stream));
-  if (C0) CK(c, cudaMemcpyAsync(d_C, C0, S * N * 4, cudaMemcpyDefault, c->stream));
-  if (f_scale) CK(c, cudaMemcpyAsync(d_fs, f_scale, size_t(Q) * N * 4, cudaMemcpyDefault, c->stream));
+  // Inputs the GPU can address (device, managed, pinned or registered host
+  // memory) are read in place by the initialisation kernels; the others are
+  // copied to the staging block first.
+  auto in_place = [](const void *p) -> const void * {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+    if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+    return nullptr;
+  };
+  {
+    const void *v = in_place(rho0);
+    if (v) d_rho = const_cast<float *>(static_cast<const float *>(v));
+    else CK(c, cudaMemcpyAsync(d_rho, rho0, N * 4, cudaMemcpyDefault, c->stream));
+    v = in_place(u0);
+    if (v) d_u = const_cast<float *>(static_cast<const float *>(v));
+    else CK(c, cudaMemcpyAsync(d_u, u0, 3 * N * 4, cudaMemcpyDefault, c->stream));
+    if (C0) {
+      v = in_place(C0);
+      if (v) d_C = const_cast<float *>(static_cast<const float *>(v));
+      else CK(c, cudaMemcpyAsync(d_C, C0, S * N * 4, cudaMemcpyDefault, c->stream));
+    }
+    if (f_scale) {
+      v = in_place(f_scale);
+      if (v) d_fs = const_cast<float *>(static_cast<const float *>(v));
+      else CK(c, cudaMemcpyAsync(d_fs, f_scale, size_t(Q) * N * 4, cudaMemcpyDefault, c->stream));
+    }
+  }
   if (c->fs) {
     CK(c, cudaMemcpyAsync(d_type, cell_type, N, cudaMemcpyDefault, c->stream));
     if (lambda0) CK(c, cudaMemcpyAsync(d_lam, lambda0, N * 4, cudaMemcpyDefault, c->stream));

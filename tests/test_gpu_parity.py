@@ -435,3 +435,28 @@ def test_poiseuille_exact_discrete_solution_on_the_gpu(storage, tol, tau):
     exact = G / (2 * nu) * (y * (nz - y) + (16 * (tau - 0.5) ** 2 - 3) / 12)
     assert np.abs(u[..., 0] - exact[:, None, None]).max() <= tol * np.abs(exact).max()
     g.close()
+
+
+@pytest.mark.parametrize("where", ["pinned", "device"])
+def test_init_reads_addressable_inputs_in_place(where):
+    """lb_init from pinned host or device arrays (read in place by the
+    initialisation) gives the state that pageable arrays (copied) give."""
+    torch = pytest.importorskip("torch")
+    p = W.random_medium(19, 13, 11, seed=8)
+    a = lb.Lattice(p, storage="fp32", init=False)
+    b = lb.Lattice(p, storage="fp32", init=False)
+    arrs = [np.ascontiguousarray(x, np.float32) for x in (p.rho0, p.u0, p.C0)]
+    lb.lb_init(a.ctx, *arrs)
+    if where == "pinned":
+        ts = [torch.from_numpy(x).pin_memory() for x in arrs]
+    else:
+        ts = [torch.from_numpy(x).cuda() for x in arrs]
+    torch.cuda.synchronize()
+    lb.lb_init(b.ctx, *ts)
+    b.sync()
+    for n in (0, 9):
+        a.step(n)
+        b.step(n)
+        fa, ha = a.populations()
+        fb, hb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
