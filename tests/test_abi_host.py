@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library loads, exports
 every function include/lb.h declares, and rejects invalid requests before
 touching the device."""
+import ctypes
 import os
 import re
 
@@ -100,3 +101,19 @@ def test_invalid_face_kinds_rejected(L):
     dom.bc[2][0] = dom.bc[2][1] = W.INLET  # fluid faces cannot be inlets
     with pytest.raises(lb.LbError):
         lb.lb_create(dom, prob.eps, prob.K6, prob.solid, lb.make_params(prob))
+
+
+def test_null_contexts_and_batches_are_refused(L):
+    """Calls on a NULL context return LB_EINVAL without touching a GPU."""
+    vp = ctypes.c_void_p
+    assert L.lb_set_graphs(None, 1) == lb.LB_EINVAL
+    assert L.lb_debug_graphs(None) == lb.LB_EINVAL
+    assert L.lb_step(None, 1) == lb.LB_EINVAL
+    assert L.lb_step_batch(None, 1, 1) == lb.LB_EINVAL
+    arr = (vp * 1)(None)
+    assert L.lb_step_batch(arr, 0, 1) == lb.LB_EINVAL      # no lattices
+    assert L.lb_arena_stats(None, None, None, None, None) == lb.LB_EINVAL
+    assert L.lb_arena_alloc(None, 256) is None
+    out = vp(1)
+    assert L.lb_arena_create(None, 16, ctypes.byref(out)) == lb.LB_EINVAL   # below one block
+    assert out.value is None
