@@ -210,7 +210,17 @@ class Server:
                         pending.pop(0)
                         ready.append(r)
                         lock.notify_all()
-            admitter = threading.Thread(target=admit_loop, daemon=True)
+            def admit_guarded():
+                # any failure of the admission thread ends the run with that
+                # error (the stepping loop checks _admit_error each pass)
+                try:
+                    admit_loop()
+                except BaseException as e:  # noqa: BLE001
+                    with lock:
+                        self._admit_error = e
+                        lock.notify_all()
+
+            admitter = threading.Thread(target=admit_guarded, daemon=True)
             admitter.start()
         while True:
             now = self.clock() - t0

@@ -223,3 +223,22 @@ def test_admission_fails_when_nothing_can_free_memory():
     with pytest.raises(MemoryError):
         srv.run(_reqs([(0.0, 10, 100)]))       # 150 000 bytes > the 64 KiB arena
     arena.close()
+
+
+def test_admission_thread_failure_ends_the_run():
+    """An error while admitting on the background thread (here an invalid
+    request) is raised by run() instead of leaving it waiting."""
+    import time
+
+    class Failing(FakeBackend):
+        def admit(self, prob):
+            if prob.N > 500:
+                raise ValueError("invalid request")
+            return super().admit(prob)
+
+    be = Failing(None)
+    be.step = lambda handles, n: None
+    srv = serve.Server(be, budget_bytes=10 ** 9, chunk=10, clock=time.perf_counter,
+                       sleep=time.sleep, admit_in_thread=True)
+    with pytest.raises(ValueError):
+        srv.run(_reqs([(0.0, 5, 20), (0.0, 10, 20)]))
