@@ -73,9 +73,13 @@ enum { LB_BC_PERIODIC = 0, LB_BC_WALL = 1, LB_BC_INLET = 2, LB_BC_OUTLET = 3,
 /* Population storage (the collision always runs in FP32, or FP64 for
  * LB_STORE_FP64). FP32 and FP64 store f_q - w_q and h_q. FP16DEV and BF16DEV
  * store deviations from the equilibrium weights scaled by the cell's own
- * totals: per cell an FP32 reference r_f = rho - 1 (and r_h = sum_q h_q), and
- * per population the 16-bit remainder (f_q - w_q)/w_q - r_f (resp.
- * h_q/w_q - r_h), so density and solute content are carried in FP32. */
+ * totals: per cell a reference r_f = rho - 1 (and r_h = sum_q h_q), and per
+ * population the 16-bit remainder (f_q - w_q)/w_q - r_f (resp. h_q/w_q - r_h)
+ * formed against the stored reference, so density and solute content never
+ * pass through the 16-bit mantissa. With the solute lattice the remainders of
+ * f_q and h_q (species 0) are stored as one 32-bit pair and the references as
+ * one FP16 pair per cell; further species and lattices without solute keep
+ * their own rows and FP32 references. */
 enum { LB_STORE_FP32 = 0, LB_STORE_FP64 = 1, LB_STORE_FP16DEV = 2, LB_STORE_BF16DEV = 3 };
 
 /* Largest number of solute species (lb_params.species). */

@@ -101,11 +101,13 @@ struct StoreF64 {
   __host__ __device__ static T from_h(double h, int, double = 0.0) { return h; }
 };
 
-// FP16 / BF16: each cell also keeps an FP32 reference per lattice (its density
+// FP16 / BF16: each cell also keeps a reference per lattice (its density
 // deviation rho - 1 for f, its solute content sum_q h_q for h), and the
 // 16-bit populations hold the remainder g_q = (f_q - w_q)/w_q - ref (resp.
 // h_q/w_q - ref): the conserved parts never pass through the short mantissa.
-// ld_*/st_* below convert w_q g_q; the kernels add / subtract w_q ref.
+// ld_*/st_* below convert w_q g_q (rows with FP32 references: lattices without
+// solute, species 1 ..); ld_e / st_raw the remainder itself, ld2 / st2 the
+// (f, h) pairs of the paired layout with its FP16 reference pairs.
 struct StoreF16 {
   using T = __half;
   using Real = float;
