@@ -182,3 +182,30 @@ def test_contact_angle_sweep_is_reproduced_and_ordered():
     spec.loader.exec_module(ca)
     i = sweep["wall_rho"].index(0.6)
     assert ca.run(0.6, -7.0) == pytest.approx(sweep["angles_deg"]["from_90deg"][i], abs=0.05)
+
+
+def test_falling_drop_follows_free_fall():
+    """Section 5.3's falling drop: with the gas carrying no momentum, a
+    drop under the body force G falls freely until it meets the wall; its
+    centre of mass moves by G t^2 / 2 (within 1.5 %: the interface cells'
+    fill and the drop's small deformation), and the liquid mass stays
+    constant. At the paper's G = 1e-6 this is the printed impact after about
+    10 600 steps for a drop whose lowest point starts 56 cells above the
+    wall (sqrt(2 * 56 / 1e-6) = 10 583)."""
+    G = 1e-5
+    p = W.drop(nx=48, ny=1, nz=80, R=8.0, gap=30.0, u_drop=0.0, perturb=0.0)
+    p = p.replace(params=dict(p.params, G=(0.0, 0.0, -G), A=0.0))
+    o = O.Oracle(p)
+    z = np.arange(p.N) // (p.nx * p.ny)
+
+    def zcm():
+        _, m = o.free_surface_state()
+        return (m * z).sum() / m.sum(), m.sum()
+
+    z0, m0 = zcm()
+    for k in range(1, 11):              # to t = 2000, before the impact at sqrt(2 * 30 / G) = 2449
+        o.step(200)
+        zc, m = zcm()
+        t = 200 * k
+        assert (z0 - zc) == pytest.approx(0.5 * G * t * t, rel=0.015)
+        assert m == pytest.approx(m0, rel=1e-12)
