@@ -8,11 +8,13 @@ the CUDA library and never calls it.
 
 Parity status per function (pins live in ``tests/test_oracle_*.py``):
   velocity set, f^eq, forcing T_q, velocity solve, h^eq, viscosity laws,
-  streaming/bounce-back, inlet/outlet fluxes, colour gradient: pinned.
-  free-surface conversion: pinned by exact mass conservation and by the
-  closed interface layer (no liquid cell next to an empty one, no mass in
-  empty cells, m - rho kept in cells that stay liquid); the thresholds and
-  the equal sharing of excess mass are readings the paper gives no value for.
+  streaming/bounce-back (the exact discrete Poiseuille solution), inlet/outlet
+  fluxes, colour gradient: pinned.
+  free surface: pinned by exact mass conservation, free fall of a drop, and
+  the closed interface layer (no liquid cell next to an empty one, no mass in
+  empty cells, m - rho kept in cells that stay liquid); the conversion
+  thresholds and the equal sharing of excess mass are readings the paper
+  gives no value for. Wetting (wall_rho): parity unpinned (no printed angle).
 """
 from __future__ import annotations
 
