@@ -1,0 +1,52 @@
+"""Host-side pieces of bench.py (CPU only): the clock record's parsing of the
+nvidia-smi samples and the code hash that keeps a recorded capture valid."""
+import json
+import os
+
+import bench
+
+
+def _sampler(lines):
+    s = bench.ClockSampler(0)
+    s.lines = lines
+    return s.summary()
+
+
+def test_clock_summary_median_and_reasons():
+    lines = ["0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, 2060, 2070, 1200.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1210.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"]
+    s = _sampler(lines)
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_clock_summary_flags_thermal_slowdown_and_ignores_junk():
+    lines = ["0, 1500, 2070, 1400.0, 0x40, Active, Not Active, Active, Not Active",
+             "garbage", "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = _sampler(lines)
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["samples"] == 1
+
+
+def test_clock_summary_without_samples():
+    assert _sampler([])["reasons"] == ["unsampled"]
+
+
+def test_traffic_record_is_consistent_and_hash_ignores_comments(tmp_path, monkeypatch):
+    """The traffic record names the code hash of its capture (the bench
+    reports the DRAM traffic only while the sources still hash to it), and the
+    hash does not move when only comments change."""
+    pj = json.load(open(os.path.join(bench.ROOT, "profiles", "step_kernel_miscible128_traffic.json")))
+    assert pj["dram_bytes_per_launch"] == pj["dram_bytes_read_per_launch"] + pj["dram_bytes_write_per_launch"]
+    assert len(pj["source_hash"]) == 16 and int(pj["source_hash"], 16) >= 0
+    csrc = os.path.join(bench.ROOT, "paper_0912_4230_gb300", "csrc")
+    fake = tmp_path / "paper_0912_4230_gb300" / "csrc"
+    fake.mkdir(parents=True)
+    for f in ("lb_common.cuh", "lb_kernels.cuh", "lb_inst.cuh"):
+        (fake / f).write_text(open(os.path.join(csrc, f)).read() + "\n// a comment\n/* another */\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    commented = bench.kernel_source_hash()
+    (fake / "lb_inst.cuh").write_text((fake / "lb_inst.cuh").read_text() + "int changed;\n")
+    changed = bench.kernel_source_hash()
+    monkeypatch.undo()
+    assert commented == bench.kernel_source_hash() and changed != commented
