@@ -36,7 +36,8 @@ def _rank(rank, ws, port, out):
 def test_two_gloo_ranks_take_the_slowest_replica():
     ws = 2
     port = _free_port()
-    with mp.Manager() as m:
+    # spawn, not fork: the test process may already hold threads (or a CUDA context)
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
