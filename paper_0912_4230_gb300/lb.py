@@ -110,12 +110,32 @@ def load() -> ctypes.CDLL:
     return L
 
 
-def _ptr(a):
-    """Raw pointer of a numpy array or torch tensor (None passes NULL)."""
+_F32, _F64, _U8, _I32 = np.float32, np.float64, np.uint8, np.int32
+
+
+def _ptr(a, dtype=None):
+    """Raw pointer of a numpy array or torch tensor (None passes NULL).
+
+    The library reads and writes each array as one dense run of its element
+    type, so a strided view, or an element type other than the one the C
+    declaration names (``dtype``), is refused here instead of being read as
+    something else; a bool array stands for uint8 (0/1 bytes)."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("lb: tensor arguments must be contiguous")
+        if dtype is not None:
+            name = str(a.dtype).replace("torch.", "")
+            if name != np.dtype(dtype).name and not (dtype is _U8 and name == "bool"):
+                raise TypeError(f"lb: tensor of {name} where the library takes {np.dtype(dtype).name}")
         return c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray):
+        raise TypeError(f"lb: array argument expected, got {type(a).__name__}")
+    if not a.flags.c_contiguous:
+        raise ValueError("lb: array arguments must be C-contiguous")
+    if dtype is not None and a.dtype != dtype and not (dtype is _U8 and a.dtype == np.bool_):
+        raise TypeError(f"lb: array of {a.dtype} where the library takes {np.dtype(dtype).name}")
     return a.ctypes.data_as(c_void_p)
 
 
@@ -129,7 +149,7 @@ def _check(rc: int, ctx=None):
 
 def lb_create(domain: lb_domain, porosity, K6, solid, params: lb_params):
     ctx = c_void_p()
-    rc = load().lb_create(ctypes.byref(domain), _ptr(porosity), _ptr(K6), _ptr(solid),
+    rc = load().lb_create(ctypes.byref(domain), _ptr(porosity, _F32), _ptr(K6, _F32), _ptr(solid, _U8),
                           ctypes.byref(params), ctypes.byref(ctx))
     _check(rc, None)
     return ctx
@@ -141,16 +161,16 @@ def lb_set_stream(ctx, stream_handle: int):
 
 
 def lb_init(ctx, rho0, u0, C0=None, cell_type=None, lambda0=None, f_scale=None):
-    _check(load().lb_init(ctx, _ptr(rho0), _ptr(u0), _ptr(C0), _ptr(cell_type), _ptr(lambda0),
-                          _ptr(f_scale)), ctx)
+    _check(load().lb_init(ctx, _ptr(rho0, _F32), _ptr(u0, _F32), _ptr(C0, _F32),
+                          _ptr(cell_type, _U8), _ptr(lambda0, _F32), _ptr(f_scale, _F32)), ctx)
 
 
 def lb_set_populations(ctx, f=None, h=None):
-    _check(load().lb_set_populations(ctx, _ptr(f), _ptr(h)), ctx)
+    _check(load().lb_set_populations(ctx, _ptr(f, _F64), _ptr(h, _F64)), ctx)
 
 
 def lb_get_populations(ctx, f=None, h=None):
-    _check(load().lb_get_populations(ctx, _ptr(f), _ptr(h)), ctx)
+    _check(load().lb_get_populations(ctx, _ptr(f, _F64), _ptr(h, _F64)), ctx)
 
 
 def lb_step(ctx, n: int):
@@ -169,11 +189,11 @@ def lb_autotune(ctx, reps: int = 5) -> int:
 def lb_step_batch(ctxs, n_steps: int):
     """Advance several contexts by n_steps in one batched launch per step."""
     arr = (c_void_p * len(ctxs))(*[c.value if isinstance(c, c_void_p) else c for c in ctxs])
-    _check(load().lb_step_batch(arr, len(ctxs), int(n_steps)), ctxs[0])
+    _check(load().lb_step_batch(arr, len(ctxs), int(n_steps)), ctxs[0] if len(ctxs) else None)
 
 
 def lb_fields(ctx, rho=None, u=None, C=None, nu=None):
-    _check(load().lb_fields(ctx, _ptr(rho), _ptr(u), _ptr(C), _ptr(nu)), ctx)
+    _check(load().lb_fields(ctx, _ptr(rho, _F32), _ptr(u, _F32), _ptr(C, _F32), _ptr(nu, _F32)), ctx)
 
 
 def lb_reduce(ctx):
@@ -183,7 +203,7 @@ def lb_reduce(ctx):
 
 
 def lb_debug_neighbors(ctx, lattice: int, src):
-    _check(load().lb_debug_neighbors(ctx, int(lattice), _ptr(src)), ctx)
+    _check(load().lb_debug_neighbors(ctx, int(lattice), _ptr(src, _I32)), ctx)
 
 
 def lb_debug_wait_timeout(ctx, limit_ns: int):
@@ -202,11 +222,11 @@ def lb_debug_graphs(ctx) -> int:
 
 
 def lb_species_state(ctx, s: int, C=None, totals=None, h=None):
-    _check(load().lb_species_state(ctx, int(s), _ptr(C), _ptr(totals), _ptr(h)), ctx)
+    _check(load().lb_species_state(ctx, int(s), _ptr(C, _F32), _ptr(totals, _F64), _ptr(h, _F64)), ctx)
 
 
 def lb_free_surface_state(ctx, cell_type=None, mass=None):
-    _check(load().lb_free_surface_state(ctx, _ptr(cell_type), _ptr(mass)), ctx)
+    _check(load().lb_free_surface_state(ctx, _ptr(cell_type, _U8), _ptr(mass, _F64)), ctx)
 
 
 def lb_sync(ctx):
@@ -228,8 +248,8 @@ def lb_destroy(ctx):
 def lb_totals_noalloc(f, h, solid, n_cells: int, out, stream_handle: int = 0):
     """FP64 (mass, solute) of caller-owned device arrays without any device
     allocation (see include/lb.h); out receives 2 doubles."""
-    rc = load().lb_totals_noalloc(_ptr(f), _ptr(h), _ptr(solid), int(n_cells), _ptr(out),
-                                  c_void_p(stream_handle))
+    rc = load().lb_totals_noalloc(_ptr(f, _F32), _ptr(h, _F32), _ptr(solid, _U8), int(n_cells),
+                                  _ptr(out, _F64), c_void_p(stream_handle))
     if rc != LB_OK:
         raise LbError(rc, "lb_totals_noalloc failed")
 

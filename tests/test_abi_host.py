@@ -117,3 +117,33 @@ def test_null_contexts_and_batches_are_refused(L):
     out = vp(1)
     assert L.lb_arena_create(None, 16, ctypes.byref(out)) == lb.LB_EINVAL   # below one block
     assert out.value is None
+
+
+def test_array_arguments_must_match_the_declared_element_type():
+    """The binding passes raw pointers, so it refuses strided views and
+    element types other than the declared one before the library sees them."""
+    torch = pytest.importorskip("torch")
+    a = np.zeros((4, 3), np.float32)
+    assert lb._ptr(None, np.float32) is None
+    assert lb._ptr(a, np.float32).value == a.ctypes.data
+    assert lb._ptr(np.zeros(3, bool), np.uint8) is not None        # 0/1 bytes
+    with pytest.raises(ValueError):
+        lb._ptr(a.T, np.float32)
+    with pytest.raises(ValueError):
+        lb._ptr(a[:, 0], np.float32)
+    with pytest.raises(TypeError):
+        lb._ptr(a.astype(np.float64), np.float32)
+    with pytest.raises(TypeError):
+        lb._ptr([0.0, 1.0], np.float32)
+    t = torch.zeros(4, 3, dtype=torch.float32)
+    assert lb._ptr(t, np.float32).value == t.data_ptr()
+    assert lb._ptr(torch.zeros(3, dtype=torch.bool), np.uint8) is not None
+    with pytest.raises(ValueError):
+        lb._ptr(t.t(), np.float32)
+    with pytest.raises(TypeError):
+        lb._ptr(t.double(), np.float32)
+    # the wrappers check before any library call: a wrong type never reaches it
+    with pytest.raises(TypeError):
+        lb.lb_fields(None, np.zeros(4, np.float64))
+    with pytest.raises(TypeError):
+        lb.lb_set_populations(None, np.zeros(19, np.float32))
