@@ -28,18 +28,25 @@ ELT = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}
 
 def device_bytes(nx: int, ny: int, nz: int, storage: str = "fp32", solute: bool = True,
                  kmode_rows: int = 3) -> int:
-    """Device memory of one lattice as the library allocates it: two
-    population buffers per lattice, static fields, exported fields, flux
-    slots, staging for initialisation."""
+    """Peak device memory of one lattice as the library allocates it: two
+    population buffers per lattice (16-bit storage: plus a 32-bit reference
+    per cell and buffer), static fields, exported fields, flux slots and
+    per-block partial sums, and the larger of the two staging buffers (the
+    creation inputs, porosity + six K components + solid mask, are released
+    before the initialisation inputs take their place), each of the about 20
+    allocations rounded up to 256 bytes. kmode_rows: 0 without K, 3 diagonal,
+    6 full tensor."""
     N = nx * ny * nz
     lattices = 2 if solute else 1
     pops = lattices * 2 * Q * N * ELT[storage]
+    refs = 2 * 4 * N if storage in ("fp16", "bf16") else 0
     real = 8 if storage == "fp64" else 4
     static = N * real * (1 + kmode_rows + (3 if solute else 0)) + 4 * N
     fields = 6 * N * 4
-    stage = 6 * N * 4 + N
+    stage_create = 4 * N + (24 * N if kmode_rows else 0) + N + 320
+    stage_init = 6 * N * 4 + N + 256
     slots = (N // 256 + 1) * 8 * 2 * 8 + (N // 256 + 1) * 4 * 8
-    return int(pops + static + fields + stage + slots)
+    return int(pops + refs + static + fields + max(stage_create, stage_init) + slots + 24 * 256)
 
 
 @dataclasses.dataclass
@@ -83,7 +90,9 @@ class LibraryBackend:
         self.step_stream = step_stream
 
     def bytes(self, prob) -> int:
-        kr = 0 if prob.K6 is None else 3
+        kr = 0
+        if prob.K6 is not None:      # the library keeps 6 rows of K^-1 for a full tensor
+            kr = 6 if np.any(np.asarray(prob.K6).reshape(-1, 6)[:, 3:] != 0) else 3
         return device_bytes(prob.nx, prob.ny, prob.nz, self.storage,
                             bool(prob.params.get("solute")), kr)
 

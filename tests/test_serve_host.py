@@ -242,3 +242,18 @@ def test_admission_thread_failure_ends_the_run():
                        sleep=time.sleep, admit_in_thread=True)
     with pytest.raises(ValueError):
         srv.run(_reqs([(0.0, 5, 20), (0.0, 10, 20)]))
+
+
+def test_device_bytes_counts_references_and_the_larger_staging():
+    """16-bit storage halves the populations but adds a 32-bit reference per
+    cell and buffer; a full permeability tensor adds three rows of K^-1; the
+    creation staging (with the six K components) outweighs the initialisation
+    staging whenever K is given."""
+    N = 32 ** 3
+    b32 = serve.device_bytes(32, 32, 32, "fp32")
+    b16 = serve.device_bytes(32, 32, 32, "fp16")
+    assert b32 - b16 == 2 * 2 * 19 * N * 2 - 8 * N
+    assert serve.device_bytes(32, 32, 32, "bf16") == b16
+    assert serve.device_bytes(32, 32, 32, "fp32", kmode_rows=6) - b32 == 3 * 4 * N
+    no_k = serve.device_bytes(32, 32, 32, "fp32", kmode_rows=0)
+    assert b32 - no_k == 3 * 4 * N + (29 * N + 320) - (25 * N + 256)
