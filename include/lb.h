@@ -306,7 +306,10 @@ void lb_destroy(lb_ctx *ctx);
 
 /* Route the library's device allocations through caller functions (for
  * example a framework's caching allocator); both NULL restores cudaMalloc.
- * Affects contexts created afterwards. alloc returns NULL on failure. */
+ * Affects contexts created afterwards (process-wide; safe to call while other
+ * threads create contexts: each takes the hooks in force when it starts).
+ * alloc returns NULL on failure; release must accept every pointer alloc
+ * returned, and a context keeps the hooks it was created with. */
 int lb_set_allocator(void *(*alloc)(size_t bytes, void *user),
                      void (*release)(void *ptr, void *user), void *user);
 

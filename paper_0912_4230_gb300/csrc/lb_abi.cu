@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -20,9 +21,16 @@ using namespace lbgb;
 
 namespace {
 
-void *(*g_alloc)(size_t, void *) = nullptr;
-void (*g_release)(void *, void *) = nullptr;
-void *g_alloc_user = nullptr;
+// process-wide allocation hooks (lb_set_allocator), read by lb_create as
+// one triple under the lock, so a context never pairs one caller's alloc
+// with another's user pointer
+struct AllocHooks {
+  void *(*alloc)(size_t, void *) = nullptr;
+  void (*release)(void *, void *) = nullptr;
+  void *user = nullptr;
+};
+AllocHooks g_hooks;
+std::mutex g_hooks_mu;
 thread_local std::string g_create_error;
 thread_local cudaStream_t g_create_stream = nullptr;  // stream of lb_create's own work
 
@@ -441,9 +449,10 @@ extern "C" {
 
 int lb_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user) {
   if ((alloc == nullptr) != (release == nullptr)) return LB_EINVAL;
-  g_alloc = alloc;
-  g_release = release;
-  g_alloc_user = user;
+  std::lock_guard<std::mutex> lock(g_hooks_mu);
+  g_hooks.alloc = alloc;
+  g_hooks.release = release;
+  g_hooks.user = user;
   return LB_OK;
 }
 
@@ -506,9 +515,12 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   c->prm = *prm;
   c->ops = ops;
   c->stream = g_create_stream;
-  c->alloc_fn = g_alloc;
-  c->release_fn = g_release;
-  c->alloc_user = g_alloc_user;
+  {
+    std::lock_guard<std::mutex> lock(g_hooks_mu);
+    c->alloc_fn = g_hooks.alloc;
+    c->release_fn = g_hooks.release;
+    c->alloc_user = g_hooks.user;
+  }
   c->N = unsigned(N64);
   c->nblk = (c->N + BLOCK - 1) / BLOCK;
   {

@@ -90,8 +90,10 @@ void *lb_arena_alloc(lb_arena *a, size_t bytes) {
 
 void lb_arena_free(lb_arena *a, void *ptr) {
   if (!a || !ptr) return;
+  const uintptr_t p = reinterpret_cast<uintptr_t>(ptr), b = reinterpret_cast<uintptr_t>(a->base);
+  if (p < b || p - b >= a->bytes) return;  // outside the region
+  const size_t off = size_t(p - b);
   std::lock_guard<std::mutex> lock(a->mu);
-  const size_t off = size_t(static_cast<char *>(ptr) - a->base);
   auto lv = a->live.find(off);
   if (lv == a->live.end()) return;  // not a block of this arena
   size_t start = off, len = lv->second;

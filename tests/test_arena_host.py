@@ -146,3 +146,18 @@ def test_invalid_regions_are_refused():
     assert e.value.code == lb.LB_EINVAL
     with pytest.raises(lb.LbError):
         lb.Arena(100, base)            # smaller than one block
+
+
+def test_foreign_pointers_are_ignored_on_release():
+    """Releasing a pointer outside the region, or inside it but not at the
+    start of a live block, leaves the bookkeeping unchanged."""
+    buf, base = _region(1 << 14)
+    a = lb.Arena(1 << 14, base)
+    p = a.alloc(1000)
+    before = a.stats()
+    for q in (base - ALIGN, base + (1 << 14), base + (1 << 20), p + ALIGN, 1):
+        a.free(q)
+        assert a.stats() == before
+    a.free(p)
+    assert a.stats()["used"] == 0 and a.stats()["largest_free"] == 1 << 14
+    a.close()
