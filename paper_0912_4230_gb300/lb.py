@@ -254,17 +254,18 @@ def lb_totals_noalloc(f, h, solid, n_cells: int, out, stream_handle: int = 0):
         raise LbError(rc, "lb_totals_noalloc failed")
 
 
-_allocator_refs = None
+# every callback pair ever installed stays referenced: a context keeps the
+# hooks it was created with and calls release from lb_destroy, possibly after
+# another allocator (or none) has been installed
+_allocator_refs = []
 
 
 def lb_set_allocator(alloc=None, release=None):
     """Route device allocations through Python callables alloc(nbytes) -> int
     pointer and release(ptr); ``use_torch_allocator()`` installs torch's."""
-    global _allocator_refs
     L = load()
     if alloc is None:
         _check(L.lb_set_allocator(L._ALLOC(0), L._FREE(0), None))
-        _allocator_refs = None
         return
 
     def _a(nbytes, _user):
@@ -277,8 +278,8 @@ def lb_set_allocator(alloc=None, release=None):
         release(ptr)
 
     refs = (L._ALLOC(_a), L._FREE(_r))
+    _allocator_refs.append(refs)
     _check(L.lb_set_allocator(refs[0], refs[1], None))
-    _allocator_refs = refs
 
 
 def use_torch_allocator():

@@ -147,3 +147,15 @@ def test_array_arguments_must_match_the_declared_element_type():
         lb.lb_fields(None, np.zeros(4, np.float64))
     with pytest.raises(TypeError):
         lb.lb_set_populations(None, np.zeros(19, np.float32))
+
+
+def test_allocator_hooks_install_reset_and_stay_referenced(L):
+    """Hooks are installed and reset without a GPU; a half-set pair is
+    refused; the binding keeps every installed pair alive, since a context
+    created under it calls its release from lb_destroy later."""
+    n0 = len(lb._allocator_refs)
+    lb.lb_set_allocator(lambda n: 0, lambda p: None)
+    keep = lb._allocator_refs[-1]
+    assert L.lb_set_allocator(L._ALLOC(0), keep[1], None) == lb.LB_EINVAL
+    lb.lb_set_allocator(None)
+    assert len(lb._allocator_refs) == n0 + 1 and lb._allocator_refs[-1] is keep
