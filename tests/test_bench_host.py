@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py (CPU only): the clock record's parsing of the
-nvidia-smi samples and the code hash that keeps a recorded capture valid."""
+nvidia-smi samples, the code hash that keeps a recorded capture valid, and
+the reference arm (the oracle on the host cores)."""
 import json
 import os
 
@@ -50,3 +51,25 @@ def test_traffic_record_is_consistent_and_hash_ignores_comments(tmp_path, monkey
     changed = bench.kernel_source_hash()
     monkeypatch.undo()
     assert commented == bench.kernel_source_hash() and changed != commented
+
+
+def test_reference_arm_prints_one_line_on_rank_zero_only():
+    """The oracle as the reference arm: one JSON line with the bench line's
+    metric, unit and direction, its own cpu_baseline and e2e; other ranks
+    print nothing and exit 0."""
+    import subprocess
+    import sys
+    cmd = [sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+           "--steps", "1", "--warmup", "3"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "MLUPS"
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0 and not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
