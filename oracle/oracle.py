@@ -8,7 +8,8 @@ the CUDA library and never calls it.
 
 Parity status per function (pins live in ``tests/test_oracle_*.py``):
   velocity set, f^eq, forcing T_q, velocity solve, h^eq, viscosity laws,
-  streaming/bounce-back (the exact discrete Poiseuille solution), inlet/outlet
+  streaming/bounce-back (the exact discrete Poiseuille solution), the viscous
+  and Darcy decay of a shear wave, inlet/outlet
   fluxes, colour gradient: pinned.
   free surface: pinned by exact mass conservation, free fall of a drop, and
   the closed interface layer (no liquid cell next to an empty one, no mass in

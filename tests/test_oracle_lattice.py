@@ -1,6 +1,7 @@
 """Pins of the oracle's lattice-level behaviour (CPU only): streaming and
 boundary classes by brute force, exact conservation, the Brinkman and Darcy
-closed forms (Section 5.1), the paper's printed anisotropic-channel numbers
+closed forms (Section 5.1), the viscous and Darcy decay of a shear wave, the
+paper's printed anisotropic-channel numbers
 (Section 5.2), Gaussian diffusion and the porosity-gradient correction of the
 solute lattice (Section 2.2), and the viscosity laws (Section 5.5)."""
 import json
@@ -347,3 +348,60 @@ def test_viscosity_field_follows_concentration(law):
     else:
         expect = k["nu_g"] * (1 + k["a"] * np.exp(k["alpha"] * 7)) * np.exp(k["beta"] * (1 - C))
     assert np.allclose(nu[live], expect[live], rtol=1e-13)
+
+
+def _shear_wave_rate(L, tau, eps=1.0, K=None, A=1e-4):
+    """Decay rate of a shear wave u_x = A sin(2 pi y / L) in a periodic
+    column, measured from the amplitudes of the sine mode at two times one
+    e-folding apart (after the initial transient), and the continuum rate
+    nu k^2 + eps nu / K of the Brinkman momentum equation (Eq. momentum with
+    nu_e = nu, no body force; the Darcy part absent without K)."""
+    p = W.gaussian_pulse(nx=1, ny=L, nz=1)
+    y = np.arange(L)
+    u0 = np.zeros((L, 3), np.float32)
+    u0[:, 0] = A * np.sin(2 * np.pi * y / L)
+    K6 = None if K is None else np.tile(np.array([K, K, K, 0, 0, 0], np.float32), L)
+    p = p.replace(u0=u0.ravel(), C0=None, params=dict(tau=tau), eps=np.full(L, eps, np.float32),
+                  K6=K6)
+    k = 2 * np.pi / L
+    nu = (tau - 0.5) / 3.0
+    lam = nu * k * k + (0.0 if K is None else eps * nu / K)
+    t1, t2 = int(0.2 / lam) + 5, int(1.2 / lam) + 5
+    s = np.sin(k * y)
+    o = O.Oracle(p)
+    o.step(t1)
+    a1 = (o.fields()[1][:, 0] * s).sum()
+    o.step(t2 - t1)
+    a2 = (o.fields()[1][:, 0] * s).sum()
+    assert np.abs(o.fields()[1][:, 1:]).max() <= 1e-9 * A   # the wave stays transverse
+    return -np.log(a2 / a1) / (t2 - t1), lam
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.2])
+def test_shear_wave_decays_at_the_viscous_rate(tau):
+    """Free fluid (eps = 1): the measured rate tends to nu k^2 with
+    nu = (tau - 1/2)/3 at second order in k (the error falls fourfold when L
+    doubles) and is within 1e-3 of it at L = 64. A wrong viscosity, or a
+    relaxation that is not BGK's 1/tau, fails by far more than that."""
+    errs = []
+    for L in (32, 64):
+        r, lam = _shear_wave_rate(L, tau)
+        errs.append(r / lam - 1.0)
+    assert abs(errs[1]) < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.2])
+def test_shear_wave_in_a_porous_medium_adds_the_darcy_rate(tau):
+    """eps = 0.6 with isotropic K = 0.004 L^2 (a fixed Darcy number, the drag
+    79 % of the rate): the rate tends to nu k^2 + eps nu / K at second order
+    (the half-force velocity V' of Eqs. expandV / expandVsub turns the drag
+    into an exact per-step factor (1 - a/2)/(1 + a/2), a = eps nu / K, whose
+    rate differs from a by a^3/12 only). Without the drag, or with K in place
+    of K/eps, the rate is off by tens of percent."""
+    errs = []
+    for L in (32, 64):
+        r, lam = _shear_wave_rate(L, tau, eps=0.6, K=0.004 * L * L)
+        errs.append(r / lam - 1.0)
+    assert abs(errs[1]) < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
