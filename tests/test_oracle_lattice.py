@@ -1,6 +1,7 @@
 """Pins of the oracle's lattice-level behaviour (CPU only): streaming and
 boundary classes by brute force, exact conservation, the Brinkman and Darcy
-closed forms (Section 5.1), the viscous and Darcy decay of a shear wave, the
+closed forms (Section 5.1), the viscous and Darcy decay of a shear wave and of a
+standing sound wave, the
 paper's printed anisotropic-channel numbers
 (Section 5.2), Gaussian diffusion and the porosity-gradient correction of the
 solute lattice (Section 2.2), and the viscosity laws (Section 5.5)."""
@@ -405,3 +406,46 @@ def test_shear_wave_in_a_porous_medium_adds_the_darcy_rate(tau):
         errs.append(r / lam - 1.0)
     assert abs(errs[1]) < 1e-3
     assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def _sound_wave_error(L, tau, eps=1.0, K=None, d=1e-5, periods=2):
+    """Largest deviation, over two periods, of the density mode of a standing
+    sound wave rho = 1 + d cos(k x) (fluid at rest, periodic row) from the
+    damped oscillation of the linearised equations: with pressure rho/3 (the
+    second moment of Eqs. equilc1 / equilc2), BGK's shear and bulk viscosity
+    (nu and 2 nu / 3) and the Darcy drag a = eps nu / K, the mode obeys
+    rho'' + (2 nu k^2 + a) rho' + (k^2 / 3) rho = 0, so with rho' = 0 at t = 0
+    it is e^{-G t} (cos w t + (G / w) sin w t), G = nu k^2 + a / 2,
+    w^2 = k^2 / 3 - G^2. Relative to the initial amplitude."""
+    p = W.gaussian_pulse(nx=L, ny=1, nz=1)
+    x = np.arange(L)
+    k = 2 * np.pi / L
+    K6 = None if K is None else np.tile(np.array([K, K, K, 0, 0, 0], np.float32), L)
+    p = p.replace(rho0=(1.0 + d * np.cos(k * x)).astype(np.float32), C0=None,
+                  params=dict(tau=tau), eps=np.full(L, eps, np.float32), K6=K6)
+    nu = (tau - 0.5) / 3.0
+    G = nu * k * k + (0.0 if K is None else 0.5 * eps * nu / K)
+    w = np.sqrt(k * k / 3.0 - G * G)
+    c = np.cos(k * x)
+    o = O.Oracle(p)
+    a0 = (o.fields()[0] - 1.0) @ c
+    err = 0.0
+    for t in range(1, int(periods * 2 * np.pi / w) + 1):
+        o.step(1)
+        model = a0 * np.exp(-G * t) * (np.cos(w * t) + G / w * np.sin(w * t))
+        err = max(err, abs((o.fields()[0] - 1.0) @ c - model))
+    return err / abs(a0)
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8])
+@pytest.mark.parametrize("porous", [False, True])
+def test_sound_wave_speed_and_damping(tau, porous):
+    """The density mode follows the damped oscillation at second order in k
+    (the deviation falls at least threefold when L doubles, below 3e-3 of
+    the amplitude at L = 64), free (eps = 1) and in a porous medium (eps =
+    0.6, K = 0.004 L^2): pins the pressure rho/3, the bulk damping of BGK and
+    the Darcy drag's share of the damping of a compressive mode."""
+    kw = lambda L: dict(eps=0.6, K=0.004 * L * L) if porous else {}
+    e32, e64 = (_sound_wave_error(L, tau, **kw(L)) for L in (32, 64))
+    assert e64 < 3e-3
+    assert e32 / e64 > 3.0
