@@ -351,7 +351,9 @@ int lb_totals_noalloc(const float *f, const float *h, const uint8_t *solid, int6
  *                    afterwards into the arena (as lb_set_allocator does);
  *                    NULL restores cudaMalloc. An arena must outlive the
  *                    contexts allocated from it.
- *   lb_arena_alloc / lb_arena_free  one block (NULL when nothing fits).
+ *   lb_arena_alloc / lb_arena_free  one block (NULL when nothing fits); a
+ *                    pointer that is not the start of a live block of the
+ *                    arena (NULL, outside the region) is ignored.
  *   lb_arena_stats   bytes in use, the largest free block, the peak use and
  *                    the number of live blocks (any pointer may be NULL).
  * The bookkeeping never touches the region, so a host region serves for
