@@ -112,6 +112,9 @@ def test_null_contexts_and_batches_are_refused(L):
     assert L.lb_step_batch(None, 1, 1) == lb.LB_EINVAL
     arr = (vp * 1)(None)
     assert L.lb_step_batch(arr, 0, 1) == lb.LB_EINVAL      # no lattices
+    with pytest.raises(lb.LbError) as e:                     # the same through the binding
+        lb.lb_step_batch([], 1)
+    assert e.value.code == lb.LB_EINVAL
     assert L.lb_arena_stats(None, None, None, None, None) == lb.LB_EINVAL
     assert L.lb_arena_alloc(None, 256) is None
     out = vp(1)
