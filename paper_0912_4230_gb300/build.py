@@ -38,7 +38,10 @@ def _deps_mtime() -> float:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link; returns the path of the shared library."""
-    srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    missing = [s for s in SOURCES if not os.path.exists(os.path.join(CSRC, s))]
+    if missing:
+        raise FileNotFoundError(f"CUDA sources missing from {CSRC}: {', '.join(missing)}")
+    srcs = list(SOURCES)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
