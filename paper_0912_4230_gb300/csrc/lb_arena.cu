@@ -72,7 +72,8 @@ int lb_arena_use(lb_arena *a) {
 }
 
 void *lb_arena_alloc(lb_arena *a, size_t bytes) {
-  if (!a || bytes == 0) return nullptr;
+  // larger than the region: nothing fits (and rounding it up could wrap to 0)
+  if (!a || bytes == 0 || bytes > a->bytes) return nullptr;
   const size_t need = round_up(bytes);
   std::lock_guard<std::mutex> lock(a->mu);
   for (auto it = a->free_list.begin(); it != a->free_list.end(); ++it) {

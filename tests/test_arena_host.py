@@ -161,3 +161,19 @@ def test_foreign_pointers_are_ignored_on_release():
     a.free(p)
     assert a.stats()["used"] == 0 and a.stats()["largest_free"] == 1 << 14
     a.close()
+
+
+def test_requests_larger_than_the_region_get_nothing():
+    """A request above the region's size fails without touching the free
+    list, including sizes so close to 2^64 that rounding them up to a
+    256-byte block would wrap around to zero."""
+    buf, base = _region(1 << 14)
+    a = lb.Arena(1 << 14, base)
+    for n in ((1 << 14) + 1, 2 ** 64 - 1, 2 ** 64 - 255, 2 ** 63):
+        assert a.alloc(n) is None
+    st = a.stats()
+    assert st["used"] == 0 and st["blocks"] == 0 and st["largest_free"] == 1 << 14
+    p = a.alloc(1 << 14)          # the whole region still fits
+    assert p == base and a.alloc(1) is None
+    a.free(p)
+    a.close()
