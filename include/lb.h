@@ -298,11 +298,31 @@ int lb_sync(lb_ctx *ctx);
 int64_t lb_time(const lb_ctx *ctx);
 
 /* Message of the context's last failure ("" if none); for a NULL context the
- * message of the last failed lb_create on this thread. */
+ * message of the last failed call without a context on this thread
+ * (lb_create, lb_bytes_required, lb_totals_noalloc). */
 const char *lb_last_error(const lb_ctx *ctx);
 
 /* Release the context and all its device memory (NULL is a no-op). */
 void lb_destroy(lb_ctx *ctx);
+
+/* Device memory one lattice takes (no counterpart in the paper; it serves
+ * admission by an HBM budget): the bytes lb_create, lb_init and the stepping,
+ * export and totals calls (lb_step, lb_step_batch, lb_fields, lb_reduce)
+ * allocate for a lattice of this domain and these parameters, each block
+ * counted in 256-byte granules as the packed arena hands them out, with the
+ * larger of the creation and initialisation staging blocks (the first is
+ * released before the second is taken) and the lattice's share of a batch
+ * work list (8 bytes per block of its per-cell launch, held by the first
+ * context of an lb_step_batch call). Computed from the same layout that
+ * lb_create allocates by; host arithmetic only, no device is touched.
+ *   k_rows   rows of K^-1 kept: 0 (K NULL), 3 (a diagonal tensor field) or
+ *            6 (a full tensor field; also the bound when unknown);
+ *   f_scale  nonzero if lb_init will be given f_scale.
+ * Population exchange calls (lb_get_populations, lb_set_populations,
+ * lb_species_state with h, lb_debug_neighbors, lb_free_surface_state with
+ * mass) stage up to 19 N doubles more. Returns LB_OK or LB_EINVAL. */
+int lb_bytes_required(const lb_domain *dom, const lb_params *prm, int32_t k_rows,
+                      int32_t f_scale, size_t *bytes);
 
 /* Route the library's device allocations through caller functions (for
  * example a framework's caching allocator); both NULL restores cudaMalloc.
@@ -331,10 +351,13 @@ int lb_set_allocator(void *(*alloc)(size_t bytes, void *user),
  * (2 * 65536 + 2) doubles on every GPU that loads the library, held until
  * the process exits; so n_cells must be <= 16777216 (LB_EINVAL beyond).
  * The first call on each device looks up that array's device address (a
- * runtime call), so make that first call before any stream capture. All
- * calls on a device share the array: calls that overlap on the GPU race.
- * Returns LB_OK, LB_EINVAL or LB_ECUDA (no context: lb_last_error does not
- * report its messages). */
+ * runtime call) and keeps it for the life of the process, so make that first
+ * call before any stream capture; a cudaDeviceReset of a device the call has
+ * been used on is not supported afterwards (the kept address would be
+ * stale). Every call ends by waiting for `stream` (the totals are in `out`
+ * when it returns). All calls on a device share the array: calls that
+ * overlap on the GPU race. Returns LB_OK, LB_EINVAL or LB_ECUDA; the message
+ * of a failure is lb_last_error(NULL) on the calling thread. */
 int lb_totals_noalloc(const float *f, const float *h, const uint8_t *solid, int64_t n_cells,
                       double *out, void *stream);
 

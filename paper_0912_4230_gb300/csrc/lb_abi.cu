@@ -36,6 +36,10 @@ thread_local cudaStream_t g_create_stream = nullptr;  // stream of lb_create's o
 
 }  // namespace
 
+// Message of a failed call that has no context (lb_create, lb_bytes_required,
+// lb_totals_noalloc), reported by lb_last_error(NULL) on the same thread.
+void lbgb::set_noctx_error(const char *msg) { g_create_error = msg; }
+
 struct lb_ctx {
   lb_domain dom{};
   lb_params prm{};
@@ -149,10 +153,16 @@ void dev_free(lb_ctx *c, void *p) {
       c->allocs.erase(c->allocs.begin() + i);
       break;
     }
-  if (c->release_fn)
+  if (c->release_fn) {
+    // A caller's allocator may hand the block out again at once (the packed
+    // arena does), while launches already enqueued on the context's stream
+    // (a batch work list, a graph replay) may still read it; cudaFree waits
+    // by itself, a release callback does not.
+    cudaStreamSynchronize(c->stream);
     c->release_fn(p, c->alloc_user);
-  else
+  } else {
     cudaFree(p);
+  }
 }
 
 void drop_graphs(lb_ctx *c) {
@@ -190,6 +200,115 @@ unsigned face_mask(const int32_t (&k)[3][2], int kind) {
       if (k[a][s] == kind) m |= 1u << (2 * a + s);
   return m;
 }
+
+const StorageOps *ops_of(int storage) {
+  switch (storage) {
+    case LB_STORE_FP32: return &ops_f32();
+    case LB_STORE_FP64: return &ops_f64();
+    case LB_STORE_FP16DEV: return &ops_f16();
+    case LB_STORE_BF16DEV: return &ops_bf16();
+    default: return nullptr;
+  }
+}
+
+// Launch shape of the per-cell step kernel: rows of BX threads (a multiple
+// of 32, up to the lattice width), BY rows per block.
+void cell_shape(const lb_domain &dom, dim3 *grid, dim3 *block) {
+  unsigned bx = 32;
+  while (bx < unsigned(STEP_BLOCK) && bx < unsigned(dom.nx)) bx *= 2;
+  *block = dim3(bx, STEP_BLOCK / bx, 1);
+  *grid = dim3((dom.nx + bx - 1) / bx, (dom.ny + block->y - 1) / block->y, dom.nz);
+}
+
+// Flux slots: one pair per warp of the widest launch any step kernel may
+// take. The per-cell kernel's launches over every row width bound the
+// others: the row-pipelined grid has at most ny nz blocks of nx/32 warps, and
+// the row-staged grid with rows of bx threads at most ceil(nx/bx) ny nz
+// blocks of bx/32 warps, which the per-cell launch with rows of bx covers.
+unsigned slot_warps(const lb_domain &dom) {
+  unsigned w = 0;
+  for (unsigned bx = 32; bx <= unsigned(STEP_BLOCK); bx *= 2) {
+    const unsigned by = STEP_BLOCK / bx;
+    w = std::max(w, ((dom.nx + bx - 1) / bx) * ((dom.ny + by - 1) / by) * dom.nz *
+                        (STEP_BLOCK / 32));
+  }
+  return w;
+}
+
+// Device memory of one lattice, block by block, as lb_create and lb_init
+// allocate it; one function, so that lb_bytes_required reports what the
+// allocation does. k_rows: rows of K^-1 kept (0, 3 diagonal, 6 full tensor).
+struct Layout {
+  size_t f, h, rf, rh;   // per population buffer (two of each; 0 = not allocated)
+  size_t vel, spec;      // several species
+  size_t eps, link, fields, partials, state, geps, rhohat, face;
+  size_t fs_type, fs_mass, fs_lam, fs_share, fs_mom, fs_flag, fs_any, fs_tiles, fs_ntiles,
+      fs_stamp, fs_stamp_ctr;
+  size_t kinv, flux_slots;
+  size_t create_stage;   // inputs of lb_create, released before it returns
+  size_t init_stage;     // inputs of lb_init, kept for later staging
+  size_t batch_share;    // this lattice's part of a batch work list (lb_step_batch)
+};
+
+Layout layout_of(const lb_domain &dom, const lb_params &prm, const StorageOps &ops, int k_rows,
+                 bool f_scale) {
+  Layout L{};
+  const size_t N = size_t(dom.nx) * dom.ny * dom.nz;
+  const size_t rb = ops.fp64 ? 8 : 4;
+  const size_t pb = size_t(Q) * N * ops.elt_bytes;
+  const bool shift = (prm.storage == LB_STORE_FP16DEV || prm.storage == LB_STORE_BF16DEV);
+  const bool solute = prm.solute != 0;
+  const size_t S = solute ? size_t(std::max(1, int(prm.species))) : 1;
+  const bool paired = shift && solute;
+  // species held in the h buffers (the paired layout keeps species 0 with f)
+  const size_t Sh = solute ? S - (paired ? 1 : 0) : 0;
+  L.f = paired ? 2 * pb : pb;
+  L.h = Sh * pb;
+  // a float per cell, or the __half2 reference pair of the paired layout
+  L.rf = shift ? N * sizeof(float) : 0;
+  L.rh = (shift && Sh) ? S * N * sizeof(float) : 0;
+  if (solute && S > 1) {
+    L.vel = 6 * N * rb;
+    L.spec = 24 * rb;
+  }
+  L.eps = N * rb;
+  L.link = N * 4;
+  L.fields = (5 + S) * N * sizeof(float);  // rho, u (3), C, nu, then C of species 1 .. S-1
+  const size_t nblk = (N + BLOCK - 1) / BLOCK;
+  L.partials = nblk * 4 * sizeof(double);
+  L.state = sizeof(DevState);
+  L.geps = solute ? 3 * N * rb : 0;
+  L.rhohat = (prm.A != 0.0 || prm.free_surface) ? N * rb : 0;
+  L.face = 30 * rb;
+  if (prm.free_surface) {
+    const size_t ntiles = size_t((unsigned(dom.nx) + FS_TX - 1) / FS_TX) *
+                          ((unsigned(dom.ny) + FS_TY - 1) / FS_TY) *
+                          ((unsigned(dom.nz) + FS_TZ - 1) / FS_TZ);
+    L.fs_type = N;
+    L.fs_mass = N * rb;
+    L.fs_lam = N * rb;
+    L.fs_share = N * rb;
+    L.fs_mom = 4 * N * rb;
+    L.fs_flag = N;
+    L.fs_any = sizeof(unsigned);
+    L.fs_tiles = ntiles * sizeof(uint32_t);
+    L.fs_ntiles = 2 * sizeof(unsigned);
+    L.fs_stamp = ntiles * sizeof(unsigned);
+    L.fs_stamp_ctr = sizeof(unsigned);
+  }
+  L.kinv = size_t(k_rows) * N * rb;
+  L.flux_slots = size_t(slot_warps(dom)) * 2 * S * sizeof(double);
+  L.create_stage = N * 4 + (k_rows ? 6 * N * 4 : 0) + N + 64 + 256;
+  L.init_stage = N * 4 * (4 + S) + (f_scale ? size_t(Q) * N * 4 : 0) + N * 4 + N + 256;
+  dim3 g, b;
+  cell_shape(dom, &g, &b);
+  L.batch_share = size_t(g.x) * g.y * g.z * sizeof(uint64_t);
+  return L;
+}
+
+// Bytes of a block as a caller's allocator with 256-byte granules (the
+// packed arena) accounts for it; dev_alloc takes at least 16 bytes.
+size_t granule(size_t b) { return b == 0 ? 0 : (std::max<size_t>(b, 16) + 255) / 256 * 256; }
 
 template <class Real>
 void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
@@ -284,7 +403,7 @@ bool pipe_shape(const lb_ctx *c, unsigned bx, lb_ctx::PipeShape *ps) {
   ps->items = ps->gxr * unsigned(c->dom.ny) * unsigned(c->dom.nz);
   ps->grid = std::min(ps->items, unsigned(bps) * unsigned(sms));
   ps->smem = smem;
-  return true;
+  return ps->grid * (bx / 32) <= c->nwarps;  // within the flux slots (always, by slot_warps)
 }
 
 // Free-surface arguments of the step that brings the state to step index t
@@ -456,6 +575,33 @@ int lb_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, voi
   return LB_OK;
 }
 
+int lb_bytes_required(const lb_domain *dom, const lb_params *prm, int32_t k_rows,
+                      int32_t f_scale, size_t *bytes) {
+  if (!dom || !prm || !bytes) return fail(nullptr, LB_EINVAL, "domain, params and bytes are required");
+  *bytes = 0;
+  if (dom->nx < 1 || dom->ny < 1 || dom->nz < 1)
+    return fail(nullptr, LB_EINVAL, "lattice size out of range");
+  if (k_rows != 0 && k_rows != 3 && k_rows != 6)
+    return fail(nullptr, LB_EINVAL, "k_rows must be 0, 3 or 6");
+  const StorageOps *ops = ops_of(prm->storage);
+  if (!ops) return fail(nullptr, LB_EINVAL, "storage");
+  if (prm->species < 0 || prm->species > LB_MAX_SPECIES)
+    return fail(nullptr, LB_EINVAL, "species outside [0, LB_MAX_SPECIES]");
+  const Layout L = layout_of(*dom, *prm, *ops, k_rows, f_scale != 0);
+  const size_t twice[] = {L.f, L.h, L.rf, L.rh, L.fs_type, L.fs_mass, L.fs_flag, L.fs_tiles};
+  const size_t once[] = {L.vel, L.spec, L.eps, L.link, L.fields, L.partials, L.state, L.geps,
+                         L.rhohat, L.face, L.fs_lam, L.fs_share, L.fs_mom, L.fs_any,
+                         L.fs_ntiles, L.fs_stamp, L.fs_stamp_ctr, L.kinv, L.flux_slots,
+                         L.batch_share};
+  size_t total = 0;
+  for (size_t b : twice) total += 2 * granule(b);
+  for (size_t b : once) total += granule(b);
+  // the creation inputs are released before lb_init takes its staging block
+  total += std::max(granule(L.create_stage), granule(L.init_stage));
+  *bytes = total;
+  return LB_OK;
+}
+
 int lb_create(const lb_domain *dom, const float *porosity, const float *K6, const uint8_t *solid,
               const lb_params *prm, lb_ctx **out) {
   if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
@@ -496,14 +642,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
                 "pressure / velocity faces with a free surface or surface tension");
   if (prm->check_every < 0) return fail(nullptr, LB_EINVAL, "check_every < 0");
   if (prm->kernel < 0 || prm->kernel > 3) return fail(nullptr, LB_EINVAL, "kernel");
-  const StorageOps *ops = nullptr;
-  switch (prm->storage) {
-    case LB_STORE_FP32: ops = &ops_f32(); break;
-    case LB_STORE_FP64: ops = &ops_f64(); break;
-    case LB_STORE_FP16DEV: ops = &ops_f16(); break;
-    case LB_STORE_BF16DEV: ops = &ops_bf16(); break;
-    default: return fail(nullptr, LB_EINVAL, "storage");
-  }
+  const StorageOps *ops = ops_of(prm->storage);
+  if (!ops) return fail(nullptr, LB_EINVAL, "storage");
   if (prm->free_surface && !ops->fs_step)
     return fail(nullptr, LB_EUNSUPPORTED, "free surface is not built for this storage");
 
@@ -523,21 +663,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   }
   c->N = unsigned(N64);
   c->nblk = (c->N + BLOCK - 1) / BLOCK;
-  {
-    // step kernel: rows of BX threads (a multiple of 32), BY rows per block
-    unsigned bx = 32;
-    while (bx < unsigned(STEP_BLOCK) && bx < unsigned(dom->nx)) bx *= 2;
-    c->sblock = dim3(bx, STEP_BLOCK / bx, 1);
-    c->sgrid = dim3((dom->nx + bx - 1) / bx, (dom->ny + c->sblock.y - 1) / c->sblock.y, dom->nz);
-    c->nwarps = c->sgrid.x * c->sgrid.y * c->sgrid.z * (STEP_BLOCK / 32);
-    // flux slots for every launch shape the autotuner may pick
-    for (unsigned cbx = 32; cbx <= unsigned(STEP_BLOCK); cbx *= 2) {
-      const unsigned cby = STEP_BLOCK / cbx;
-      const unsigned w = ((dom->nx + cbx - 1) / cbx) * ((dom->ny + cby - 1) / cby) * dom->nz *
-                         (STEP_BLOCK / 32);
-      c->nwarps = std::max(c->nwarps, w);
-    }
-  }
+  cell_shape(*dom, &c->sgrid, &c->sblock);
+  c->nwarps = slot_warps(*dom);  // flux slots for every launch shape the autotuner may pick
   c->solute = prm->solute != 0;
   c->fs = prm->free_surface != 0;
   c->f_wall = face_mask(dom->bc, LB_BC_WALL);
@@ -557,25 +684,18 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   };
   const size_t N = c->N;
   const size_t rb = ops->fp64 ? 8 : 4;
-  const size_t pb = size_t(Q) * N * ops->elt_bytes;
-  // device memory
+  // device memory, block by block as layout_of lists it
+  const Layout L = layout_of(*dom, *prm, *ops, K6 ? 6 : 0, false);
   const bool shift = (prm->storage == LB_STORE_FP16DEV || prm->storage == LB_STORE_BF16DEV);
   c->S = c->solute ? std::max(1, int(prm->species)) : 0;
-  const size_t S = size_t(std::max(c->S, 1));
   c->paired = shift && c->solute;
-  // species held in the h buffers (the paired layout keeps species 0 with f)
-  const size_t Sh = c->solute ? S - (c->paired ? 1 : 0) : 0;
   for (int b = 0; b < 2; ++b) {
-    if (!(c->f[b] = dev_alloc(c, c->paired ? 2 * pb : pb)))
-      return bail(fail(c, LB_ENOMEM, "populations f"));
-    if (Sh && !(c->h[b] = dev_alloc(c, Sh * pb))) return bail(fail(c, LB_ENOMEM, "populations h"));
-    if (shift) {
-      // a float per cell, or the __half2 reference pair of the paired layout
-      c->rf[b] = static_cast<float *>(dev_alloc(c, N * sizeof(float)));
-      if (!c->rf[b]) return bail(fail(c, LB_ENOMEM, "references"));
-      if (Sh && !(c->rh[b] = static_cast<float *>(dev_alloc(c, S * N * sizeof(float)))))
-        return bail(fail(c, LB_ENOMEM, "references"));
-    }
+    if (!(c->f[b] = dev_alloc(c, L.f))) return bail(fail(c, LB_ENOMEM, "populations f"));
+    if (L.h && !(c->h[b] = dev_alloc(c, L.h))) return bail(fail(c, LB_ENOMEM, "populations h"));
+    if (L.rf && !(c->rf[b] = static_cast<float *>(dev_alloc(c, L.rf))))
+      return bail(fail(c, LB_ENOMEM, "references"));
+    if (L.rh && !(c->rh[b] = static_cast<float *>(dev_alloc(c, L.rh))))
+      return bail(fail(c, LB_ENOMEM, "references"));
   }
   if (c->S > 1) {
     double sv[24] = {};
@@ -586,7 +706,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
       sv[8 + sp] = sp ? prm->species_C_in[sp] : prm->C_in;
       sv[16 + sp] = ((tD - 0.5) / 3.0) / D0;
     }
-    if (!(c->vel = dev_alloc(c, 6 * N * rb)) || !(c->spec = dev_alloc(c, 24 * rb)))
+    if (!(c->vel = dev_alloc(c, L.vel)) || !(c->spec = dev_alloc(c, L.spec)))
       return bail(fail(c, LB_ENOMEM, "species"));
     float sf[24];
     for (int i = 0; i < 24; ++i) sf[i] = float(sv[i]);
@@ -596,16 +716,15 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     if (e != cudaSuccess)
       return bail(fail(c, LB_ECUDA, std::string("species values: ") + cudaGetErrorString(e)));
   }
-  c->eps = dev_alloc(c, N * rb);
-  c->link = static_cast<uint32_t *>(dev_alloc(c, N * 4));
-  // rho, u (3), C, nu, then C of species 1 .. S-1
-  c->fields = static_cast<float *>(dev_alloc(c, (5 + S) * N * sizeof(float)));
-  c->partials = static_cast<double *>(dev_alloc(c, size_t(c->nblk) * 4 * sizeof(double)));
-  c->state = static_cast<DevState *>(dev_alloc(c, sizeof(DevState)));
+  c->eps = dev_alloc(c, L.eps);
+  c->link = static_cast<uint32_t *>(dev_alloc(c, L.link));
+  c->fields = static_cast<float *>(dev_alloc(c, L.fields));
+  c->partials = static_cast<double *>(dev_alloc(c, L.partials));
+  c->state = static_cast<DevState *>(dev_alloc(c, L.state));
   if (!c->eps || !c->link || !c->fields || !c->partials || !c->state)
     return bail(fail(c, LB_ENOMEM, "static fields"));
-  if (c->solute && !(c->geps = dev_alloc(c, 3 * N * rb))) return bail(fail(c, LB_ENOMEM, "geps"));
-  if ((prm->A != 0.0 || c->fs) && !(c->rhohat = dev_alloc(c, N * rb)))
+  if (L.geps && !(c->geps = dev_alloc(c, L.geps))) return bail(fail(c, LB_ENOMEM, "geps"));
+  if (L.rhohat && !(c->rhohat = dev_alloc(c, L.rhohat)))
     return bail(fail(c, LB_ENOMEM, "rhohat"));
   {
     // per-face values: 3 x pressure (the face density over eps), velocity,
@@ -618,7 +737,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
       for (int i = 0; i < 3; ++i) fv[6 + 3 * f + i] = prm->face_u[f / 2][f % 2][i];
       if (rb == 4) fv[24 + f] = fv[f] - double(float(fv[f]));
     }
-    if (!(c->face = dev_alloc(c, 30 * rb))) return bail(fail(c, LB_ENOMEM, "face values"));
+    if (!(c->face = dev_alloc(c, L.face))) return bail(fail(c, LB_ENOMEM, "face values"));
     float ff[30];
     for (int i = 0; i < 30; ++i) ff[i] = float(fv[i]);
     cudaError_t e = cudaMemcpyAsync(c->face, rb == 8 ? static_cast<const void *>(fv) : ff,
@@ -629,25 +748,25 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   }
   if (c->fs) {
     for (int b = 0; b < 2; ++b) {
-      c->type[b] = static_cast<uint8_t *>(dev_alloc(c, N));
-      c->mass[b] = dev_alloc(c, N * rb);
+      c->type[b] = static_cast<uint8_t *>(dev_alloc(c, L.fs_type));
+      c->mass[b] = dev_alloc(c, L.fs_mass);
       if (!c->type[b] || !c->mass[b]) return bail(fail(c, LB_ENOMEM, "free surface"));
     }
-    c->lam = dev_alloc(c, N * rb);
-    c->share = dev_alloc(c, N * rb);
-    c->mom = dev_alloc(c, 4 * N * rb);
-    c->flag_a = static_cast<uint8_t *>(dev_alloc(c, N));
-    c->flag_b = static_cast<uint8_t *>(dev_alloc(c, N));
-    c->any = static_cast<unsigned *>(dev_alloc(c, sizeof(unsigned)));
+    c->lam = dev_alloc(c, L.fs_lam);
+    c->share = dev_alloc(c, L.fs_share);
+    c->mom = dev_alloc(c, L.fs_mom);
+    c->flag_a = static_cast<uint8_t *>(dev_alloc(c, L.fs_flag));
+    c->flag_b = static_cast<uint8_t *>(dev_alloc(c, L.fs_flag));
+    c->any = static_cast<unsigned *>(dev_alloc(c, L.fs_any));
     c->ntx = (unsigned(dom->nx) + FS_TX - 1) / FS_TX;
     c->nty = (unsigned(dom->ny) + FS_TY - 1) / FS_TY;
     c->ntz = (unsigned(dom->nz) + FS_TZ - 1) / FS_TZ;
     const size_t ntiles = size_t(c->ntx) * c->nty * c->ntz;
-    c->tiles[0] = static_cast<uint32_t *>(dev_alloc(c, ntiles * sizeof(uint32_t)));
-    c->tiles[1] = static_cast<uint32_t *>(dev_alloc(c, ntiles * sizeof(uint32_t)));
-    c->n_tiles = static_cast<unsigned *>(dev_alloc(c, 2 * sizeof(unsigned)));
-    c->stamp = static_cast<unsigned *>(dev_alloc(c, ntiles * sizeof(unsigned)));
-    c->stamp_ctr = static_cast<unsigned *>(dev_alloc(c, sizeof(unsigned)));
+    c->tiles[0] = static_cast<uint32_t *>(dev_alloc(c, L.fs_tiles));
+    c->tiles[1] = static_cast<uint32_t *>(dev_alloc(c, L.fs_tiles));
+    c->n_tiles = static_cast<unsigned *>(dev_alloc(c, L.fs_ntiles));
+    c->stamp = static_cast<unsigned *>(dev_alloc(c, L.fs_stamp));
+    c->stamp_ctr = static_cast<unsigned *>(dev_alloc(c, L.fs_stamp_ctr));
     if (!c->lam || !c->share || !c->mom || !c->flag_a || !c->flag_b || !c->any || !c->tiles[0] ||
         !c->tiles[1] || !c->n_tiles || !c->stamp || !c->stamp_ctr)
       return bail(fail(c, LB_ENOMEM, "free surface"));
@@ -661,7 +780,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   }
   // inputs -> device (caller pointers may be host or device)
   const size_t in_bytes = N * 4 + (K6 ? 6 * N * 4 : 0) + N + 64;
-  char *in = static_cast<char *>(dev_alloc(c, in_bytes + 256));
+  char *in = static_cast<char *>(dev_alloc(c, L.create_stage));  // in_bytes + 256
   if (!in) return bail(fail(c, LB_ENOMEM, "staging"));
   float *eps_in = reinterpret_cast<float *>(in);
   float *K_in = K6 ? eps_in + N : nullptr;
@@ -702,7 +821,8 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
   if (c->kmode == KM_SPD && prm->forchheimer != 0.0)
     return bail(fail(c, LB_EUNSUPPORTED, "Forchheimer drag needs a diagonal permeability tensor"));
   if (c->kmode == KM_DIAG && prm->forchheimer != 0.0) c->kmode = KM_FORCH;
-  if (K6 && !(c->kinv = dev_alloc(c, (c->kmode == KM_SPD ? 6 : 3) * N * rb)))
+  if (K6 && !(c->kinv = dev_alloc(c, layout_of(*dom, *prm, *ops, c->kmode == KM_SPD ? 6 : 3,
+                                                 false).kinv)))
     return bail(fail(c, LB_ENOMEM, "K inverse"));
   // row-pipelined kernel: eligible shapes only; grid = resident blocks of all SMs
   // (automatic selection keeps the per-cell kernel: on GB300 at 128^3 it is
@@ -715,28 +835,20 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
       const unsigned rows = unsigned(dom->ny) * unsigned(dom->nz);
       c->tma_grid = std::min(rows, unsigned(bps) * unsigned(sms));
-      c->tma_ok = true;
-      c->use_tma = prm->kernel == 2;
-      c->nwarps = std::max(c->nwarps, c->tma_grid * unsigned(dom->nx / 32));
+      // the flux slots cover its warps (slot_warps bounds every launch shape)
+      c->tma_ok = c->tma_grid * unsigned(dom->nx / 32) <= c->nwarps;
+      c->use_tma = c->tma_ok && prm->kernel == 2;
     }
     cudaGetLastError();
   }
   if (prm->kernel == 2 && !c->use_tma)
     return bail(fail(c, LB_EUNSUPPORTED, "row-pipelined kernel: this lattice shape or storage"));
-  // row-staged kernel: flux slots for every row width it may run with
-  if (!c->fs && ops->pipe_config) {
-    for (unsigned bx = 32; bx <= unsigned(STEP_BLOCK); bx *= 2) {
-      lb_ctx::PipeShape ps;
-      if (pipe_shape(c, bx, &ps)) c->nwarps = std::max(c->nwarps, ps.grid * (bx / 32));
-    }
-  }
   if (prm->kernel == 3) {
     const unsigned bx = c->sblock.x;
     if (c->fs || !ops->pipe_config || !pipe_shape(c, bx, &c->pipe))
       return bail(fail(c, LB_EUNSUPPORTED, "row-staged kernel: this lattice or storage"));
   }
-  c->flux_slots = static_cast<double *>(
-      dev_alloc(c, size_t(c->nwarps) * 2 * size_t(std::max(c->S, 1)) * sizeof(double)));
+  c->flux_slots = static_cast<double *>(dev_alloc(c, L.flux_slots));
   if (!c->flux_slots) return bail(fail(c, LB_ENOMEM, "flux slots"));
   sa.eps = c->eps;
   sa.kinv = c->kinv;
@@ -776,7 +888,7 @@ int lb_init(lb_ctx *c, const float *rho0, const float *u0, const float *C0,
   if (c->fs && !cell_type) return fail(c, LB_EINVAL, "cell_type is required with a free surface");
   const size_t N = c->N;
   const size_t S = size_t(std::max(c->S, 1));  // C0: N values per species
-  const size_t bytes = N * 4 * (4 + S) + (f_scale ? size_t(Q) * N * 4 : 0) + N * 4 + N + 256;
+  const size_t bytes = layout_of(c->dom, c->prm, *c->ops, 0, f_scale != nullptr).init_stage;
   char *st = static_cast<char *>(stage(c, bytes));
   if (!st) return fail(c, LB_ENOMEM, "staging");
   float *d_rho = reinterpret_cast<float *>(st);

@@ -20,6 +20,10 @@ struct PopView {
   int ref_pair;
 };
 
+// Record the message of a failed call that has no context; lb_last_error(NULL)
+// returns it on the same thread.
+void set_noctx_error(const char *msg);
+
 // The totals kernel runs at most this many blocks (grid-stride over the
 // cells), so the fixed-order finish sums few partials.
 constexpr unsigned TOTALS_BLOCKS = 1024;

@@ -15,12 +15,12 @@
 
 #include "../../include/lb.h"
 #include "lb_kernels.cuh"
+#include "lb_ops.h"
 
 namespace {
 
 using namespace lbgb;
 
-thread_local std::string g_noctx_error;  // kept for debugging; the status code is the result
 
 // Largest lattice accepted: 2^24 cells (256^3), i.e. 65536 blocks of 256
 // cells. The array holds two partial sums per block and the two totals:
@@ -38,8 +38,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double *g_scratch_ptr[kMaxDevices] = {};
 
+// the message is read back by lb_last_error(NULL) on the calling thread
 int set_error(int code, const std::string &msg) {
-  g_noctx_error = msg;
+  set_noctx_error(msg.c_str());
   return code;
 }
 

@@ -31,7 +31,8 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_set_populations", "lb_ge
            "lb_sync", "lb_time", "lb_last_error", "lb_destroy", "lb_set_allocator",
            "lb_totals_noalloc", "lb_step_batch", "lb_autotune", "lb_debug_wait_timeout",
            "lb_species_state", "lb_set_graphs", "lb_debug_graphs", "lb_arena_create",
-           "lb_arena_destroy", "lb_arena_use", "lb_arena_alloc", "lb_arena_free", "lb_arena_stats"]
+           "lb_arena_destroy", "lb_arena_use", "lb_arena_alloc", "lb_arena_free", "lb_arena_stats",
+           "lb_bytes_required"]
 
 
 class LbError(RuntimeError):
@@ -106,6 +107,8 @@ def load() -> ctypes.CDLL:
     L.lb_arena_free.argtypes = [vp, vp]
     L.lb_arena_free.restype = None
     L.lb_arena_stats.argtypes = [vp] * 5
+    L.lb_bytes_required.argtypes = [POINTER(lb_domain), POINTER(lb_params), c_int32, c_int32,
+                                    POINTER(c_size_t)]
     _lib = L
     return L
 
@@ -245,13 +248,21 @@ def lb_destroy(ctx):
     load().lb_destroy(ctx)
 
 
+def lb_bytes_required(domain: lb_domain, params: lb_params, k_rows: int, f_scale: bool = False) -> int:
+    """Device bytes one lattice takes, from the library's own allocation
+    layout (k_rows: 0 without K, 3 diagonal, 6 full tensor or unknown)."""
+    out = c_size_t()
+    _check(load().lb_bytes_required(ctypes.byref(domain), ctypes.byref(params), int(k_rows),
+                                    1 if f_scale else 0, ctypes.byref(out)), None)
+    return out.value
+
+
 def lb_totals_noalloc(f, h, solid, n_cells: int, out, stream_handle: int = 0):
     """FP64 (mass, solute) of caller-owned device arrays without any device
     allocation (see include/lb.h); out receives 2 doubles."""
     rc = load().lb_totals_noalloc(_ptr(f, _F32), _ptr(h, _F32), _ptr(solid, _U8), int(n_cells),
                                   _ptr(out, _F64), c_void_p(stream_handle))
-    if rc != LB_OK:
-        raise LbError(rc, "lb_totals_noalloc failed")
+    _check(rc, None)
 
 
 # every callback pair ever installed stays referenced: a context keeps the

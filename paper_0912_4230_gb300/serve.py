@@ -15,6 +15,7 @@ library; tests of the host-side logic use a fake backend on the CPU.
 """
 from __future__ import annotations
 
+import collections
 import dataclasses
 import threading
 import time
@@ -22,31 +23,21 @@ from typing import Callable, List, Optional
 
 import numpy as np
 
-Q = 19
-ELT = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}
 
 
-def device_bytes(nx: int, ny: int, nz: int, storage: str = "fp32", solute: bool = True,
-                 kmode_rows: int = 3) -> int:
-    """Peak device memory of one lattice as the library allocates it: two
-    population buffers per lattice (16-bit storage: plus a 32-bit reference
-    per cell and buffer), static fields, exported fields, flux slots and
-    per-block partial sums, and the larger of the two staging buffers (the
-    creation inputs, porosity + six K components + solid mask, are released
-    before the initialisation inputs take their place), each of the about 20
-    allocations rounded up to 256 bytes. kmode_rows: 0 without K, 3 diagonal,
-    6 full tensor."""
-    N = nx * ny * nz
-    lattices = 2 if solute else 1
-    pops = lattices * 2 * Q * N * ELT[storage]
-    refs = 2 * 4 * N if storage in ("fp16", "bf16") else 0
-    real = 8 if storage == "fp64" else 4
-    static = N * real * (1 + kmode_rows + (3 if solute else 0)) + 4 * N
-    fields = 6 * N * 4
-    stage_create = 4 * N + (24 * N if kmode_rows else 0) + N + 320
-    stage_init = 6 * N * 4 + N + 256
-    slots = (N // 256 + 1) * 8 * 2 * 8 + (N // 256 + 1) * 4 * 8
-    return int(pops + refs + static + fields + max(stage_create, stage_init) + slots + 24 * 256)
+def device_bytes(prob, storage: str = "fp32") -> int:
+    """Device memory one lattice of this problem takes, as the library
+    allocates it (lb_bytes_required: the library's own allocation layout,
+    each block in the packed arena's 256-byte granules, the larger of the
+    creation and initialisation staging, and the lattice's share of a batch
+    work list). A permeability field keeps 6 rows of K^-1 when any cell has
+    an off-diagonal entry, else 3."""
+    from . import lb
+    kr = 0
+    if prob.K6 is not None:
+        kr = 6 if np.any(np.asarray(prob.K6).reshape(-1, 6)[:, 3:] != 0) else 3
+    return lb.lb_bytes_required(lb.make_domain(prob), lb.make_params(prob, storage), kr,
+                                prob.f_scale is not None)
 
 
 @dataclasses.dataclass
@@ -90,11 +81,7 @@ class LibraryBackend:
         self.step_stream = step_stream
 
     def bytes(self, prob) -> int:
-        kr = 0
-        if prob.K6 is not None:      # the library keeps 6 rows of K^-1 for a full tensor
-            kr = 6 if np.any(np.asarray(prob.K6).reshape(-1, 6)[:, 3:] != 0) else 3
-        return device_bytes(prob.nx, prob.ny, prob.nz, self.storage,
-                            bool(prob.params.get("solute")), kr)
+        return device_bytes(prob, self.storage)
 
     def admit(self, prob):
         """Create and initialise a lattice (may run on a background thread).
@@ -128,13 +115,32 @@ class LibraryBackend:
             handle.ready_event = None
 
     def step(self, handles, n: int):
+        """Enqueue n steps of every handle; returns an event recorded after
+        them on the step stream (None without torch streams)."""
         if self.batched:
             self.lb.lb_step_batch([h.ctx for h in handles], n)
         else:
             for h in handles:   # the plain per-lattice path: one launch per lattice and step
                 h.step(n)
+        if self.step_stream is None:
+            return None
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(self.step_stream)
+        return ev
 
-    def finish(self, handle):
+    def finish(self, handle, after=None):
+        """Export (keep_fields) and release a finished lattice. With `after`
+        (the event of the chunk that finished it) the lattice moves to a
+        stream of its own that waits for that event, so the export and the
+        release wait for its own last step only, not for the chunks enqueued
+        for the other lattices since."""
+        if after is not None:
+            import torch
+            if not hasattr(self, "_finish_stream"):
+                self._finish_stream = torch.cuda.Stream()
+            self._finish_stream.wait_event(after)
+            self.lb.lb_set_stream(handle.ctx, self._finish_stream.cuda_stream)
         out = None
         if self.keep_fields:
             rho, u, C, nu = handle.fields()
@@ -168,6 +174,19 @@ class Server:
         self.sleep = sleep
         self.log: List[dict] = []
 
+    def _finish(self, finishing, finished, lock, t0):
+        for r, ev in finishing:
+            r.result = (self.backend.finish(r.handle, ev) if ev is not None
+                        else self.backend.finish(r.handle))
+            r.handle = None
+            r.done = self.clock() - t0
+            with lock:
+                self._used -= r.bytes
+                self._released += 1
+                lock.notify_all()
+            finished.append(r)
+        finishing.clear()
+
     def run(self, requests: List[Request]) -> dict:
         pending = sorted(requests, key=lambda r: (r.arrival, r.id))
         for r in pending:
@@ -177,6 +196,8 @@ class Server:
                 raise ValueError(f"request {r.id} needs {r.bytes} bytes, above the whole budget")
         active: List[Request] = []
         finished: List[Request] = []
+        finishing: List[tuple] = []   # (request, event of the chunk that finished it)
+        inflight = collections.deque()
         self._used = 0
         self._released = 0       # requests finished so far (wakes a waiting admission)
         self._admit_error = None
@@ -280,27 +301,32 @@ class Server:
                     if cells >= self.fill_cells:
                         break
             n = min(self.chunk, min(r.remaining for r in stepping))
-            self.backend.step([r.handle for r in stepping], n)
+            ev = self.backend.step([r.handle for r in stepping], n)
+            if ev is not None:
+                # at most two chunks queued ahead of the GPU, so that requests
+                # admitted meanwhile join soon
+                inflight.append(ev)
+                while len(inflight) > 2:
+                    inflight.popleft().synchronize()
             for r in stepping:
                 r.remaining -= n
                 lups += n * r.problem.N
+            # requests finished by an earlier chunk are exported and released
+            # now, after this chunk is enqueued, so the GPU has work while
+            # the host waits for them
+            self._finish(finishing, finished, lock, t0)
             still = []
             for r in active:
                 if r.remaining == 0:
-                    r.result = self.backend.finish(r.handle)
-                    r.handle = None
-                    r.done = self.clock() - t0
-                    with lock:
-                        self._used -= r.bytes
-                        self._released += 1
-                        lock.notify_all()
-                    finished.append(r)
+                    finishing.append((r, ev))
                 else:
                     still.append(r)
             self.log.append(dict(t=self.clock() - t0, resident=len(active), stepped=len(stepping),
                                  steps=n, used=self._used))
             with lock:
                 active[:] = still
+            if not still:
+                self._finish(finishing, finished, lock, t0)
         if admitter is not None:
             admitter.join()
         wall = self.clock() - t0

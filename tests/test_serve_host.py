@@ -92,10 +92,13 @@ def test_request_above_budget_is_refused():
 
 
 def test_device_bytes_scale():
-    b32 = serve.device_bytes(64, 64, 64, "fp32")
-    b16 = serve.device_bytes(64, 64, 64, "fp16")
+    """The library's size query, through the serving estimate: 16-bit storage
+    takes less than FP32 and more than half of it; a 128^3 lattice holds at
+    least its two FP32 buffers of f and h."""
+    p = W.miscible(64, 64, 64)
+    b32, b16 = serve.device_bytes(p, "fp32"), serve.device_bytes(p, "fp16")
     assert b16 < b32 < 2 * b16 + 64 ** 3 * 100
-    assert serve.device_bytes(128, 128, 128) > 600e6   # 2 x 2 x 19 x 4 B x 2.1M cells alone
+    assert serve.device_bytes(W.miscible(128, 128, 128)) > 2 * 2 * 19 * 4 * 128 ** 3
 
 
 def test_request_stream_matches_the_serving_workload():
@@ -245,15 +248,32 @@ def test_admission_thread_failure_ends_the_run():
 
 
 def test_device_bytes_counts_references_and_the_larger_staging():
-    """16-bit storage halves the populations but adds a 32-bit reference per
-    cell and buffer; a full permeability tensor adds three rows of K^-1; the
-    creation staging (with the six K components) outweighs the initialisation
-    staging whenever K is given."""
+    """The library's layout arithmetic (lb_bytes_required), checked block by
+    block against what each storage and permeability choice must add: 16-bit
+    storage halves the four population buffers of f and h and adds a 32-bit
+    reference pair per cell and buffer; a full permeability tensor keeps three
+    more rows of K^-1; without K the creation staging loses its six K rows,
+    and the initialisation staging (larger then) takes its place."""
+    from paper_0912_4230_gb300 import lb
     N = 32 ** 3
-    b32 = serve.device_bytes(32, 32, 32, "fp32")
-    b16 = serve.device_bytes(32, 32, 32, "fp16")
-    assert b32 - b16 == 2 * 2 * 19 * N * 2 - 8 * N
-    assert serve.device_bytes(32, 32, 32, "bf16") == b16
-    assert serve.device_bytes(32, 32, 32, "fp32", kmode_rows=6) - b32 == 3 * 4 * N
-    no_k = serve.device_bytes(32, 32, 32, "fp32", kmode_rows=0)
-    assert b32 - no_k == 3 * 4 * N + (29 * N + 320) - (25 * N + 256)
+    p = W.miscible(32, 32, 32)
+    dom = lb.make_domain(p)
+
+    def req(storage, k_rows):
+        return lb.lb_bytes_required(dom, lb.make_params(p, storage), k_rows)
+
+    def g(b):   # 256-byte granule
+        return -(-b // 256) * 256
+
+    b32, b16 = req("fp32", 3), req("fp16", 3)
+    assert b32 - b16 == 2 * (g(19 * N * 4 * 2) - g(19 * N * 2 * 2)) - 2 * g(4 * N)
+    assert req("bf16", 3) == b16
+    assert req("fp32", 6) - b32 == g(6 * 4 * N) - g(3 * 4 * N)
+    create = g(4 * N + 24 * N + N + 64 + 256)
+    init = g(4 * N * 5 + 4 * N + N + 256)
+    assert create > init
+    assert b32 - req("fp32", 0) == g(3 * 4 * N) + create - max(g(4 * N + N + 64 + 256), init)
+    assert req("fp64", 3) > b32 > b16
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_bytes_required(dom, lb.make_params(p, "fp32"), 4)
+    assert e.value.code == lb.LB_EINVAL and "k_rows" in lb.lb_last_error(None)

@@ -1,7 +1,8 @@
 """lb_totals_noalloc: the allocation-free variant of the totals behind
 lb_reduce, for callers that cannot allocate device memory where they need
-the totals. Checked through the C ABI against lb_reduce on the same state,
-twice in a row (the second call reuses the library's fixed scratch array).
+the totals. Checked through the C ABI against an FP64 host sum of the same
+device arrays and against lb_reduce on the same state, twice in a row (the
+second call reuses the library's fixed scratch array).
 Collected last so that a failure here leaves every other test already run.
 """
 import numpy as np
@@ -36,9 +37,18 @@ def test_noalloc_totals_match_lb_reduce_twice():
     live = p.solid == 0
     bound_m = 18 * 2.0 ** -24 * np.abs(f32[:, live]).sum()
     bound_s = 18 * 2.0 ** -24 * np.abs(h32[:, live]).sum()
+    # an independent check: the FP64 sum on the host of the same device
+    # arrays, copied back, every value widened as the call widens it. Both
+    # are FP64 sums of the same ~2e5 terms in different orders (tree sums of
+    # O(log n) depth): they agree to ~1e-14 of the sum of magnitudes.
+    fh = fd.cpu().numpy().reshape(19, p.N).astype(np.float64) + w[:, None]
+    hh = hd.cpu().numpy().reshape(19, p.N).astype(np.float64)
+    host_m, host_s = fh[:, live].sum(), hh[:, live].sum()
     for _ in range(2):
         out = np.zeros(2)
         lb.lb_totals_noalloc(fd, hd, sd, p.N, out, stream)
+        assert abs(out[0] - host_m) <= 1e-13 * np.abs(fh[:, live]).sum()
+        assert abs(out[1] - host_s) <= 1e-13 * np.abs(hh[:, live]).sum()
         assert abs(out[0] - mass) <= bound_m + 1e-13 * abs(mass)
         assert abs(out[1] - solute) <= bound_s + 1e-13 * abs(solute)
     # device output buffer, solid mask omitted (all cells counted)
@@ -53,6 +63,8 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(lb.LbError) as e:
         lb.lb_totals_noalloc(np.zeros(19, np.float32), None, None, (1 << 24) + 1, np.zeros(2))
     assert e.value.code == lb.LB_EINVAL
+    # the reason reaches the caller (lb_last_error(NULL) on this thread)
+    assert "16777216" in str(e.value) and "16777216" in lb.lb_last_error(None)
 
 
 def _weights():
