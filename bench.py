@@ -1,9 +1,12 @@
 """Benchmark of the coupled fluid + solute lattice-Boltzmann step on GB300.
 
 Workload: the miscible layered anisotropic medium, 128^3 cells, FP32
-population storage, solute inlet/outlet, linear hardening viscosity, FP64
-mass / solute / flux reductions every step (the fused per-cell update of
-the paper's Sections 2-4). One "step" = one lattice update of every cell.
+population storage, solute inlet/outlet, linear hardening viscosity (the
+fused per-cell update of the paper's Sections 2-4). Every step accumulates
+the inlet/outlet solute flux in FP64 and checks that each warp's mass and
+solute sums are finite; the FP64 mass and solute totals are formed by
+lb_reduce in the end-to-end leg. One "step" = one lattice update of every
+cell.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,9 +33,9 @@ sys.path.insert(0, ROOT)
 NX = NY = NZ = 128
 ALGO_BYTES_PER_LUP = 321  # f 152 + h 152 + eps 4 + K^-1 12 + solid mask 1 (FP32 storage)
 METRIC = "coupled LB MLUPS"
-WORKLOAD = ("miscible porous medium 128^3, D3Q19 fluid + D3Q19 solute, FP32 storage, "
-            "diagonal anisotropic K, linear hardening tau(C), inlet/outlet flux, "
-            "FP64 reductions every step")
+WORKLOAD = ("miscible porous medium 128^3, D3Q19 fluid + D3Q19 solute, diagonal anisotropic K, "
+            "linear hardening tau(C), solute inlet/outlet; every step: FP64 accumulation of the "
+            "inlet/outlet flux and a finite check of each warp's mass and solute sums")
 PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_miscible128_traffic.json")
 
 # Other workloads timed the same way (--workload); the default line is "miscible".
@@ -143,6 +146,82 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml,
+    read-only queries) as often as the host can while the timed launches run,
+    so that a timed region of a few milliseconds still has samples."""
+
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, index: int):
+        import ctypes
+        self.samples = []
+        self.ok = False
+        try:
+            L = ctypes.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if L.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+                return
+            self.L, self.ct = L, ctypes
+            self.reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(L, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            mx = ctypes.c_uint()
+            self.max_mhz = float(mx.value) if L.nvmlDeviceGetMaxClockInfo(
+                self.h, ctypes.c_int(1), ctypes.byref(mx)) == 0 else None
+            self.ok = True
+        except (OSError, AttributeError):
+            self.ok = False
+
+    def sample(self):
+        if not self.ok:
+            return
+        ct = self.ct
+        mhz, bits = ct.c_uint(), ct.c_ulonglong()
+        if (self.L.nvmlDeviceGetClockInfo(self.h, ct.c_int(1), ct.byref(mhz)) == 0 and
+                self.reasons_fn(self.h, ct.byref(bits)) == 0):
+            self.samples.append((float(mhz.value), int(bits.value)))
+
+    def summary(self):
+        if not self.samples:
+            return None
+        reasons = sorted({n for n, b in self.BITS.items() for _, r in self.samples if r & b})
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples),
+                "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(self.samples),
+                "source": "NVML during the timed region"}
+
+
+def clocks_record(nvml, smi):
+    """The line's clock record: NVML samples taken during the timed launches
+    when there are any, else nvidia-smi's over warm-up and timed region."""
+    s = nvml.summary() if nvml is not None else None
+    if s is None:
+        s = dict(smi.summary())
+        s["source"] = "nvidia-smi over warm-up and timed region"
+    elif s["sm_max_mhz"] is None:
+        s["sm_max_mhz"] = smi.summary().get("sm_max_mhz")
+    return s
+
+
+def nvml_index(local: int) -> int:
+    """NVML's index of this process's CUDA device (CUDA_VISIBLE_DEVICES may
+    renumber it)."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v.strip() for v in vis.split(",") if v.strip()]
+    if ids and all(v.isdigit() for v in ids) and local < len(ids):
+        return int(ids[local])
+    return local
+
+
+def workload_config(ws: int, workload: str, N: int, lattice, algo: int) -> dict:
+    """The config of a bench line; both arms print the same one."""
+    return {"workload": workload, "cells": N, "lattice": list(lattice),
+            "parallelism": f"replicas{ws}",
+            "l2": f"inputs larger than L2: {algo * N / 1e6:.0f} MB moved per step"}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -231,7 +310,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 * (NZ / nz),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "cells": NX * NY * NZ},
+        "data": "synthetic",
+        "config": workload_config(ws, WORKLOAD, NX * NY * NZ, (NX, NY, NZ), ALGO_BYTES_PER_LUP),
+        "arm": "FP64 CPU oracle (plain, cell by cell) on the host cores",
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -351,19 +432,22 @@ def main():
     if args.graphs == "off":
         lat.set_graphs(False)
     # one call, so that a CUDA graph of the step pair is captured before timing
-    lat.step(args.warmup)
-    torch.cuda.synchronize()
-
     K = args.steps
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(ws)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    nvml = NvmlClocks(nvml_index(local))
+    with ClockSampler(local) as clk:   # nvidia-smi over warm-up and the timed region
+        lat.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
         # K steps in one lb_step call: K launches of the step kernel (the
         # fields are exported by the last one only), nothing else on the stream
+        nvml.sample()
         start.record(stream)
         lat.step(K)
         stop.record(stream)
+        while not stop.query():       # NVML samples while the launches run
+            nvml.sample()
         torch.cuda.synchronize()
     barrier(ws)
     total_ms = start.elapsed_time(stop)
@@ -396,8 +480,11 @@ def main():
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
     e2e_val = ws * N * args.e2e_inner * args.e2e_iters / e2e_s / 1e6
-    h2d = (5 if C0 is not None else 4) * N * 4 + (N * 5 if ctype is not None else 0)
-    d2h = 6 * N * 4 + 2 * 8 + 48
+    # copies of one end-to-end iteration (inputs up, fields and totals down),
+    # reported per lattice step of it
+    h2d_iter = (5 if C0 is not None else 4) * N * 4 + (N * 5 if ctype is not None else 0)
+    d2h_iter = 6 * N * 4 + 4 * 8
+    h2d, d2h = h2d_iter / args.e2e_inner, d2h_iter / args.e2e_inner
 
     peak, peak_kind = measured_peaks()
     species = int(prob.params.get("species", 1))
@@ -428,9 +515,8 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)",
                   "bf16": "f32 (bf16 storage)"}[storage], "data": "synthetic",
-        "config": {"workload": workload, "cells": N, "lattice": [prob.nx, prob.ny, prob.nz],
-                   "parallelism": f"replicas{ws}", "cuda_graphs": args.graphs,
-                   "l2": f"inputs larger than L2: {algo * N / 1e6:.0f} MB moved per step"},
+        "config": workload_config(ws, workload, N, (prob.nx, prob.ny, prob.nz), algo),
+        "storage": storage, "cuda_graphs": args.graphs,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind,
@@ -448,9 +534,11 @@ def main():
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "step": f"lb_init from pinned host fields + {args.e2e_inner} lattice steps + "
-                        f"lb_fields to pinned host + lb_reduce"},
+                        f"lb_fields to pinned host + lb_reduce; bytes per lattice step (one "
+                        f"iteration's {h2d_iter} B up and {d2h_iter} B down over its "
+                        f"{args.e2e_inner} steps)"},
         "gpu_launches": K * launches_per_step,
-        "clocks": clk.summary(),
+        "clocks": clocks_record(nvml, clk),
     }
     print(json.dumps(line), flush=True)
     lat.close()

@@ -20,6 +20,7 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 import subprocess
 import sys
@@ -56,13 +57,24 @@ class OrcParams(ctypes.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP, no intrinsics)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "lb_oracle.h"))):
-        return _SO
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", "{out}", "-lm"]
+    # rebuilt unless the hash of the sources and the command recorded beside
+    # the library matches (file times are not trusted)
+    h = hashlib.sha256(" ".join(cmd).encode())
+    for p in (_SRC, os.path.join(_HERE, "lb_oracle.h")):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    digest, stamp = h.hexdigest(), _SO + ".sha256"
+    if not force and os.path.exists(_SO) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == digest:
+                return _SO
     tmp = _SO + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    subprocess.run([tmp if a == "{out}" else a for a in cmd], check=True)
     os.replace(tmp, _SO)
+    with open(stamp + f".{os.getpid()}.tmp", "w") as fh:
+        fh.write(digest + "\n")
+    os.replace(stamp + f".{os.getpid()}.tmp", stamp)
     return _SO
 
 

@@ -7,6 +7,7 @@ shared library that exports the C ABI of ``include/lb.h``. Run as a script
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import subprocess
 import sys
@@ -30,10 +31,21 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _deps_mtime() -> float:
-    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+def source_hash() -> str:
+    """SHA-256 over every file the library is compiled from (the CUDA sources
+    and headers, the C ABI header) and the compile flags: the build reuses an
+    existing library only when the hash recorded beside it matches, never on
+    file times (a library copied in with the tree is rebuilt)."""
+    h = hashlib.sha256()
+    h.update(" ".join(ARCH + FLAGS + SOURCES).encode())
+    paths = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                   if f.endswith((".cu", ".cuh", ".h")))
     paths.append(os.path.join(ROOT, "include", "lb.h"))
-    return max(os.path.getmtime(p) for p in paths)
+    for p in paths:
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -42,8 +54,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if missing:
         raise FileNotFoundError(f"CUDA sources missing from {CSRC}: {', '.join(missing)}")
     srcs = list(SOURCES)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
+    digest = source_hash()
+    stamp = LIB + ".sha256"
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == digest:
+                return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(OBJ_DIR, exist_ok=True)
     nvcc = _nvcc()
@@ -69,6 +85,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp + f".{os.getpid()}.tmp", "w") as fh:
+        fh.write(digest + "\n")
+    os.replace(stamp + f".{os.getpid()}.tmp", stamp)
     return LIB
 
 

@@ -33,6 +33,32 @@ def test_clock_summary_without_samples():
     assert _sampler([])["reasons"] == ["unsampled"]
 
 
+def test_clock_record_prefers_nvml_samples_of_the_timed_region():
+    """NVML samples taken while the timed launches run make the record (their
+    median and every throttle reason seen); without them the nvidia-smi
+    samples over warm-up and timed region do."""
+    smi = bench.ClockSampler(0)
+    smi.lines = ["0, 1980, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    nv = bench.NvmlClocks.__new__(bench.NvmlClocks)
+    nv.samples, nv.max_mhz = [(2070.0, 0x0), (2055.0, 0x4), (2070.0, 0x0)], 2070.0
+    r = bench.clocks_record(nv, smi)
+    assert r["sm_mhz"] == 2070.0 and r["reasons"] == ["sw_power_cap"] and r["samples"] == 3
+    assert r["source"].startswith("NVML")
+    nv.samples = [(1500.0, 0x40 | 0x8)]
+    assert bench.clocks_record(nv, smi)["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    nv.samples = []
+    r = bench.clocks_record(nv, smi)
+    assert r["sm_mhz"] == 1980.0 and r["source"].startswith("nvidia-smi")
+    assert bench.clocks_record(None, smi)["sm_max_mhz"] == 2070.0
+
+
+def test_nvml_index_follows_visible_devices(monkeypatch):
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3,5")
+    assert bench.nvml_index(0) == 3 and bench.nvml_index(1) == 5
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.nvml_index(2) == 2
+
+
 def test_traffic_record_is_consistent_and_hash_ignores_comments(tmp_path, monkeypatch):
     """The traffic record names the code hash of its capture (the bench
     reports the DRAM traffic only while the sources still hash to it), and the
@@ -70,6 +96,10 @@ def test_reference_arm_prints_one_line_on_rank_zero_only():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the same config as the default line of the CUDA arm
+    assert d["config"] == bench.workload_config(1, bench.WORKLOAD, 128 ** 3, (128, 128, 128),
+                                                bench.ALGO_BYTES_PER_LUP)
+    assert "FP64" in d["arm"] and d["dtype"] == "f64"
     env = dict(os.environ, RANK="1", WORLD_SIZE="2")
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env)
     assert r.returncode == 0 and not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
