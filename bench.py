@@ -320,6 +320,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def mix_kernel_rate(stream, storage: str, per_class: int = 3, steps: int = 200) -> dict:
+    """The step kernel's own MLUPS on the serving mix, the yardstick of the
+    serving loop's throughput: for each side class, a few of the stream's
+    lattices each stepped alone (one lb_step call of `steps` steps after a
+    warm-up, CUDA graphs on, timed with CUDA events on its stream); the mix
+    rate weights each class's mean time per lattice update by the lattice
+    updates the whole stream asks of that class."""
+    import torch
+    from paper_0912_4230_gb300 import lb, workloads as W
+    s = torch.cuda.current_stream()
+    by_side = {}
+    for q in stream:
+        by_side.setdefault(q["nx"], []).append(q)
+    rate, total_lup, total_s = {}, 0.0, 0.0
+    for side, qs in sorted(by_side.items()):
+        secs = []
+        for q in qs[:per_class]:
+            p = W.request_problem(q, storage=storage)
+            g = lb.Lattice(p, storage=storage, kernel="cell", stream=s.cuda_stream)
+            g.step(21)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            g.step(steps)
+            e1.record(s)
+            e1.synchronize()
+            secs.append(e0.elapsed_time(e1) * 1e-3 / (steps * p.N))   # s per lattice update
+            g.close()
+        per_lup = sum(secs) / len(secs)
+        lup = sum(q["nx"] * q["ny"] * q["nz"] * q["steps"] for q in qs)
+        rate[str(side)] = 1e-6 / per_lup
+        total_lup += lup
+        total_s += lup * per_lup
+    return {"mlups": total_lup / total_s / 1e6, "by_side_mlups": rate,
+            "how": f"per side class up to {per_class} of the stream's lattices stepped alone "
+                   f"for {steps} steps, weighted by the stream's lattice updates"}
+
+
 def run_serving(args):
     """Serving workload: a Poisson stream of miscible-medium solves of sizes
     32..160 (z-aspect up to 2) under a 120 GB HBM budget, steps scaled down so
@@ -341,9 +378,12 @@ def run_serving(args):
     step_s, admit_s = torch.cuda.Stream(), torch.cuda.Stream()
     res = {}
     cap = args.max_resident or None
-    for name, storage, batched, maxres in (("batched_fp32", "fp32", True, cap),
-                                           ("batched_fp16", "fp16", True, cap),
-                                           ("per_lattice_fp32", "fp32", False, 1)):
+    arms = [a for a in (("batched_fp32", "fp32", True, cap),
+                        ("batched_fp16", "fp16", True, cap),
+                        ("per_lattice_fp32", "fp32", False, 1))
+            if a[0] in args.arms.split(",")]
+    kernel = {st: mix_kernel_rate(stream, st) for st in sorted({a[1] for a in arms})}
+    for name, storage, batched, maxres in arms:
         reqs = serve.make_requests(stream, storage=storage, steps_scale=scale)
         be = serve.LibraryBackend(storage, keep_fields=False, batched=batched,
                                   admit_stream=admit_s, step_stream=step_s)
@@ -356,11 +396,15 @@ def run_serving(args):
             torch.cuda.synchronize()
         st["clocks"] = clk.summary()
         st["arena_peak_bytes"] = arena.stats()["peak"]
+        st["chunks"] = len(srv.log)
+        st["mean_cells_stepped"] = (sum(e["stepped_cells"] for e in srv.log) / len(srv.log)
+                                    if srv.log else 0)
+        st["of_kernel_mix_rate"] = st["mlups"] / kernel[storage]["mlups"]
         res[name] = st
     lb.Arena.use_none()
     arena.close()
     del region
-    b = res["batched_fp32"]
+    b = res[arms[0][0]]
     line = {
         "metric": "served-solve throughput (MLUPS) and p50/p99 latency", "value": b["mlups"],
         "unit": "MLUPS", "n_gpus": 1, "steps": sum(r.steps for r in serve.make_requests(stream, steps_scale=scale)),
@@ -372,6 +416,7 @@ def run_serving(args):
                                f"{args.max_resident or 'budget-many'} resident, oldest stepped "
                                f"together up to {args.fill_cells or 'all'} cells"},
         "serving": res,
+        "kernel_mix_rate": kernel,
         "gpu_launches": None,
     }
     print(json.dumps(line), flush=True)
@@ -392,6 +437,8 @@ def main():
     ap.add_argument("--graphs", default="on", choices=["on", "off"],
                     help="replay step pairs from a CUDA graph (on) or launch every step")
     ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--arms", default="batched_fp32,batched_fp16,per_lattice_fp32",
+                    help="serving: the arms to run, comma-separated")
     ap.add_argument("--steps-scale", type=float, default=0.02)
     ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--max-resident", type=int, default=0,

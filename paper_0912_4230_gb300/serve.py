@@ -322,6 +322,7 @@ class Server:
                 else:
                     still.append(r)
             self.log.append(dict(t=self.clock() - t0, resident=len(active), stepped=len(stepping),
+                                 stepped_cells=sum(r.problem.N for r in stepping),
                                  steps=n, used=self._used))
             with lock:
                 active[:] = still
