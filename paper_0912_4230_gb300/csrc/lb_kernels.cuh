@@ -24,6 +24,12 @@ namespace lbgb {
 // cell's bare V and V' for the pass over further solute species.
 enum : int { FEAT_OPEN = 1, FEAT_VEL = 2 };
 
+// the first direction of each pair of opposite directions (its partner is opp)
+__host__ __device__ constexpr int pair_first(int k) {
+  constexpr int t[9] = {1, 2, 5, 7, 8, 11, 13, 14, 17};
+  return t[k];
+}
+
 template <int I, int N>
 struct Unroll {
   template <class F>
@@ -174,6 +180,22 @@ __device__ __forceinline__ Real tau_of(const StepArgs<Real> &a, Real C) {
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
+// Inside an iteration that corrects its own errors (the Forchheimer Newton
+// solve) FP32 takes the hardware's single-instruction approximations (at
+// most 1 ulp off: PTX rcp.approx / sqrt.approx); FP64 keeps exact operations.
+__device__ __forceinline__ float rcp_iter(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double rcp_iter(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_iter(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double sqrt_iter(double x) { return sqrt(x); }
+
 // V' = Lambda^-1 (V + eps G / 2), Lambda = I + (eps nu / 2) K^-1, and
 // F^ext = -eps nu K^-1 V' + eps G (Eqs. forcement, expandV, expandVsub).
 // kv(r) returns row r of the cell's K^-1 (diagonal: xx, yy, zz; full: xx, yy,
@@ -217,19 +239,20 @@ __device__ __forceinline__ void velocity_solve_kv(KV kv, Real eps, Real nu, cons
       const Real ab = (r0 * r0 * a[0] + r1 * r1 * a[1] + r2 * r2 * a[2]) * iws;
       const Real bb = (r0 * r0 * b[0] + r1 * r1 * b[1] + r2 * r2 * b[2]) * iws;
       const Real rn = sqrt(ws);
-      s = Real(2) * rn * rcp(ab + sqrt(ab * ab + Real(4) * bb * rn));
+      s = Real(2) * rn * rcp_iter(ab + sqrt_iter(ab * ab + Real(4) * bb * rn));
       // Newton on phi(s) = s - |V'(s)|: s <- s - (s - |V'|) |V'| / (|V'| + g),
-      // g = sum_i V'_i^2 b_i / (a_i + b_i s)
+      // g = sum_i V'_i^2 b_i / (a_i + b_i s); the iteration absorbs the
+      // approximate reciprocals and roots, the final V' takes exact ones
       constexpr int kIters = sizeof(Real) == 4 ? 3 : 4;
       for (int it = 0; it < kIters; ++it) {
         Real vv = Real(0), g = Real(0);
         for (int i = 0; i < 3; ++i) {
-          const Real iD = rcp(a[i] + b[i] * s), v = r[i] * iD;
+          const Real iD = rcp_iter(a[i] + b[i] * s), v = r[i] * iD;
           vv += v * v;
           g += v * v * b[i] * iD;
         }
-        const Real vn = sqrt(vv);
-        s -= (s - vn) * vn * rcp(vn + g);
+        const Real vn = sqrt_iter(vv);
+        s -= (s - vn) * vn * rcp_iter(vn + g);
       }
     }
     for (int i = 0; i < 3; ++i) Vp[i] = r[i] * rcp(a[i] + b[i] * s);
@@ -329,6 +352,23 @@ struct FluidCollide {
       b += S2 * cs * cs;
     }
     return b;
+  }
+  // b_q and b_qbar of a pair of opposite directions: the even part K +
+  // cu (B45 cu + P9 cF) [+ S2 (c.F)^2] is shared, the odd part B3 cu + P3 cF
+  // changes sign (cu = c_q.V', cF = c_q.F_e). Every step is an explicit
+  // fma, product or sum, so every kernel rounds it alike.
+  template <int q>
+  __device__ __forceinline__ void br_pair(Real &bq, Real &bo) const {
+    const Real cu = Real(cx(q)) * Vp[0] + Real(cy(q)) * Vp[1] + Real(cz(q)) * Vp[2];
+    const Real cF = Real(cx(q)) * Fe[0] + Real(cy(q)) * Fe[1] + Real(cz(q)) * Fe[2];
+    Real ev = fma(cu, fma(B45, cu, P9 * cF), K);
+    if (st) {
+      const Real cs = Real(cx(q)) * F[0] + Real(cy(q)) * F[1] + Real(cz(q)) * F[2];
+      ev = fma(S2 * cs, cs, ev);
+    }
+    const Real od = fma(B3, cu, P3 * cF);
+    bq = ev + od;
+    bo = ev - od;
   }
   // f^eq_q - w_q (with the surface-tension part), for initialisation
   template <int q>
@@ -555,6 +595,8 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
     // h^eq_q/w_q = sC (1 + 3 c_q.v), stored scale (h~_q/w_q - Rh); the rest
     // direction takes sC - sum_{q>0} h^eq_q, divided by its weight with a
     // correctly rounded division, so the weights' rounding adds no solute.
+    // Opposite directions are formed together: they share c.V', c.F_e and
+    // c.v, and their h^eq sum to 2 w sC.
     const __half2 r2 = __floats2half2_rn(drho, sC);
     const float2 R = __half22float2(r2);
     using T2 = typename S::T2;
@@ -565,14 +607,18 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
     const Real vs0 = fc.Vp[0] + gx, vs1 = fc.Vp[1] + gy, vs2 = fc.Vp[2] + gz;
     const Real itd = a.inv_tau_D;
     const Real sod = sc * (Real(1) - itd), h0 = sc * (itd * sC - R.y),
-               h3 = Real(3) * sc * itd * sC, s3 = Real(3) * sC;
+               h3 = Real(3) * sc * itd * sC;
     Real hsum = Real(0);
-    Unroll<1, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
+    Unroll<0, 9>::run([&](auto kc) {
+      constexpr int q = pair_first(decltype(kc)::value), o = opp(q);
+      const auto qq = std::integral_constant<int, q>{};
+      const auto oo = std::integral_constant<int, o>{};
       const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
-      hsum = fma(wq<Real>(q), fma(s3, cv, sC), hsum);
-      S::st2(po + int(q * N), fma(so, fv(qc), fc.template br<q>()),
-             fma(sod, hv(qc), fma(h3, cv, h0)));
+      hsum = fma(Real(2) * wq<Real>(q), sC, hsum);
+      Real bq, bo;
+      fc.template br_pair<q>(bq, bo);
+      S::st2(po + int(q * N), fma(so, fv(qq), bq), fma(sod, hv(qq), fma(h3, cv, h0)));
+      S::st2(po + int(o * N), fma(so, fv(oo), bo), fma(sod, hv(oo), fma(-h3, cv, h0)));
     });
     const Real he0 = (sC - hsum) / wq<Real>(0);
     const auto q0 = std::integral_constant<int, 0>{};
