@@ -56,7 +56,7 @@ def _other_workloads():
         # eps, K^-1 and the mask read once
         "species": (lambda r: W.miscible_species(seed=r), "fp32", 4 * 152 + 17,
                     "miscible medium 128^3 with three solute species (tau_D 0.8 / 1.2 / 0.6), "
-                    "D3Q19 fluid + 3 solute lattices, FP32; step = fused pass + species pass"),
+                    "D3Q19 fluid + 3 solute lattices, FP32; one fused pass per step"),
         "wood": (lambda r: W.wood(nx=256, ny=192, nz=64, wood_depth=128), "fp32", 333,
                  "adhesive pressed into wood 256x192x64 (year rings of 30 cells at 45 deg, "
                  "full SPD K, pressure faces, solute inlet/outlet, hardening law), FP32"),
@@ -536,12 +536,12 @@ def main():
     peak, peak_kind = measured_peaks()
     species = int(prob.params.get("species", 1))
     # launches of one step: the free surface's six passes and its tile
-    # compaction; the fused step and the species pass; else the fused step
-    # (plus the density pre-pass with surface tension)
+    # compaction; else the fused step (which also advances further solute
+    # species), plus the density pre-pass with surface tension
     if prob.cell_type is not None:
         launches_per_step = 7
     else:
-        launches_per_step = (2 if species > 1 else 1) + (1 if prob.params.get("A", 0.0) else 0)
+        launches_per_step = 1 + (1 if prob.params.get("A", 0.0) else 0)
     units = N
     if prob.cell_type is not None:
         units = int(((prob.cell_type != W.EMPTY) & (prob.solid == 0)).sum())  # updated cells
@@ -568,7 +568,7 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind,
                      "kernel": ("seven free-surface launches of one step" if prob.cell_type is not None
-                                else "step_kernel + species_kernel of one step"
+                                else "step_kernel (fluid and every solute species)"
                                 if species > 1 else
                                 "tma_step_kernel (row-pipelined)" if choice == 256 else
                                 f"pipe_step_kernel (row-staged), rows of {choice - 1000} threads"

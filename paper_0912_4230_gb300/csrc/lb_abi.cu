@@ -65,7 +65,6 @@ struct lb_ctx {
   unsigned f_wall = 0, f_press = 0, f_vel = 0, s_wall = 0, s_inlet = 0, s_outlet = 0;
   bool open_faces = false;  // pressure or velocity faces: per-cell kernel only
   int S = 0;                // solute species (0 without the solute lattice)
-  void *vel = nullptr;      // S > 1: bare V and V' of the step (6 N Real)
   void *spec = nullptr;     // S > 1: per-species 1/tau_D, C_in, D_s/D_0 (24 Real)
   void *face = nullptr;  // per-face values of pressure / velocity faces (30 Real)
   // CUDA graphs: two steps (both buffer parities) captured once on a private
@@ -240,7 +239,7 @@ unsigned slot_warps(const lb_domain &dom) {
 // allocation does. k_rows: rows of K^-1 kept (0, 3 diagonal, 6 full tensor).
 struct Layout {
   size_t f, h, rf, rh;   // per population buffer (two of each; 0 = not allocated)
-  size_t vel, spec;      // several species
+  size_t spec;           // several species: per-species constants
   size_t eps, link, fields, partials, state, geps, rhohat, face;
   size_t fs_type, fs_mass, fs_lam, fs_share, fs_mom, fs_flag, fs_any, fs_tiles, fs_ntiles,
       fs_stamp, fs_stamp_ctr;
@@ -268,7 +267,6 @@ Layout layout_of(const lb_domain &dom, const lb_params &prm, const StorageOps &o
   L.rf = shift ? N * sizeof(float) : 0;
   L.rh = (shift && Sh) ? S * N * sizeof(float) : 0;
   if (solute && S > 1) {
-    L.vel = 6 * N * rb;
     L.spec = 24 * rb;
   }
   L.eps = N * rb;
@@ -321,7 +319,6 @@ void fill_args(const lb_ctx *c, StepArgs<Real> &a) {
   a.f_press = c->f_press;
   a.f_vel = c->f_vel;
   a.face = static_cast<const Real *>(c->face);
-  a.vel = static_cast<Real *>(c->vel);
   a.spec = static_cast<const Real *>(c->spec);
   a.species = c->S;
   a.slot_stride = c->nwarps * 2;
@@ -477,7 +474,6 @@ int enqueue_step(lb_ctx *c, cudaStream_t s, bool last) {
                               c->pipe.gxr, c->pipe.items, s));
     else {
       CK(c, c->ops->step(c->kmode, c->solute, step_feat(c), args, c->sgrid, c->sblock, s));
-      if (c->S > 1) CK(c, c->ops->species_step(args, c->sgrid, c->sblock, s));
     }
     return int(LB_OK);
   });
@@ -531,7 +527,7 @@ int capture_pair(lb_ctx *c, cudaGraphExec_t *out, StepFn &&step) {
 }
 
 // features of the per-cell step kernel this lattice needs
-int step_feat(const lb_ctx *c) { return (c->open_faces ? FEAT_OPEN : 0) | (c->S > 1 ? FEAT_VEL : 0); }
+int step_feat(const lb_ctx *c) { return (c->open_faces ? FEAT_OPEN : 0) | (c->S > 1 ? FEAT_SPEC : 0); }
 
 // One warp waits, with the step kernels' bounded wait, on a shared-memory
 // barrier that nothing completes; on giving up it sets the timeout bit of the
@@ -589,7 +585,7 @@ int lb_bytes_required(const lb_domain *dom, const lb_params *prm, int32_t k_rows
     return fail(nullptr, LB_EINVAL, "species outside [0, LB_MAX_SPECIES]");
   const Layout L = layout_of(*dom, *prm, *ops, k_rows, f_scale != 0);
   const size_t twice[] = {L.f, L.h, L.rf, L.rh, L.fs_type, L.fs_mass, L.fs_flag, L.fs_tiles};
-  const size_t once[] = {L.vel, L.spec, L.eps, L.link, L.fields, L.partials, L.state, L.geps,
+  const size_t once[] = {L.spec, L.eps, L.link, L.fields, L.partials, L.state, L.geps,
                          L.rhohat, L.face, L.fs_lam, L.fs_share, L.fs_mom, L.fs_any,
                          L.fs_ntiles, L.fs_stamp, L.fs_stamp_ctr, L.kinv, L.flux_slots,
                          L.batch_share};
@@ -706,7 +702,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
       sv[8 + sp] = sp ? prm->species_C_in[sp] : prm->C_in;
       sv[16 + sp] = ((tD - 0.5) / 3.0) / D0;
     }
-    if (!(c->vel = dev_alloc(c, L.vel)) || !(c->spec = dev_alloc(c, L.spec)))
+    if (!(c->spec = dev_alloc(c, L.spec)))
       return bail(fail(c, LB_ENOMEM, "species"));
     float sf[24];
     for (int i = 0; i < 24; ++i) sf[i] = float(sv[i]);
@@ -1085,7 +1081,6 @@ int step_batch_t(lb_ctx *const *ctxs, int n, int64_t steps) {
       step_args(ctxs[i], a);
       CK(c0, c0->ops->step(c0->kmode, c0->solute, step_feat(ctxs[i]), &a, ctxs[i]->sgrid,
                            ctxs[i]->sblock, st));
-      if (ctxs[i]->S > 1) CK(c0, c0->ops->species_step(&a, ctxs[i]->sgrid, ctxs[i]->sblock, st));
     }
     for (int g0 = 0; g0 < ns; g0 += BATCH_MAX) {
       const int g1 = std::min(ns, g0 + BATCH_MAX);

@@ -263,11 +263,9 @@ struct StepArgs {
   float *fields;        // NULL or 6 x N: rho, ux, uy, uz, C, nu
   double *flux_slots;   // 2 per warp of the step launch: cumulative inlet / outlet flux
   DevState *state;
-  // Several solute species: the fused step (kernel feature FEAT_VEL) writes
-  // each cell's bare V and V' (vel, 6 x N) for the species pass; spec holds
-  // per species [0, 8) 1/tau_D, [8, 16) C_in, [16, 24) D_s / D_0; species s
-  // uses the flux slots at flux_slots + s * slot_stride.
-  Real *vel;
+  // Several solute species (kernel feature FEAT_SPEC): spec holds per species
+  // [0, 8) 1/tau_D, [8, 16) C_in, [16, 24) D_s / D_0; species s uses the flux
+  // slots at flux_slots + s * slot_stride.
   const Real *spec;
   int species;
   unsigned slot_stride;

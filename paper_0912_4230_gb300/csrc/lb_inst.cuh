@@ -53,15 +53,11 @@ struct Instance {
       switch (feat) {
         case 0: return step_t<K, L, 0>(a, grid, block, s);
         case FEAT_OPEN: return step_t<K, L, FEAT_OPEN>(a, grid, block, s);
-        case FEAT_VEL: return L ? step_t<K, L, FEAT_VEL>(a, grid, block, s) : cudaErrorInvalidValue;
+        case FEAT_SPEC: return L ? step_t<K, L, FEAT_SPEC>(a, grid, block, s) : cudaErrorInvalidValue;
         default:
-          return L ? step_t<K, L, FEAT_OPEN | FEAT_VEL>(a, grid, block, s) : cudaErrorInvalidValue;
+          return L ? step_t<K, L, FEAT_OPEN | FEAT_SPEC>(a, grid, block, s) : cudaErrorInvalidValue;
       }
     });
-  }
-  static cudaError_t species_step(const void *args, dim3 grid, dim3 block, cudaStream_t s) {
-    species_kernel<S><<<grid, block, 0, s>>>(*static_cast<const A *>(args));
-    return cudaGetLastError();
   }
   static cudaError_t species_init(const void *args, const float *u0, const float *C0,
                                   unsigned nblk, cudaStream_t s) {
@@ -251,7 +247,6 @@ struct Instance {
       o.fs_seed = &fs_seed;
     }
     o.batch_step = &batch_step;
-    o.species_step = &species_step;
     o.species_init = &species_init;
     o.tma_config = nullptr;
     o.tma_step = nullptr;

@@ -20,9 +20,9 @@ namespace lbgb {
 
 // Compile-time features of the per-cell step kernel, each a separate
 // instantiation so that lattices without them keep the plain code:
-// pressure / velocity faces of the fluid lattice, and the export of each
-// cell's bare V and V' for the pass over further solute species.
-enum : int { FEAT_OPEN = 1, FEAT_VEL = 2 };
+// pressure / velocity faces of the fluid lattice, and further solute species
+// (1 .. S-1, advanced by the same thread after the fluid and species 0).
+enum : int { FEAT_OPEN = 1, FEAT_SPEC = 2 };
 
 // the first direction of each pair of opposite directions (its partner is opp)
 __host__ __device__ constexpr int pair_first(int k) {
@@ -550,14 +550,17 @@ __device__ __forceinline__ void fluid_moments(FV fv, Real &drho, Real (&V)[3]) {
 // stores and exported fields. fv(q) and hv(q) give the arriving f_q - w_q and
 // h_q (16-bit storage: (f_q - w_q)/w_q and h_q/w_q), kv(r) the rows of K^-1;
 // drho, rho, V are the fluid moments, sC the solute total of the arriving h.
-template <class S, int KMODE, bool SOLUTE, bool VEL = false, class FV, class HV, class KV>
+// VOUT: the cell's bare V and V' are returned in vout[0..2], vout[3..5]
+// (for the further solute species of the same thread).
+template <class S, int KMODE, bool SOLUTE, bool VOUT = false, class FV, class HV, class KV>
 __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a, unsigned n,
                                              const CellGeo &g, FV fv, HV hv, KV kv,
                                              typename S::Real drho, typename S::Real rho,
                                              const typename S::Real (&V)[3], typename S::Real ie,
                                              typename S::Real eps, typename S::Real sC,
                                              typename S::Real gx, typename S::Real gy,
-                                             typename S::Real gz) {
+                                             typename S::Real gz,
+                                             typename S::Real *vout = nullptr) {
   using Real = typename S::Real;
   using T = typename S::T;
   const unsigned N = a.N;
@@ -665,13 +668,13 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
     }
   }
   if (a.fields) write_fields(a.fields, N, n, rho, fc.Vp, C, nu);
-  if constexpr (VEL) {
-    a.vel[n] = V[0];
-    a.vel[size_t(N) + n] = V[1];
-    a.vel[2 * size_t(N) + n] = V[2];
-    a.vel[3 * size_t(N) + n] = fc.Vp[0];
-    a.vel[4 * size_t(N) + n] = fc.Vp[1];
-    a.vel[5 * size_t(N) + n] = fc.Vp[2];
+  if constexpr (VOUT) {
+    vout[0] = V[0];
+    vout[1] = V[1];
+    vout[2] = V[2];
+    vout[3] = fc.Vp[0];
+    vout[4] = fc.Vp[1];
+    vout[5] = fc.Vp[2];
   }
 }
 
@@ -683,7 +686,8 @@ template <class S, int KMODE, int FEAT>
 __device__ __forceinline__ void update_cell_paired(const StepArgs<float> &a, unsigned x, unsigned y,
                                                    unsigned z, unsigned n, uint32_t link,
                                                    float &fin_acc, float &fout_acc, float &drho,
-                                                   float &sC, bool &open_face) {
+                                                   float &sC, bool &open_face,
+                                                   float *vout = nullptr) {
   using Real = float;
   using T2 = typename S::T2;
   const unsigned N = a.N;
@@ -755,11 +759,11 @@ __device__ __forceinline__ void update_cell_paired(const StepArgs<float> &a, uns
     constexpr int q = decltype(qc)::value;
     sC = fma(wq<Real>(q), hh[q], sC);
   });
-  collide_tail<S, KMODE, true, (FEAT & FEAT_VEL) != 0>(
+  collide_tail<S, KMODE, true, (FEAT & FEAT_SPEC) != 0>(
       a, n, g, [&](auto qc) { return d[decltype(qc)::value]; },
       [&](auto qc) { return hh[decltype(qc)::value]; },
       [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
-      gz);
+      gz, vout);
 }
 
 // The per-cell update of one step from global memory: stream f (and h),
@@ -770,7 +774,8 @@ __device__ __forceinline__ void update_cell_sep(const StepArgs<typename S::Real>
                                             unsigned y, unsigned z, unsigned n, uint32_t link,
                                             typename S::Real &fin_acc,
                                             typename S::Real &fout_acc, typename S::Real &drho,
-                                            typename S::Real &sC, bool &open_face) {
+                                            typename S::Real &sC, bool &open_face,
+                                            typename S::Real *vout = nullptr) {
   using Real = typename S::Real;
   using T = typename S::T;
   const unsigned N = a.N;
@@ -874,11 +879,11 @@ __device__ __forceinline__ void update_cell_sep(const StepArgs<typename S::Real>
     }
     Unroll<0, Q>::run([&](auto qc) { sC += hh[SOLUTE ? decltype(qc)::value : 0]; });
   }
-  collide_tail<S, KMODE, SOLUTE, (FEAT & FEAT_VEL) != 0>(
+  collide_tail<S, KMODE, SOLUTE, (FEAT & FEAT_SPEC) != 0>(
       a, n, g, [&](auto qc) { return d[decltype(qc)::value]; },
       [&](auto qc) { return hh[SOLUTE ? decltype(qc)::value : 0]; },
       [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
-      gz);
+      gz, vout);
 }
 
 template <class S, int KMODE, bool SOLUTE, int FEAT = 0>
@@ -886,12 +891,95 @@ __device__ __forceinline__ void update_cell(const StepArgs<typename S::Real> &a,
                                             unsigned y, unsigned z, unsigned n, uint32_t link,
                                             typename S::Real &fin_acc,
                                             typename S::Real &fout_acc, typename S::Real &drho,
-                                            typename S::Real &sC, bool &open_face) {
+                                            typename S::Real &sC, bool &open_face,
+                                            typename S::Real *vout = nullptr) {
   if constexpr (S::kShift && SOLUTE)
-    update_cell_paired<S, KMODE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
+    update_cell_paired<S, KMODE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face,
+                                       vout);
   else
     update_cell_sep<S, KMODE, SOLUTE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC,
-                                            open_face);
+                                            open_face, vout);
+}
+
+// Solute species sp >= 1 of one cell, after the fluid and species 0 of the
+// same step (Eqs. equild, boltzeqD for each species, reading R24): each
+// species is its own D3Q19 lattice with its own tau_D and inlet
+// concentration; all share the cell's V' (vel[3..5]) and, for populations
+// entering through an inlet face, its bare streamed velocity V (vel[0..2]).
+// The gather with its boundary classes, C = sum_q h_q / eps, h^eq at V* = V' +
+// D_s grad(eps)/eps with the rest component as the remainder, BGK.
+template <class S>
+__device__ __forceinline__ void species_update(const StepArgs<typename S::Real> &a, int sp,
+                                               unsigned x, unsigned y, unsigned z, unsigned n,
+                                               uint32_t link, const typename S::Real (&vel)[6],
+                                               typename S::Real &fin_acc,
+                                               typename S::Real &fout_acc, typename S::Real &sC,
+                                               bool &open_face) {
+  using Real = typename S::Real;
+  using T = typename S::T;
+  const unsigned N = a.N;
+  const CellGeo g = cell_geo_xyz(x, y, z, a.nx, a.ny, a.nz);
+  // the paired layout keeps species 0 with f, so the h buffers start at species 1
+  const size_t off = size_t(sp - a.paired) * Q * N;
+  const T *__restrict__ hb = static_cast<const T *>(a.h_in) + off + n;
+  T *__restrict__ ho = static_cast<T *>(a.h_out) + off + n;
+  const float *rh_in = S::kShift ? a.rh_in + size_t(sp) * N : nullptr;
+  const Real eps = __ldg(a.eps + n);
+  const Real ratio = __ldg(a.spec + 16 + sp);  // D_s / D_0 (geps holds D_0 grad(eps)/eps)
+  const Real gx = ratio * __ldg(a.geps + n), gy = ratio * __ldg(a.geps + N + n),
+             gz = ratio * __ldg(a.geps + 2 * size_t(N) + n);
+  const Real C_in = __ldg(a.spec + 8 + sp), itd = __ldg(a.spec + sp);
+  const unsigned s_open = a.s_inlet | a.s_outlet;
+  open_face = (g.onface & s_open) != 0;
+  Real hh[Q];
+  if (link == 0 && !(g.onface & (a.s_wall | s_open))) {
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      hh[q] = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+      if constexpr (S::kShift) hh[q] += wq<Real>(q) * __ldg(rh_in + (long long)n + src_delta<q>(g));
+    });
+  } else {
+    const Real vi0 = vel[0] + gx, vi1 = vel[1] + gy, vi2 = vel[2] + gz;
+    Unroll<0, Q>::run([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const int cls = solute_class<q>(g, link, a.s_wall, a.s_inlet, a.s_outlet);
+      Real v;
+      const Real own = S::kShift ? wq<Real>(q) * __ldg(rh_in + n) : Real(0);
+      if (cls == PULL_CELL) {
+        v = S::template ld_h<q>(hb + (int(q * N) + src_delta<q>(g)));
+        if constexpr (S::kShift) v += wq<Real>(q) * __ldg(rh_in + (long long)n + src_delta<q>(g));
+      } else if (cls == PULL_BOUNCE) {
+        v = S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own;
+      } else if (cls == PULL_INLET) {
+        const Real cv = Real(cx(q)) * vi0 + Real(cy(q)) * vi1 + Real(cz(q)) * vi2;
+        v = wq<Real>(q) * eps * C_in * (Real(1) + Real(3) * cv);
+        fin_acc += v - (S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own);
+      } else {
+        v = S::template ld_h<q>(hb + int(q * N)) + own;
+        fout_acc += (S::template ld_h<opp(q)>(hb + int(opp(q) * N)) + own) - v;
+      }
+      hh[q] = v;
+    });
+  }
+  Unroll<0, Q>::run([&](auto qc) { sC += hh[decltype(qc)::value]; });
+  const Real vs0 = vel[3] + gx, vs1 = vel[4] + gy, vs2 = vel[5] + gz;
+  Real hsum = Real(0);
+  Unroll<1, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const Real cv = Real(cx(q)) * vs0 + Real(cy(q)) * vs1 + Real(cz(q)) * vs2;
+    const Real heq = wq<Real>(q) * sC * (Real(1) + Real(3) * cv);
+    hsum += heq;
+    const Real h = hh[q];
+    const Real shift = S::kShift ? wq<Real>(q) * sC : Real(0);
+    S::template st_h<q>(ho + int(q * N), h + (heq - h) * itd - shift);
+  });
+  {
+    const Real h = hh[0];
+    const Real shift = S::kShift ? wq<Real>(0) * sC : Real(0);
+    S::template st_h<0>(ho, h + ((sC - hsum) - h) * itd - shift);
+  }
+  if constexpr (S::kShift) a.rh_out[size_t(sp) * N + n] = float(sC);
+  if (a.fields) a.fields[(5 + size_t(sp)) * N + n] = float(sC * rcp(eps));
 }
 
 // One time step for every non-solid cell (see update_cell).
@@ -920,8 +1008,32 @@ __global__ void __launch_bounds__(STEP_BLOCK, 6) step_kernel(const StepArgs<type
   }
   Real fin_acc = Real(0), fout_acc = Real(0), drho = Real(0), sC = Real(0);
   bool open_face = false;
-  if (live) update_cell<S, KMODE, SOLUTE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC, open_face);
+  Real vel[6];
+  if (live)
+    update_cell<S, KMODE, SOLUTE, FEAT>(a, x, y, z, n, link, fin_acc, fout_acc, drho, sC,
+                                        open_face, (FEAT & FEAT_SPEC) ? vel : nullptr);
   warp_reductions(a, warp_gid, open_face, fin_acc, fout_acc, drho, sC);
+  if constexpr ((FEAT & FEAT_SPEC) != 0) {
+    // further species, each with its per-warp flux slots and finite check
+    const unsigned lane = threadIdx.x & 31u;
+    for (int sp = 1; sp < a.species; ++sp) {
+      Real fin_s = Real(0), fout_s = Real(0), sC_s = Real(0);
+      bool of = false;
+      if (live) species_update<S>(a, sp, x, y, z, n, link, vel, fin_s, fout_s, sC_s, of);
+      if (a.flux && __any_sync(0xffffffffu, of)) {
+        const Real si = warp_sum(fin_s), so = warp_sum(fout_s);
+        if (lane == 0) {
+          double *slot = a.flux_slots + size_t(sp) * a.slot_stride + 2 * size_t(warp_gid);
+          slot[0] += double(si);
+          slot[1] += double(so);
+        }
+      }
+      if (a.reduce) {
+        const Real c = warp_sum(sC_s);
+        if (lane == 0 && !isfinite(c)) atomicOr(&a.state->status, 1u);
+      }
+    }
+  }
 }
 
 // Post-stream density for the colour gradient (flowchart: stream -> moments

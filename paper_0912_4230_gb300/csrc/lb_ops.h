@@ -34,13 +34,12 @@ struct StorageOps {
   size_t elt_bytes;  // bytes per stored population
   bool fp64;         // collision type is double (StepArgs<double>)
   // step / init / rhohat take a StepArgs<Real>* matching fp64
-  // feat: FEAT_OPEN (pressure / velocity faces) | FEAT_VEL (export V and V'
-  // for further solute species), each its own instantiation
+  // feat: FEAT_OPEN (pressure / velocity faces) | FEAT_SPEC (further solute
+  // species advanced by the same launch), each its own instantiation
   cudaError_t (*step)(int kmode, bool solute, int feat, const void *args, dim3 grid,
                       dim3 block, cudaStream_t s);
-  // further solute species 1 .. species-1 of a step (after step) and their
-  // initial populations (u0 3N, C0 species x N, device)
-  cudaError_t (*species_step)(const void *args, dim3 grid, dim3 block, cudaStream_t s);
+  // initial populations of further solute species 1 .. species-1 (u0 3N,
+  // C0 species x N, device)
   cudaError_t (*species_init)(const void *args, const float *u0, const float *C0, unsigned nblk,
                               cudaStream_t s);
   cudaError_t (*init)(int kmode, bool solute, const void *args, const void *init_args,
