@@ -66,8 +66,7 @@ def _other_workloads():
         # free surface: algorithmic bytes counted per updated (liquid or interface) cell
         "drop": (lambda r: W.drop(seed=r), "fp32", 171,
                  "free-surface drop 192x192x128 (R 24, 40 cells above a solid wall), A 1e-3, "
-                 "FP32, six passes over the active tiles and one compaction per step; roofline "
-                 "per updated cell"),
+                 "FP32, five passes over the active tiles per step; roofline per updated cell"),
     }
 
 
@@ -535,11 +534,11 @@ def main():
 
     peak, peak_kind = measured_peaks()
     species = int(prob.params.get("species", 1))
-    # launches of one step: the free surface's six passes and its tile
-    # compaction; else the fused step (which also advances further solute
-    # species), plus the density pre-pass with surface tension
+    # launches of one step: the free surface's five passes; else the fused
+    # step (which also advances further solute species), plus the density
+    # pre-pass with surface tension
     if prob.cell_type is not None:
-        launches_per_step = 7
+        launches_per_step = 5
     else:
         launches_per_step = 1 + (1 if prob.params.get("A", 0.0) else 0)
     units = N
@@ -567,7 +566,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind,
-                     "kernel": ("seven free-surface launches of one step" if prob.cell_type is not None
+                     "kernel": ("five free-surface launches of one step" if prob.cell_type is not None
                                 else "step_kernel (fluid and every solute species)"
                                 if species > 1 else
                                 "tma_step_kernel (row-pipelined)" if choice == 256 else

@@ -93,7 +93,7 @@ struct lb_ctx {
   // free surface
   uint8_t *type[2] = {nullptr, nullptr};
   void *mass[2] = {nullptr, nullptr};
-  void *lam = nullptr, *share = nullptr, *mom = nullptr;
+  void *lam = nullptr, *rho_post = nullptr, *share = nullptr, *mom = nullptr;
   uint8_t *flag_a = nullptr, *flag_b = nullptr;
   unsigned *any = nullptr;
   // free surface: active-tile lists (step parity), their lengths, tile stamps
@@ -241,7 +241,7 @@ struct Layout {
   size_t f, h, rf, rh;   // per population buffer (two of each; 0 = not allocated)
   size_t spec;           // several species: per-species constants
   size_t eps, link, fields, partials, state, geps, rhohat, face;
-  size_t fs_type, fs_mass, fs_lam, fs_share, fs_mom, fs_flag, fs_any, fs_tiles, fs_ntiles,
+  size_t fs_type, fs_mass, fs_lam, fs_rho, fs_share, fs_mom, fs_flag, fs_any, fs_tiles, fs_ntiles,
       fs_stamp, fs_stamp_ctr;
   size_t kinv, flux_slots;
   size_t create_stage;   // inputs of lb_create, released before it returns
@@ -285,6 +285,7 @@ Layout layout_of(const lb_domain &dom, const lb_params &prm, const StorageOps &o
     L.fs_type = N;
     L.fs_mass = N * rb;
     L.fs_lam = N * rb;
+    L.fs_rho = N * rb;
     L.fs_share = N * rb;
     L.fs_mom = 4 * N * rb;
     L.fs_flag = N;
@@ -419,6 +420,7 @@ FsArgs<Real> fs_args(lb_ctx *c, const StepArgs<Real> &a, long long t) {
   fa.rhohat_w = static_cast<Real *>(c->rhohat);
   fa.flag_a = c->flag_a;
   fa.flag_b = c->flag_b;
+  fa.rho_post = static_cast<Real *>(c->rho_post);
   fa.share = static_cast<Real *>(c->share);
   fa.mom = static_cast<Real *>(c->mom);
   fa.any = c->any;
@@ -586,7 +588,7 @@ int lb_bytes_required(const lb_domain *dom, const lb_params *prm, int32_t k_rows
   const Layout L = layout_of(*dom, *prm, *ops, k_rows, f_scale != 0);
   const size_t twice[] = {L.f, L.h, L.rf, L.rh, L.fs_type, L.fs_mass, L.fs_flag, L.fs_tiles};
   const size_t once[] = {L.spec, L.eps, L.link, L.fields, L.partials, L.state, L.geps,
-                         L.rhohat, L.face, L.fs_lam, L.fs_share, L.fs_mom, L.fs_any,
+                         L.rhohat, L.face, L.fs_lam, L.fs_rho, L.fs_share, L.fs_mom, L.fs_any,
                          L.fs_ntiles, L.fs_stamp, L.fs_stamp_ctr, L.kinv, L.flux_slots,
                          L.batch_share};
   size_t total = 0;
@@ -749,6 +751,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
       if (!c->type[b] || !c->mass[b]) return bail(fail(c, LB_ENOMEM, "free surface"));
     }
     c->lam = dev_alloc(c, L.fs_lam);
+    c->rho_post = dev_alloc(c, L.fs_rho);
     c->share = dev_alloc(c, L.fs_share);
     c->mom = dev_alloc(c, L.fs_mom);
     c->flag_a = static_cast<uint8_t *>(dev_alloc(c, L.fs_flag));
@@ -763,7 +766,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     c->n_tiles = static_cast<unsigned *>(dev_alloc(c, L.fs_ntiles));
     c->stamp = static_cast<unsigned *>(dev_alloc(c, L.fs_stamp));
     c->stamp_ctr = static_cast<unsigned *>(dev_alloc(c, L.fs_stamp_ctr));
-    if (!c->lam || !c->share || !c->mom || !c->flag_a || !c->flag_b || !c->any || !c->tiles[0] ||
+    if (!c->lam || !c->rho_post || !c->share || !c->mom || !c->flag_a || !c->flag_b || !c->any || !c->tiles[0] ||
         !c->tiles[1] || !c->n_tiles || !c->stamp || !c->stamp_ctr)
       return bail(fail(c, LB_ENOMEM, "free surface"));
     // persistent grid of the tile passes: enough resident blocks to cover

@@ -273,8 +273,9 @@ struct StepArgs {
 
 // Free-surface state of one step (Section 3): cell types, liquid mass m,
 // liquid fraction lambda and the re-typing scratch.
-enum : uint8_t { CELL_NEW_INTERFACE = 3 };
-enum : uint8_t { FS_NONE = 0, FS_FILL = 1, FS_EMPTYING = 2 };
+// Conversion flags: an interface cell that fills or empties, and (re-typing
+// pass onwards) an empty cell that has become an interface cell.
+enum : uint8_t { FS_NONE = 0, FS_FILL = 1, FS_EMPTYING = 2, FS_NEWCELL = 3 };
 
 template <class Real>
 struct FsArgs {
@@ -286,6 +287,8 @@ struct FsArgs {
   Real *lam;             // lambda(t) in, lambda(t+1) out
   Real *rhohat_w;        // colour-gradient field written by the mass exchange
   uint8_t *flag_a, *flag_b;
+  Real *rho_post;        // post-collision density of each live cell (new interface cells:
+                         // of their initial populations)
   Real *share;           // excess mass handed to each interface neighbour
   Real *mom;             // rho, V'_x, V'_y, V'_z (4 x N) of each live cell that pulls
                          // from an empty cell, written by the step pass

@@ -1,11 +1,14 @@
 // Free-surface kernels (Section 3 of the paper): liquid-mass exchange,
 // stream/collide of liquid and interface cells with the reconstruction of
 // populations coming from empty cells, and the re-typing of cells whose
-// liquid fraction leaves [0, 1]. One step is six passes over the active
+// liquid fraction leaves [0, 1]. One step is five passes over the active
 // tiles (tiles within one tile of a liquid or interface cell; every cell
-// outside them is empty with nothing to do) and one compaction of the next
-// step's tiles. The re-typing passes return at once unless some cell flagged
-// a conversion in this step.
+// outside them is empty with nothing to do): the mass exchange, the
+// stream/collide with the conversion flags, the re-typing, the new interface
+// cells and excess mass, and the finish (shares received, liquid fraction,
+// the next step's tile list). Each pass needs its neighbours' results of the
+// one before; the conversion passes do nothing unless some cell flagged a
+// conversion in this step.
 #pragma once
 
 #include "lb_kernels.cuh"
@@ -45,7 +48,10 @@ __device__ __forceinline__ unsigned fs_tile_mask(unsigned lx, unsigned ly, unsig
 }
 
 // Stamps, for the next step, the tiles of the block-wide OR of the cells'
-// masks around tile (bx, by, bz) (wrapped; every thread of the block calls it).
+// masks around tile (bx, by, bz) (wrapped; every thread of the block calls
+// it); the stamp that first marks a tile for the next step also appends it to
+// the next step's list, so every tile is listed once (in no particular order:
+// a cell's update depends only on the previous step's values).
 template <class Real>
 __device__ __forceinline__ void fs_stamp_tiles(const FsArgs<Real> &s, unsigned bx, unsigned by,
                                                unsigned bz, unsigned mask) {
@@ -60,7 +66,8 @@ __device__ __forceinline__ void fs_stamp_tiles(const FsArgs<Real> &s, unsigned b
     const unsigned mx = (bx + s.ntx + k % 3 - 1) % s.ntx;
     const unsigned my = (by + s.nty + (k / 3) % 3 - 1) % s.nty;
     const unsigned mz = (bz + s.ntz + k / 9 - 1) % s.ntz;
-    s.stamp[mx + s.ntx * (my + s.nty * mz)] = *s.stamp_ctr + 1u;
+    const unsigned t = mx + s.ntx * (my + s.nty * mz), v = *s.stamp_ctr + 1u;
+    if (atomicExch(s.stamp + t, v) != v) s.next_tiles[atomicAdd(s.next_n_tiles, 1u)] = t;
   }
   __syncthreads();  // block_mask is reset for the next tile only after every read
 }
@@ -86,15 +93,6 @@ __device__ __forceinline__ void fs_tile_loop(const FsArgs<Real> &s, F &&cell) {
   }
 }
 
-// Lists the tiles stamped for the next step (order is immaterial: every
-// cell's update depends only on the previous step's values).
-template <class Real>
-__global__ void __launch_bounds__(BLOCK) fs_compact_kernel(const FsArgs<Real> s) {
-  const unsigned t = blockIdx.x * BLOCK + threadIdx.x;
-  if (t >= s.ntx * s.nty * s.ntz) return;
-  if (s.stamp[t] == *s.stamp_ctr + 1u) s.next_tiles[atomicAdd(s.next_n_tiles, 1u)] = t;
-}
-
 // After initialisation: one block per tile stamps the tiles the first step
 // needs around its liquid and interface cells.
 template <class Real>
@@ -112,21 +110,6 @@ __global__ void __launch_bounds__(BLOCK) fs_seed_kernel(const FsArgs<Real> s) {
     mask = fs_tile_mask(tx, ty, tz, live, live);
   }
   fs_stamp_tiles(s, bx, by, bz, mask);
-}
-
-// Density of a live cell from its populations of the step being completed
-// (the f_out buffer), in the collision type.
-template <class S>
-__device__ __forceinline__ typename S::Real cell_rho(const StepArgs<typename S::Real> &a,
-                                                     unsigned n) {
-  using Real = typename S::Real;
-  const typename S::T *f = static_cast<const typename S::T *>(a.f_out);
-  Real r = Real(0);
-  Unroll<0, Q>::run([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    r += S::template ld_f<q>(f + size_t(q) * a.N + n);
-  });
-  return Real(1) + r;
 }
 
 // Flowchart step g, Eqs. eq:massmacro, eq:massevol, eq:deltamass:
@@ -192,6 +175,7 @@ template <class S>
 __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
   using T = typename S::T;
+  static_assert(std::is_same<T, Real>::value, "free surface: storage in the collision type");
   const StepArgs<Real> &a = s.a;
   const unsigned N = a.N;
   fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
@@ -279,10 +263,16 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
   fc.stc = fc.st ? a.A * eps * tau : Real(0);
   fc.iFn = fc.st ? Real(1) / fc.Fn : Real(0);
   fc.fold(Real(1), Real(0));
+  // the post-collision density, summed from the stored values in direction
+  // order (as the liquid fraction and a filled cell's excess mass need it)
+  Real rp = Real(0);
   Unroll<0, Q>::run([&](auto qc) {
     constexpr int q = decltype(qc)::value;
-    S::template st_f<q>(fout + size_t(q) * N + n, fc.template post<q>(d[q]));
+    const Real v = fc.template post<q>(d[q]);
+    S::template st_f<q>(fout + size_t(q) * N + n, v);
+    rp += v;  // the stored value: FP32 / FP64 storage holds the collision type
   });
+  s.rho_post[n] = Real(1) + rp;
   write_fields(a.fields, N, n, rho, fc.Vp, Real(0), nu);
   // the moments a new interface cell averages: it was empty, so each of its
   // live neighbours pulled from it in this pass
@@ -307,31 +297,27 @@ __global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S:
   });
 }
 
-// An emptying cell next to a filling cell stays an interface cell.
+// Whether an emptying cell y is next to a filling one (then it stays an
+// interface cell), from the step's flags.
 template <class Real>
-__global__ void __launch_bounds__(BLOCK) fs_cancel_kernel(const FsArgs<Real> s) {
+__device__ __forceinline__ bool fs_near_fill(const FsArgs<Real> &s, long long y) {
   const StepArgs<Real> &a = s.a;
-  if (*s.any == 0u) return;
-  fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
-  uint8_t f = s.flag_a[n];
-  if (f == FS_EMPTYING) {
-    const uint32_t link = a.link ? a.link[n] : 0u;
-    const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
-    bool near_fill = false;
-    Unroll<1, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
-      if (y >= 0 && s.flag_a[y] == FS_FILL) near_fill = true;
-    });
-    if (near_fill) f = FS_NONE;
-  }
-  s.flag_b[n] = f;
-  return 0u;
+  const uint32_t link = a.link ? a.link[y] : 0u;
+  const CellGeo g = cell_geo(unsigned(y), a.nx, a.ny, a.nz);
+  bool near = false;
+  Unroll<1, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const long long y2 = fs_neighbor<q>(g, unsigned(y), link, a.f_wall);
+    if (y2 >= 0 && s.flag_a[y2] == FS_FILL) near = true;
   });
+  return near;
 }
 
-// New cell types: filled -> liquid, emptied -> empty, empty next to a filled
-// cell -> new interface, liquid next to an emptied cell -> interface.
+// New cell types, with the cancellation of an emptying cell next to a filling
+// one folded in (it reads the step's flags two links away): filled -> liquid,
+// emptied -> empty, empty next to a filled cell -> interface (flagged
+// FS_NEWCELL), liquid next to an emptied cell -> interface. flag_b gets each
+// cell's settled flag.
 template <class Real>
 __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) {
   const StepArgs<Real> &a = s.a;
@@ -339,22 +325,29 @@ __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) 
   uint8_t t = s.type_old[n];
   const uint32_t link = a.link ? a.link[n] : 0u;
   if (*s.any != 0u && !(link >> 31)) {
-    const uint8_t f = s.flag_b[n];
+    uint8_t f = s.flag_a[n];
+    if (f == FS_EMPTYING && fs_near_fill(s, n)) f = FS_NONE;
     if (f == FS_FILL) {
       t = CELL_LIQUID;
     } else if (f == FS_EMPTYING) {
       t = CELL_EMPTY;
     } else if (t == CELL_EMPTY || t == CELL_LIQUID) {
-      const uint8_t look = (t == CELL_EMPTY) ? FS_FILL : FS_EMPTYING;
       const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
+      const bool empty = t == CELL_EMPTY;
       bool hit = false;
       Unroll<1, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
-        if (y >= 0 && s.flag_b[y] == look) hit = true;
+        if (y < 0) return;
+        const uint8_t fy = s.flag_a[y];
+        if (empty ? fy == FS_FILL : (fy == FS_EMPTYING && !fs_near_fill(s, y))) hit = true;
       });
-      if (hit) t = (t == CELL_EMPTY) ? CELL_NEW_INTERFACE : CELL_INTERFACE;
+      if (hit) {
+        t = CELL_INTERFACE;
+        if (empty) f = FS_NEWCELL;
+      }
     }
+    s.flag_b[n] = f;
   }
   s.type_new[n] = t;
   return 0u;
@@ -362,9 +355,10 @@ __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) 
 }
 
 // New interface cells take f = f^eq(mean rho, mean V') of their liquid and
-// interface neighbours (hydrodynamic equilibrium, no mass); filled and
-// emptied cells hand their excess mass (m - rho, or m) in equal shares to the
-// neighbours that are interface cells after the re-typing.
+// interface neighbours that are not new themselves (hydrodynamic
+// equilibrium, no mass); filled and emptied cells hand their excess mass (m -
+// rho, or m) in equal shares to the neighbours that are interface cells after
+// the re-typing (they keep it when there are none).
 template <class S>
 __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
@@ -373,12 +367,11 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
   const unsigned N = a.N;
   if (*s.any == 0u) return;
   fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
-  const uint8_t tn = s.type_new[n];
   const uint8_t f = s.flag_b[n];
-  if (tn != CELL_NEW_INTERFACE && f == FS_NONE) return 0u;
+  if (f == FS_NONE) return 0u;
   const uint32_t link = a.link ? a.link[n] : 0u;
   const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
-  if (tn == CELL_NEW_INTERFACE) {
+  if (f == FS_NEWCELL) {
     // density and V' of each neighbour as its collision in this step left
     // them (its post-collision populations carry the same moments: the
     // collision conserves mass, and without Darcy drag their momentum is
@@ -390,7 +383,7 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
       const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
       if (y < 0) return;
       const uint8_t ty = s.type_new[y];
-      if (ty != CELL_LIQUID && ty != CELL_INTERFACE) return;
+      if ((ty != CELL_LIQUID && ty != CELL_INTERFACE) || s.flag_b[y] == FS_NEWCELL) return;
       rs += s.mom[y];
       u0 += s.mom[size_t(N) + y];
       u1 += s.mom[2 * size_t(N) + y];
@@ -403,6 +396,7 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
     const Real eps = a.eps[n];
     const Real ie = Real(1) / eps, uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     T *fout = static_cast<T *>(a.f_out);
+    Real rp = Real(0);
     Unroll<0, Q>::run([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       const Real cu = Real(cx(q)) * u[0] + Real(cy(q)) * u[1] + Real(cz(q)) * u[2];
@@ -410,34 +404,34 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
                                       r * (Real(3) * cu + Real(4.5) * ie * cu * cu -
                                            Real(1.5) * ie * uu));
       S::template st_f<q>(fout + size_t(q) * N + n, dev);
+      rp += dev;
     });
+    s.rho_post[n] = Real(1) + rp;  // the density of the stored populations, for lambda
     write_fields(a.fields, N, n, r, u, Real(0), (a.tau - Real(0.5)) / Real(3));
+    return 0u;
   }
-  if (f != FS_NONE) {
-    int cnt = 0;
-    Unroll<1, Q>::run([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
-      if (y < 0) return;
-      const uint8_t ty = s.type_new[y];
-      if (ty == CELL_INTERFACE || ty == CELL_NEW_INTERFACE) ++cnt;
-    });
-    // a filled cell keeps m = rho: its post-collision density, recomputed in
-    // the collision type (the exported field is float)
-    Real share = Real(0);
-    if (cnt > 0) {
-      const Real m = s.m_new[n];
-      const Real excess = (f == FS_FILL) ? m - cell_rho<S>(a, n) : m;
-      share = excess / Real(cnt);
-      s.m_new[n] = m - excess;
-    }
-    s.share[n] = share;
+  int cnt = 0;
+  Unroll<1, Q>::run([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
+    if (y >= 0 && s.type_new[y] == CELL_INTERFACE) ++cnt;
+  });
+  // a filled cell keeps m = rho: its post-collision density in the collision
+  // type (the exported field is float)
+  Real share = Real(0);
+  if (cnt > 0) {
+    const Real m = s.m_new[n];
+    const Real excess = (f == FS_FILL) ? m - s.rho_post[n] : m;
+    share = excess / Real(cnt);
+    s.m_new[n] = m - excess;
   }
+  s.share[n] = share;
   return 0u;
   });
 }
 
-// Excess mass arrives at interface cells; types settle; lambda = m / rho.
+// Excess mass arrives at interface cells; types settle; lambda = m / rho;
+// the next step's tiles are stamped and listed.
 template <class S>
 __global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
@@ -449,25 +443,23 @@ __global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename 
     s.lam[n] = Real(0);
     return 0u;
   }
-  uint8_t tn = s.type_new[n];
+  const uint8_t tn = s.type_new[n];
   Real m = s.m_new[n];
   if (*s.any != 0u) {
-    if (tn == CELL_INTERFACE || tn == CELL_NEW_INTERFACE) {
+    if (tn == CELL_INTERFACE) {
       const CellGeo g = cell_geo(n, a.nx, a.ny, a.nz);
       Unroll<1, Q>::run([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const long long y = fs_neighbor<q>(g, n, link, a.f_wall);
-        if (y >= 0 && s.flag_b[y] != FS_NONE) m += s.share[y];
+        if (y < 0) return;
+        const uint8_t fy = s.flag_b[y];
+        if (fy == FS_FILL || fy == FS_EMPTYING) m += s.share[y];
       });
       s.m_new[n] = m;
     }
-    if (tn == CELL_NEW_INTERFACE) {
-      tn = CELL_INTERFACE;
-      s.type_new[n] = tn;
-    }
     if (tn == CELL_EMPTY && s.flag_b[n] == FS_EMPTYING) zero_fields(a.fields, N, n);
   }
-  s.lam[n] = tn == CELL_LIQUID ? Real(1) : (tn == CELL_EMPTY ? Real(0) : m / cell_rho<S>(a, n));
+  s.lam[n] = tn == CELL_LIQUID ? Real(1) : (tn == CELL_EMPTY ? Real(0) : m / s.rho_post[n]);
   // both buffers of the type and the mass agree after the step, so a cell
   // whose tile leaves the list keeps the same values under either parity
   s.type_old[n] = tn;

@@ -54,11 +54,11 @@ struct StorageOps {
                           cudaStream_t s);
   cudaError_t (*totals)(PopView f, PopView h, const uint32_t *link, unsigned N, double *partials,
                         unsigned nblk, cudaStream_t s);
-  // one free-surface step, FsArgs<Real>*: six passes over the active tiles
-  // (grid blocks each) and the compaction of the next step's tiles
-  // (tile_blocks = ceil(tiles / BLOCK)); fs_seed stamps and lists the first
-  // step's tiles after initialisation (one block per tile). NULL when the
-  // storage format has no free-surface build
+  // one free-surface step, FsArgs<Real>*: five passes over the active tiles
+  // (grid blocks each; the last one also lists the next step's tiles);
+  // fs_seed stamps and lists the first step's tiles after initialisation (one
+  // block per tile; tile_blocks is unused). NULL when the storage format has
+  // no free-surface build
   cudaError_t (*fs_step)(const void *fs_args, unsigned grid, unsigned tile_blocks, cudaStream_t s);
   cudaError_t (*fs_seed)(const void *fs_args, unsigned tiles, unsigned tile_blocks, cudaStream_t s);
   // row-pipelined step kernel (NULL when not built for this storage):
