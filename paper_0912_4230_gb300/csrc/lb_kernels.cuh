@@ -678,6 +678,30 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
   }
 }
 
+// The rows of a cell's K^-1 for the velocity solve. With a full tensor, and
+// with the Forchheimer drag, they are loaded with the cell's other static
+// fields, before the moments, so their latency hides behind the gather
+// (loaded inside the solve they were a second wait per cell: 256^3 FP32
+// 0.955 -> 0.862 ms, FP16 0.738 -> 0.675 ms, 128^3 Forchheimer 0.136 ->
+// 0.122 ms); the three rows of a plain diagonal tensor stay in the solve,
+// where the register budget prefers them (128^3 FP32 0.1126 ms, 0.1165 ms
+// early).
+template <class Real, int KMODE>
+struct KinvRows {
+  static constexpr bool kEarly = KMODE == KM_SPD || KMODE == KM_FORCH;
+  Real v[kEarly ? 6 : 1];
+  __device__ __forceinline__ void load(const Real *kinv, unsigned N, unsigned n) {
+    if constexpr (kEarly)
+      for (int r = 0; r < 6; ++r) v[r] = __ldg(kinv + size_t(r) * N + n);
+  }
+  __device__ __forceinline__ Real row(const Real *kinv, unsigned N, unsigned n, int r) const {
+    if constexpr (kEarly)
+      return v[r];
+    else
+      return __ldg(kinv + size_t(r) * N + n);
+  }
+};
+
 // update_cell for 16-bit storage with solute (the paired layout): one 32-bit
 // load brings f_q and h_q of a source cell, one more its reference pair, and
 // both lattices are gathered per unit weight, d[q] = (f_q - w_q)/w_q and
@@ -725,6 +749,8 @@ __device__ __forceinline__ void update_cell_paired(const StepArgs<float> &a, uns
   const Real eps = __ldg(a.eps + n);
   const Real gx = __ldg(a.geps + n), gy = __ldg(a.geps + N + n),
              gz = __ldg(a.geps + 2 * size_t(N) + n);
+  KinvRows<Real, KMODE> kr;
+  kr.load(a.kinv, N, n);
   Real V[3];
   fluid_moments<true>([&](auto qc) { return d[decltype(qc)::value]; }, drho, V);
   const Real rho = Real(1) + drho;
@@ -762,8 +788,8 @@ __device__ __forceinline__ void update_cell_paired(const StepArgs<float> &a, uns
   collide_tail<S, KMODE, true, (FEAT & FEAT_SPEC) != 0>(
       a, n, g, [&](auto qc) { return d[decltype(qc)::value]; },
       [&](auto qc) { return hh[decltype(qc)::value]; },
-      [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
-      gz, vout);
+      [&](int r) { return kr.row(a.kinv, N, n, r); }, drho, rho, V, ie, eps, sC, gx, gy, gz,
+      vout);
 }
 
 // The per-cell update of one step from global memory: stream f (and h),
@@ -830,6 +856,8 @@ __device__ __forceinline__ void update_cell_sep(const StepArgs<typename S::Real>
   // every load of the interior path is issued before any arithmetic, so a
   // warp keeps its 38 population rows and static fields in flight together
   const Real eps = __ldg(a.eps + n);
+  KinvRows<Real, KMODE> kr;
+  kr.load(a.kinv, N, n);
   Real hh[SOLUTE ? Q : 1];
   Real gx = Real(0), gy = Real(0), gz = Real(0);
   const T *__restrict__ hb = static_cast<const T *>(a.h_in) + n;
@@ -882,8 +910,8 @@ __device__ __forceinline__ void update_cell_sep(const StepArgs<typename S::Real>
   collide_tail<S, KMODE, SOLUTE, (FEAT & FEAT_SPEC) != 0>(
       a, n, g, [&](auto qc) { return d[decltype(qc)::value]; },
       [&](auto qc) { return hh[SOLUTE ? decltype(qc)::value : 0]; },
-      [&](int r) { return __ldg(a.kinv + size_t(r) * N + n); }, drho, rho, V, ie, eps, sC, gx, gy,
-      gz, vout);
+      [&](int r) { return kr.row(a.kinv, N, n, r); }, drho, rho, V, ie, eps, sC, gx, gy, gz,
+      vout);
 }
 
 template <class S, int KMODE, bool SOLUTE, int FEAT = 0>
