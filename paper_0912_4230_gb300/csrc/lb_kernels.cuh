@@ -678,17 +678,20 @@ __device__ __forceinline__ void collide_tail(const StepArgs<typename S::Real> &a
   }
 }
 
-// The rows of a cell's K^-1 for the velocity solve. With a full tensor, and
-// with the Forchheimer drag, they are loaded with the cell's other static
-// fields, before the moments, so their latency hides behind the gather
-// (loaded inside the solve they were a second wait per cell: 256^3 FP32
-// 0.955 -> 0.862 ms, FP16 0.738 -> 0.675 ms, 128^3 Forchheimer 0.136 ->
-// 0.122 ms); the three rows of a plain diagonal tensor stay in the solve,
-// where the register budget prefers them (128^3 FP32 0.1126 ms, 0.1165 ms
-// early).
-template <class Real, int KMODE>
+// The rows of a cell's K^-1 for the velocity solve. With a full tensor, with
+// the Forchheimer drag, in the kernel that also advances further solute
+// species, and with 16-bit paired storage, they are loaded with the cell's
+// other static fields, before the moments, so their latency hides behind the
+// gather (loaded inside the solve they were a second wait per cell: 256^3
+// FP32 0.955 -> 0.862 ms, FP16 0.738 -> 0.675 ms, 128^3 Forchheimer 0.136 ->
+// 0.122 ms, three species 0.230 -> 0.221 ms, 128^3 FP16 0.0985 -> 0.0914 ms);
+// the three rows of a plain diagonal tensor with FP32/FP64 storage stay in the
+// solve, where the register budget prefers them (128^3 FP32 0.1126 ms,
+// 0.1165 ms early).
+template <class Real, int KMODE, bool SPEC = false, bool PAIRED = false>
 struct KinvRows {
-  static constexpr bool kEarly = KMODE == KM_SPD || KMODE == KM_FORCH;
+  static constexpr bool kEarly =
+      KMODE == KM_SPD || KMODE == KM_FORCH || ((SPEC || PAIRED) && KMODE == KM_DIAG);
   Real v[kEarly ? 6 : 1];
   __device__ __forceinline__ void load(const Real *kinv, unsigned N, unsigned n) {
     if constexpr (kEarly)
@@ -749,7 +752,7 @@ __device__ __forceinline__ void update_cell_paired(const StepArgs<float> &a, uns
   const Real eps = __ldg(a.eps + n);
   const Real gx = __ldg(a.geps + n), gy = __ldg(a.geps + N + n),
              gz = __ldg(a.geps + 2 * size_t(N) + n);
-  KinvRows<Real, KMODE> kr;
+  KinvRows<Real, KMODE, (FEAT & FEAT_SPEC) != 0, true> kr;
   kr.load(a.kinv, N, n);
   Real V[3];
   fluid_moments<true>([&](auto qc) { return d[decltype(qc)::value]; }, drho, V);
@@ -856,7 +859,7 @@ __device__ __forceinline__ void update_cell_sep(const StepArgs<typename S::Real>
   // every load of the interior path is issued before any arithmetic, so a
   // warp keeps its 38 population rows and static fields in flight together
   const Real eps = __ldg(a.eps + n);
-  KinvRows<Real, KMODE> kr;
+  KinvRows<Real, KMODE, (FEAT & FEAT_SPEC) != 0> kr;
   kr.load(a.kinv, N, n);
   Real hh[SOLUTE ? Q : 1];
   Real gx = Real(0), gy = Real(0), gz = Real(0);
