@@ -775,7 +775,7 @@ int lb_create(const lb_domain *dom, const float *porosity, const float *K6, cons
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return bail(fail(c, LB_ECUDA, "device attributes"));
-    c->fs_grid = unsigned(std::min<size_t>(ntiles, size_t(8) * unsigned(sms)));
+    c->fs_grid = unsigned(std::min<size_t>(ntiles, size_t(FS_BLOCKS_PER_SM) * unsigned(sms)));
   }
   // inputs -> device (caller pointers may be host or device)
   const size_t in_bytes = N * 4 + (K6 ? 6 * N * 4 : 0) + N + 64;

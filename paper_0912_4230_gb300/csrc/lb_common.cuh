@@ -296,7 +296,7 @@ struct FsArgs {
   // Active tiles of FS_TX x FS_TY x FS_TZ cells: the tiles within one tile
   // (26-neighbourhood, wrapped) of a tile holding a liquid or interface cell.
   // The step runs over this step's list; its last pass stamps the tiles of
-  // the next step and a compaction pass lists them.
+  // the next step and lists each tile the first time it stamps it.
   const uint32_t *tiles;
   const unsigned *n_tiles;
   uint32_t *next_tiles;
@@ -306,6 +306,10 @@ struct FsArgs {
                          // first pass of a step advances it, so a step is launch-invariant)
   unsigned ntx, nty, ntz;
 };
-constexpr unsigned FS_TX = 32, FS_TY = 4, FS_TZ = 2;  // one BLOCK of cells
+constexpr unsigned FS_TX = 32, FS_TY = 1, FS_TZ = 2;
+// the tile passes run one block of FS_BLOCK threads per tile (one thread a
+// cell), with as many blocks per SM as its 2048 threads and 32 blocks allow
+constexpr unsigned FS_BLOCK = FS_TX * FS_TY * FS_TZ;
+constexpr unsigned FS_BLOCKS_PER_SM = 2048 / FS_BLOCK < 32 ? 2048 / FS_BLOCK : 32;
 
 }  // namespace lbgb

@@ -26,7 +26,8 @@ __device__ __forceinline__ long long fs_neighbor(const CellGeo &g, unsigned n, u
   return (long long)n + ahead_delta<q>(g);
 }
 
-static_assert(FS_TX * FS_TY * FS_TZ == BLOCK, "one tile per block of BLOCK threads");
+static_assert(FS_BLOCK % 32 == 0 && FS_BLOCK >= 27,
+              "whole warps per tile, and a thread for each of the 27 tiles around it");
 
 // Tiles needed by the next step around one cell, as a mask over the 27
 // tile offsets (bit (dx+1) + 3(dy+1) + 9(dz+1)): the cell's own tile when
@@ -96,7 +97,7 @@ __device__ __forceinline__ void fs_tile_loop(const FsArgs<Real> &s, F &&cell) {
 // After initialisation: one block per tile stamps the tiles the first step
 // needs around its liquid and interface cells.
 template <class Real>
-__global__ void __launch_bounds__(BLOCK) fs_seed_kernel(const FsArgs<Real> s) {
+__global__ void __launch_bounds__(FS_BLOCK) fs_seed_kernel(const FsArgs<Real> s) {
   const unsigned tile = blockIdx.x;
   const unsigned bx = tile % s.ntx, r = tile / s.ntx, by = r % s.nty, bz = r / s.nty;
   const unsigned tx = threadIdx.x % FS_TX, ty = (threadIdx.x / FS_TX) % FS_TY,
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(BLOCK) fs_seed_kernel(const FsArgs<Real> s) {
 // interface cells, and no exchange with empty or solid cells. The colour
 // gradient field is the new liquid mass (0 in empty, wall_rho in solid cells).
 template <class S>
-__global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S::Real> s) {
+__global__ void __launch_bounds__(FS_BLOCK) fs_mass_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
   using T = typename S::T;
   const StepArgs<Real> &a = s.a;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(BLOCK) fs_mass_kernel(const FsArgs<typename S:
 // without Darcy drag); moments, colour gradient, BGK collision with forcing
 // and surface tension; then lambda = m / rho and the fill/empty flags.
 template <class S>
-__global__ void __launch_bounds__(BLOCK) fs_step_kernel(const FsArgs<typename S::Real> s) {
+__global__ void __launch_bounds__(FS_BLOCK) fs_step_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
   using T = typename S::T;
   static_assert(std::is_same<T, Real>::value, "free surface: storage in the collision type");
@@ -319,7 +320,7 @@ __device__ __forceinline__ bool fs_near_fill(const FsArgs<Real> &s, long long y)
 // FS_NEWCELL), liquid next to an emptied cell -> interface. flag_b gets each
 // cell's settled flag.
 template <class Real>
-__global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) {
+__global__ void __launch_bounds__(FS_BLOCK) fs_retype_kernel(const FsArgs<Real> s) {
   const StepArgs<Real> &a = s.a;
   fs_tile_loop<false>(s, [&](unsigned n, unsigned, unsigned, unsigned) -> unsigned {
   uint8_t t = s.type_old[n];
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(BLOCK) fs_retype_kernel(const FsArgs<Real> s) 
 // rho, or m) in equal shares to the neighbours that are interface cells after
 // the re-typing (they keep it when there are none).
 template <class S>
-__global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename S::Real> s) {
+__global__ void __launch_bounds__(FS_BLOCK) fs_newcell_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
   using T = typename S::T;
   const StepArgs<Real> &a = s.a;
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(BLOCK) fs_newcell_kernel(const FsArgs<typename
 // Excess mass arrives at interface cells; types settle; lambda = m / rho;
 // the next step's tiles are stamped and listed.
 template <class S>
-__global__ void __launch_bounds__(BLOCK) fs_finish_kernel(const FsArgs<typename S::Real> s) {
+__global__ void __launch_bounds__(FS_BLOCK) fs_finish_kernel(const FsArgs<typename S::Real> s) {
   using Real = typename S::Real;
   const StepArgs<Real> &a = s.a;
   const unsigned N = a.N;

@@ -108,18 +108,18 @@ struct Instance {
   static cudaError_t fs_step(const void *args, unsigned grid, unsigned tile_blocks,
                              cudaStream_t s) {
     const FsArgs<Real> &f = *static_cast<const FsArgs<Real> *>(args);
-    fs_mass_kernel<S><<<grid, BLOCK, 0, s>>>(f);
-    fs_step_kernel<S><<<grid, BLOCK, 0, s>>>(f);
-    fs_retype_kernel<Real><<<grid, BLOCK, 0, s>>>(f);
-    fs_newcell_kernel<S><<<grid, BLOCK, 0, s>>>(f);
-    fs_finish_kernel<S><<<grid, BLOCK, 0, s>>>(f);
+    fs_mass_kernel<S><<<grid, FS_BLOCK, 0, s>>>(f);
+    fs_step_kernel<S><<<grid, FS_BLOCK, 0, s>>>(f);
+    fs_retype_kernel<Real><<<grid, FS_BLOCK, 0, s>>>(f);
+    fs_newcell_kernel<S><<<grid, FS_BLOCK, 0, s>>>(f);
+    fs_finish_kernel<S><<<grid, FS_BLOCK, 0, s>>>(f);
     (void)tile_blocks;
     return cudaGetLastError();
   }
   static cudaError_t fs_seed(const void *args, unsigned tiles, unsigned tile_blocks,
                              cudaStream_t s) {
     const FsArgs<Real> &f = *static_cast<const FsArgs<Real> *>(args);
-    fs_seed_kernel<Real><<<tiles, BLOCK, 0, s>>>(f);
+    fs_seed_kernel<Real><<<tiles, FS_BLOCK, 0, s>>>(f);
     (void)tile_blocks;
     return cudaGetLastError();
   }

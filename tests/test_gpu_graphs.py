@@ -104,7 +104,7 @@ def test_batch_graph_equals_direct_launches(storage):
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 def test_free_surface_steps_from_the_graph(storage):
-    """The free-surface step (seven passes over device-side tile lists, the
+    """The free-surface step (five passes over device-side tile lists, the
     stamp counter on the device) replayed from a graph: cell types, liquid
     mass and populations bit-identical to direct launches."""
     p = W.drop(nx=24, ny=24, nz=28, R=5.0, gap=6.0, seed=3)
